@@ -1,0 +1,257 @@
+"""CPU oracle for the tetrahedral-mesh projectors -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its
+``cpu_baseline`` and ``--impl reference`` legs) may import this package.  The
+product library never loads it, and it shares no code with the CUDA path.
+
+``oracle.c`` evaluates the paper's plain definition (Eq. 1-3): every chord
+a_ij = |half-line j  intersected with closed tet i| is computed by brute-force
+clipping of every ray against every tet, in FP64.  ``exact.py`` holds exact
+rational predicates (orientation, the symbolic tie-break) used to pin the
+predicate cascade of the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_c_dp = ctypes.POINTER(ctypes.c_double)
+_c_ip = ctypes.POINTER(ctypes.c_int32)
+_c_lp = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain C, FP64, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.oracle_version.restype = ctypes.c_int64
+        L.oracle_cone_rays.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_double, ctypes.c_double, _c_dp,
+                                       ctypes.c_int64, _c_lp, ctypes.c_int64, _c_dp, _c_dp]
+        L.oracle_tet_chord.argtypes = [_c_dp, _c_dp, _c_dp, _c_dp, _c_dp]
+        L.oracle_tet_chord.restype = ctypes.c_double
+        L.oracle_forward_rays.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
+                                          ctypes.c_int, _c_dp, _c_dp, _c_dp, ctypes.c_int64,
+                                          _c_dp, ctypes.c_int]
+        L.oracle_forward_cone.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                          ctypes.c_double, _c_dp, ctypes.c_int64, _c_lp,
+                                          ctypes.c_int64, _c_dp, ctypes.c_int]
+        L.oracle_backward_rays.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
+                                           ctypes.c_int, _c_dp, _c_dp, _c_dp, ctypes.c_int64,
+                                           _c_dp, ctypes.c_int]
+        L.oracle_backward_cone.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
+                                           ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                           ctypes.c_double, _c_dp, ctypes.c_int64, _c_dp,
+                                           ctypes.c_int]
+        L.oracle_backward_cone_subset.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64,
+                                                  _c_dp, ctypes.c_int, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                                  ctypes.c_double, ctypes.c_double, _c_dp,
+                                                  ctypes.c_int64, _c_lp, ctypes.c_int64, _c_dp,
+                                                  ctypes.c_int]
+        L.oracle_trace_rays.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
+                                        _c_dp, ctypes.c_int64, ctypes.c_int64, _c_ip, _c_dp,
+                                        _c_dp, _c_lp, _c_dp, _c_ip, ctypes.c_int]
+        for f in ("oracle_forward_rays", "oracle_forward_cone", "oracle_backward_rays",
+                  "oracle_backward_cone", "oracle_backward_cone_subset", "oracle_trace_rays"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_c_dp)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_c_ip)
+
+
+def _l(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(_c_lp)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"{what} failed with code {rc}")
+
+
+def cone_rays(geom, idx=None):
+    """(S, P) endpoints [n,3] for cone-beam ray indices j = (a*nv + iv)*nu + iu."""
+    ang, angp = _d(geom.angles)
+    n = geom.nrays if idx is None else len(idx)
+    S = np.empty((n, 3))
+    P = np.empty((n, 3))
+    if idx is None:
+        ip = None
+    else:
+        idx, ip = _l(idx)
+    lib().oracle_cone_rays(geom.dso, geom.dsd, geom.nu, geom.nv, geom.du, geom.dv, angp,
+                           geom.nangles, ip, n, S.ctypes.data_as(_c_dp), P.ctypes.data_as(_c_dp))
+    return S, P
+
+
+def tet_chord(tet_verts, S, P):
+    """a for one tet [4,3] and one ray; returns (length, t_lo, t_hi)."""
+    v, vp = _d(np.asarray(tet_verts).reshape(12))
+    s, sp = _d(S)
+    p, pp = _d(P)
+    lo = ctypes.c_double()
+    hi = ctypes.c_double()
+    a = lib().oracle_tet_chord(vp, sp, pp, ctypes.byref(lo), ctypes.byref(hi))
+    return a, lo.value, hi.value
+
+
+def _mesh(verts, tets):
+    v, vp = _d(verts)
+    t, tp = _i(tets)
+    return v, vp, t, tp
+
+
+def _channels(x, n):
+    x = np.asarray(x, dtype=np.float64)
+    C = 1 if x.ndim == 1 else x.shape[1]
+    return np.ascontiguousarray(x.reshape(n, C)), C
+
+
+def forward_rays(verts, tets, mu, S, P, side=None, threads=None):
+    """b_j = sum_i a_ij mu_i for explicit rays (Eq. 2).  ``side``: per-ray
+    directions [n,3] choosing one-sided limits for rays in face planes."""
+    v, vp, t, tp = _mesh(verts, tets)
+    mu2, C = _channels(mu, t.shape[0])
+    m, mp = _d(mu2)
+    s, sp = _d(S)
+    p, pp = _d(P)
+    n = s.shape[0]
+    w, wp = (None, None) if side is None else _d(side)
+    out = np.empty((n, C))
+    _check(lib().oracle_forward_rays(vp, v.shape[0], tp, t.shape[0], mp, C, sp, pp, wp, n,
+                                     out.ctypes.data_as(_c_dp), threads or default_threads()),
+           "oracle_forward_rays")
+    return out[:, 0] if np.asarray(mu).ndim == 1 else out
+
+
+def forward_cone(verts, tets, mu, geom, ray_idx=None, threads=None):
+    """b = A mu for cone-beam rays (all, or the selected ray indices)."""
+    v, vp, t, tp = _mesh(verts, tets)
+    mu2, C = _channels(mu, t.shape[0])
+    m, mp = _d(mu2)
+    ang, angp = _d(geom.angles)
+    if ray_idx is None:
+        ip, n = None, geom.nrays
+    else:
+        ray_idx, ip = _l(ray_idx)
+        n = ray_idx.size
+    out = np.empty((n, C))
+    _check(lib().oracle_forward_cone(vp, v.shape[0], tp, t.shape[0], mp, C, geom.dso, geom.dsd,
+                                     geom.nu, geom.nv, geom.du, geom.dv, angp, geom.nangles, ip, n,
+                                     out.ctypes.data_as(_c_dp), threads or default_threads()),
+           "oracle_forward_cone")
+    return out[:, 0] if np.asarray(mu).ndim == 1 else out
+
+
+def backward_rays(verts, tets, y, S, P, side=None, threads=None):
+    """x_i = sum_j a_ij y_j for explicit rays (Eq. 3)."""
+    v, vp, t, tp = _mesh(verts, tets)
+    s, sp = _d(S)
+    n = s.shape[0]
+    y2, C = _channels(y, n)
+    yy, yp = _d(y2)
+    p, pp = _d(P)
+    w, wp = (None, None) if side is None else _d(side)
+    out = np.empty((t.shape[0], C))
+    _check(lib().oracle_backward_rays(vp, v.shape[0], tp, t.shape[0], yp, C, sp, pp, wp, n,
+                                      out.ctypes.data_as(_c_dp), threads or default_threads()),
+           "oracle_backward_rays")
+    return out[:, 0] if np.asarray(y).ndim == 1 else out
+
+
+def backward_cone(verts, tets, y, geom, threads=None):
+    """x = A^T y over all cone-beam rays; y laid out [angle][iv][iu](,C)."""
+    v, vp, t, tp = _mesh(verts, tets)
+    y = np.asarray(y, dtype=np.float64)
+    C = y.size // geom.nrays
+    y2 = y.reshape(geom.nrays, C)
+    yy, yp = _d(y2)
+    ang, angp = _d(geom.angles)
+    out = np.empty((t.shape[0], C))
+    _check(lib().oracle_backward_cone(vp, v.shape[0], tp, t.shape[0], yp, C, geom.dso, geom.dsd,
+                                      geom.nu, geom.nv, geom.du, geom.dv, angp, geom.nangles,
+                                      out.ctypes.data_as(_c_dp), threads or default_threads()),
+           "oracle_backward_cone")
+    return out[:, 0] if C == 1 else out
+
+
+def backward_cone_subset(verts, tets, y, geom, tet_idx, threads=None):
+    """x_i for the selected tets only, summed over all cone-beam rays."""
+    v, vp, t, tp = _mesh(verts, tets)
+    y = np.asarray(y, dtype=np.float64)
+    C = 1 if y.size == geom.nrays else y.size // geom.nrays
+    yy, yp = _d(y.reshape(geom.nrays, C))
+    ang, angp = _d(geom.angles)
+    tet_idx, ip = _l(tet_idx)
+    out = np.empty((tet_idx.size, C))
+    _check(lib().oracle_backward_cone_subset(vp, v.shape[0], tp, t.shape[0], yp, C, geom.dso,
+                                             geom.dsd, geom.nu, geom.nv, geom.du, geom.dv, angp,
+                                             geom.nangles, ip, tet_idx.size,
+                                             out.ctypes.data_as(_c_dp),
+                                             threads or default_threads()),
+           "oracle_backward_cone_subset")
+    return out[:, 0] if C == 1 else out
+
+
+def trace_rays(verts, tets, S, P, max_visits=1024, threads=None):
+    """Row j of A per ray: (tets, t_lo, t_hi, count, margin, planar).
+
+    tets[j, :count[j]] are the tets with a_ij > 0 sorted by entry parameter;
+    margin[j] is the smallest |t_hi - t_lo| * |P - S| over all tets (small =
+    the ray grazes an edge or vertex); planar[j] = ray lies in a face plane."""
+    v, vp, t, tp = _mesh(verts, tets)
+    s, sp = _d(S)
+    p, pp = _d(P)
+    n = s.shape[0]
+    tt = np.full((n, max_visits), -1, np.int32)
+    lo = np.zeros((n, max_visits))
+    hi = np.zeros((n, max_visits))
+    cnt = np.zeros(n, np.int64)
+    mg = np.zeros(n)
+    pl = np.zeros(n, np.int32)
+    _check(lib().oracle_trace_rays(vp, v.shape[0], tp, t.shape[0], sp, pp, n, max_visits,
+                                   tt.ctypes.data_as(_c_ip), lo.ctypes.data_as(_c_dp),
+                                   hi.ctypes.data_as(_c_dp), cnt.ctypes.data_as(_c_lp),
+                                   mg.ctypes.data_as(_c_dp), pl.ctypes.data_as(_c_ip),
+                                   threads or default_threads()),
+           "oracle_trace_rays")
+    return tt, lo, hi, cnt, mg, pl.astype(bool)

@@ -1,0 +1,243 @@
+"""Exact rational geometry for pinning -- TEST INFRASTRUCTURE ONLY.
+
+Every FP64 input is converted to a ``fractions.Fraction`` (exactly), so signs
+and parameters below are exact.  This module is independent of both the C
+oracle (which clips with plane equations in FP64) and the CUDA library.
+
+Contents
+--------
+side(S, P, p, q)
+    The Pluecker side of the line through S, P against the directed edge p->q:
+    det[P - S, p - S, q - S].  Its sign says on which side of the edge line the
+    ray line passes (Sec. II-C uses four triangle tests per tet; a triangle is
+    crossed iff the three edge sides agree in sign).
+side_sos(S, P, p, q)
+    Sign of ``side`` for the symbolically perturbed line through
+    S + (e, e^2, e^4) and P + (e^8, e^16, e^32), e -> 0+.  This is the tie-break
+    used where the paper only says that zero-length intersections need a check
+    (Alg. 2, "if t2 = t1 check if they need to be swapped"): perturbing the
+    *line*, not the vertices, makes every tet see the same perturbed ray, so
+    the walk can neither leak nor loop.
+side_sos_bruteforce(S, P, p, q, eps)
+    Sign of the exact determinant for that perturbed line at a concrete tiny
+    rational eps; pins ``side_sos``.
+plucker_interval(V, S, P)
+    Exact parameter interval of the line inside a tet, found from the
+    barycentric coordinates of the crossing points (edge sides as weights),
+    not from plane equations; pins the oracle's Cyrus-Beck clipper.
+kuhn_crossings(n, S, P)
+    Exact count of positive-length pieces of a ray in the unjittered Kuhn
+    split of [-1,1]^n-cells: the split is the arrangement of the planes
+    x_i = (2k - n)/n and x_i - x_j = 2k/n.
+cube_interval(S, P)
+    Exact parameter interval of the half-line in [-1, 1]^3.
+"""
+from __future__ import annotations
+
+from fractions import Fraction as Fr
+from typing import Sequence
+
+Vec = Sequence
+
+
+def fr3(v) -> tuple:
+    return tuple(Fr(float(x)) for x in v)
+
+
+def sub(a, b):
+    return (a[0] - b[0], a[1] - b[1], a[2] - b[2])
+
+
+def cross(a, b):
+    return (a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0])
+
+
+def dot(a, b):
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
+
+
+def det3(r0, r1, r2):
+    return dot(r0, cross(r1, r2))
+
+
+def sign(x) -> int:
+    return (x > 0) - (x < 0)
+
+
+def side(S, P, p, q) -> Fr:
+    S, P, p, q = fr3(S), fr3(P), fr3(p), fr3(q)
+    return det3(sub(P, S), sub(p, S), sub(q, S))
+
+
+def _sos_coefficients(S, P, p, q):
+    """Coefficients of side(S + s, P + r, p, q) in powers of e, for
+    s = (e, e^2, e^4), r = (e^8, e^16, e^32), listed by increasing exponent.
+
+    side is affine in S and in P (it is a 4x4 determinant with rows (S,1),
+    (P,1), (p,1), (q,1)), so the expansion has a constant term, terms linear in
+    s and in r, and a bilinear term (q - p).(s x r).
+      d side / dS = -(p - P) x (q - P)       (exponents 1, 2, 4)
+      d side / dP =  (p - S) x (q - S)       (exponents 8, 16, 32)
+      (q - p).(s x r): s_i r_j has exponent 2^i + 2^(3+j).
+    """
+    S, P, p, q = fr3(S), fr3(P), fr3(p), fr3(q)
+    d2 = sub(q, p)
+    cs = cross(sub(p, P), sub(q, P))
+    cs = (-cs[0], -cs[1], -cs[2])
+    cr = cross(sub(p, S), sub(q, S))
+    terms = {0: det3(sub(P, S), sub(p, S), sub(q, S))}
+    for i in range(3):
+        terms[1 << i] = cs[i]
+        terms[1 << (3 + i)] = cr[i]
+    e = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    for i in range(3):
+        for j in range(3):
+            k = (1 << i) + (1 << (3 + j))
+            terms[k] = terms.get(k, 0) + dot(d2, cross(e[i], e[j]))
+    return [terms[k] for k in sorted(terms)]
+
+
+def side_sos(S, P, p, q) -> int:
+    for c in _sos_coefficients(S, P, p, q):
+        if c != 0:
+            return sign(c)
+    return 0  # only when p == q
+
+
+def side_sos_bruteforce(S, P, p, q, eps: Fr = Fr(1, 2 ** 40)) -> int:
+    """Exact sign of the determinant for the perturbed line at a concrete eps.
+
+    Equals side_sos when eps is small enough that the lowest non-zero
+    coefficient dominates the rest (true for the inputs of the tests, whose
+    coefficients are bounded and whose exponents differ by >= 1)."""
+    S, P, p, q = fr3(S), fr3(P), fr3(p), fr3(q)
+    s = (eps, eps ** 2, eps ** 4)
+    r = (eps ** 8, eps ** 16, eps ** 32)
+    S2 = tuple(S[i] + s[i] for i in range(3))
+    P2 = tuple(P[i] + r[i] for i in range(3))
+    return sign(det3(sub(P2, S2), sub(p, S2), sub(q, S2)))
+
+
+def orient3d(a, b, c, d) -> Fr:
+    a, b, c, d = fr3(a), fr3(b), fr3(c), fr3(d)
+    return det3(sub(b, a), sub(c, a), sub(d, a))
+
+
+# Local faces of a positively oriented tet (v0, v1, v2, v3): face f is opposite
+# v_f; the triple is ordered so that orient3d(a, b, c, v_f) > 0.
+FACE_TRIPLE = {0: (1, 3, 2), 1: (0, 2, 3), 2: (0, 3, 1), 3: (0, 1, 2)}
+
+
+def plucker_interval(V, S, P):
+    """Exact (t_in, t_out) of the line S + t (P - S) inside tet V [4][3], or None.
+
+    A face (a, b, c), ordered so the opposite vertex is on its positive side,
+    is crossed inward iff side(a->b), side(b->c), side(c->a) are all > 0 and
+    outward iff all < 0 (for rays crossing no edge).  The crossing point is
+    X = (w_a a + w_b b + w_c c) / (w_a + w_b + w_c) with w_a = side(b->c),
+    w_b = side(c->a), w_c = side(a->b), and t = (X - S).(P - S) / |P - S|^2.
+    The interval is NOT clipped to t >= 0 here.
+    """
+    Vf = [fr3(v) for v in V]
+    if orient3d(*Vf) < 0:
+        Vf[2], Vf[3] = Vf[3], Vf[2]
+    Sf, Pf = fr3(S), fr3(P)
+    d = sub(Pf, Sf)
+    dd = dot(d, d)
+    t_in = t_out = None
+    for f, (i, j, k) in FACE_TRIPLE.items():
+        a, b, c = Vf[i], Vf[j], Vf[k]
+        wc = det3(d, sub(a, Sf), sub(b, Sf))
+        wa = det3(d, sub(b, Sf), sub(c, Sf))
+        wb = det3(d, sub(c, Sf), sub(a, Sf))
+        if (wa > 0 and wb > 0 and wc > 0) or (wa < 0 and wb < 0 and wc < 0):
+            W = wa + wb + wc
+            X = tuple((wa * a[m] + wb * b[m] + wc * c[m]) / W for m in range(3))
+            t = dot(sub(X, Sf), d) / dd
+            if wa > 0:
+                t_in = t
+            else:
+                t_out = t
+    if t_in is None or t_out is None:
+        return None
+    return t_in, t_out
+
+
+def cube_interval(S, P, half: Fr = Fr(1)):
+    """Exact parameter interval of the half-line (t >= 0) inside [-half, half]^3."""
+    Sf, Pf = fr3(S), fr3(P)
+    d = sub(Pf, Sf)
+    lo, hi = Fr(0), None
+    for i in range(3):
+        if d[i] == 0:
+            if not (-half <= Sf[i] <= half):
+                return None
+            continue
+        t1 = (-half - Sf[i]) / d[i]
+        t2 = (half - Sf[i]) / d[i]
+        if t1 > t2:
+            t1, t2 = t2, t1
+        lo = max(lo, t1)
+        hi = t2 if hi is None else min(hi, t2)
+    if hi is None or hi <= lo:
+        return None
+    return lo, hi
+
+
+def box_interval(S, P, lo_corner, hi_corner):
+    """Exact parameter interval of the half-line inside an axis-aligned box."""
+    Sf, Pf = fr3(S), fr3(P)
+    d = sub(Pf, Sf)
+    lo, hi = Fr(0), None
+    for i in range(3):
+        a, b = Fr(lo_corner[i]), Fr(hi_corner[i])
+        if d[i] == 0:
+            if not (a <= Sf[i] <= b):
+                return None
+            continue
+        t1 = (a - Sf[i]) / d[i]
+        t2 = (b - Sf[i]) / d[i]
+        if t1 > t2:
+            t1, t2 = t2, t1
+        lo = max(lo, t1)
+        hi = t2 if hi is None else min(hi, t2)
+    if hi is None or hi <= lo:
+        return None
+    return lo, hi
+
+
+def kuhn_crossings(n: int, S, P):
+    """(#positive-length pieces, in_plane) of the half-line in the Kuhn split of
+    [-1,1]^3 into n^3 cells.  in_plane is True when the ray lies inside one of
+    the arrangement's planes (then the count is not meaningful)."""
+    iv = cube_interval(S, P)
+    if iv is None:
+        return 0, False
+    t0, t1 = iv
+    Sf, Pf = fr3(S), fr3(P)
+    d = sub(Pf, Sf)
+    ts = set()
+    for i in range(3):
+        if d[i] == 0:
+            for k in range(n + 1):
+                if Sf[i] == Fr(2 * k - n, n):
+                    return 0, True
+            continue
+        for k in range(n + 1):
+            t = (Fr(2 * k - n, n) - Sf[i]) / d[i]
+            if t0 < t < t1:
+                ts.add(t)
+    for i in range(3):
+        for j in range(i + 1, 3):
+            dd = d[i] - d[j]
+            ss = Sf[i] - Sf[j]
+            if dd == 0:
+                for k in range(-n, n + 1):
+                    if ss == Fr(2 * k, n):
+                        return 0, True
+                continue
+            for k in range(-n, n + 1):
+                t = (Fr(2 * k, n) - ss) / dd
+                if t0 < t < t1:
+                    ts.add(t)
+    return 1 + len(ts), False

@@ -1,0 +1,520 @@
+/*
+ * oracle.c -- plain FP64 CPU reference for the tetrahedral-mesh projectors.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call
+ * this file; only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * reference leg use it.  It shares no code with the CUDA library.
+ *
+ * What it computes is the paper's plain definition, not its algorithm:
+ *
+ *   Eq. 1   A x = b + e,  a_ij = length of (ray j  intersected with element i)
+ *   Eq. 2   b_j = sum_i a_ij x_i                        (forward projection)
+ *   Eq. 3   x_i = sum_j a_ij b_j                        (backprojection; the
+ *           paper prints b_i under a sum over j, read as b_j)
+ *
+ * a_ij is evaluated by brute force for every (ray, tet) pair: the half-line
+ * X(t) = S + t (P - S), t >= 0, is clipped against the four face half-spaces of
+ * the closed tet (Cyrus-Beck), giving the parameter interval [lo, hi]; then
+ * a_ij = max(0, hi - lo) * |P - S|.  There is no traversal, no adjacency, no
+ * acceleration structure: every tet is tested against every ray.
+ *
+ * Ray convention (the paper leaves it implicit; Alg. 2 launches one ray per
+ * detector pixel and uses l = |R2 - R1|): R1 = source S, R2 = pixel centre P.
+ * Circular cone beam about the z axis, for angle theta:
+ *   S = (dso cos, dso sin, 0), C = S - dsd (cos, sin, 0), U = (-sin, cos, 0),
+ *   V = (0, 0, 1), P = C + u U + v V with
+ *   u = (iu - (nu-1)/2) du, v = (iv - (nv-1)/2) dv.
+ * Ray index j = (a * nv + iv) * nu + iu.  Every product and sum is rounded
+ * separately (this file must be compiled with -ffp-contract=off) so that the
+ * rays are bit-identical to any other implementation of the same convention.
+ *
+ * Sums over tets (forward) and over rays (backward) use Neumaier compensated
+ * summation in FP64.  Backward sums are accumulated per thread over disjoint
+ * ray ranges and added in thread order, so results do not depend on timing.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_VERSION 1
+
+int64_t oracle_version(void) { return ORACLE_VERSION; }
+
+/* ---------------------------------------------------------------- geometry */
+
+typedef struct {
+    double dso, dsd, du, dv;
+    int64_t nu, nv, na;
+    const double *angles;
+} cone_geom;
+
+static void cone_ray(const cone_geom *g, int64_t j, double S[3], double P[3]) {
+    int64_t iu = j % g->nu;
+    int64_t iv = (j / g->nu) % g->nv;
+    int64_t a = j / (g->nu * g->nv);
+    double th = g->angles[a];
+    double c = cos(th), s = sin(th);
+    double Sx = g->dso * c, Sy = g->dso * s, Sz = 0.0;
+    double Cx = Sx - g->dsd * c, Cy = Sy - g->dsd * s, Cz = 0.0;
+    double Ux = -s, Uy = c, Uz = 0.0;
+    double Vx = 0.0, Vy = 0.0, Vz = 1.0;
+    double u = ((double)iu - 0.5 * (double)(g->nu - 1)) * g->du;
+    double v = ((double)iv - 0.5 * (double)(g->nv - 1)) * g->dv;
+    S[0] = Sx; S[1] = Sy; S[2] = Sz;
+    P[0] = (Cx + u * Ux) + v * Vx;
+    P[1] = (Cy + u * Uy) + v * Vy;
+    P[2] = (Cz + u * Uz) + v * Vz;
+}
+
+/* Ray endpoints for a list of ray indices (or all rays when idx == NULL). */
+void oracle_cone_rays(double dso, double dsd, int64_t nu, int64_t nv, double du, double dv,
+                      const double *angles, int64_t na, const int64_t *idx, int64_t n,
+                      double *S_out, double *P_out) {
+    cone_geom g = {dso, dsd, du, dv, nu, nv, na, angles};
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t j = idx ? idx[k] : k;
+        cone_ray(&g, j, S_out + 3 * k, P_out + 3 * k);
+    }
+}
+
+/* ------------------------------------------------------------ one tet clip */
+
+static double dot3(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+static void sub3(const double a[3], const double b[3], double r[3]) {
+    r[0] = a[0] - b[0]; r[1] = a[1] - b[1]; r[2] = a[2] - b[2];
+}
+static void cross3(const double a[3], const double b[3], double r[3]) {
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/*
+ * Clip the half-line S + t d (t >= 0) against the closed tet with vertices
+ * v[0..3].  Face k is the triangle of the three vertices other than v[k]; its
+ * normal is turned to point away from v[k] (outward).  A point X is inside the
+ * face's half-space iff n.(X - q) <= 0 for a face vertex q, i.e.
+ *   t (n.d) <= n.(q - S).
+ * Returns 0 if the tet is degenerate (a face plane contains the opposite
+ * vertex), 1 otherwise; *lo, *hi receive the clipped parameter interval
+ * (empty when *hi <= *lo).
+ *
+ * A ray lying in a face plane (|n.d| and |n.(q-S)| both below PLANE_TOL
+ * relative) is on the boundary of both tets sharing that face, so the closed
+ * measure counts it twice and FP64 cannot tell the sides apart.  *planar is
+ * set for such rays.  When a side direction w is given, the face constraint is
+ * replaced by its limit for the ray moved by +0*w: satisfied if n.w < 0, empty
+ * otherwise.  That gives the one-sided limits of the integral.
+ */
+#define PLANE_TOL 1e-12
+static int tet_clip(const double v[4][3], const double S[3], const double d[3],
+                    const double *w, double *lo, double *hi, int *planar) {
+    double l = 0.0, h = INFINITY;
+    int empty = 0;
+    *planar = 0;
+    double dd = sqrt(dot3(d, d));
+    for (int k = 0; k < 4; ++k) {
+        const double *q0 = v[(k + 1) & 3], *q1 = v[(k + 2) & 3], *q2 = v[(k + 3) & 3];
+        double e1[3], e2[3], n[3], x[3];
+        sub3(q1, q0, e1);
+        sub3(q2, q0, e2);
+        cross3(e1, e2, n);
+        sub3(v[k], q0, x);
+        double side = dot3(n, x);
+        if (side == 0.0) return 0;
+        if (side > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+        double qs[3];
+        sub3(q0, S, qs);
+        double num = dot3(n, qs);
+        double den = dot3(n, d);
+        double nn = sqrt(dot3(n, n));
+        int inplane = fabs(den) <= PLANE_TOL * nn * dd &&
+                      fabs(num) <= PLANE_TOL * nn * sqrt(dot3(qs, qs));
+        if (inplane) {
+            *planar = 1;
+            if (w) {
+                if (dot3(n, w) >= 0.0) empty = 1;
+                continue;
+            }
+        }
+        if (den > 0.0) {
+            double t = num / den;
+            if (t < h) h = t;
+        } else if (den < 0.0) {
+            double t = num / den;
+            if (t > l) l = t;
+        } else if (num < 0.0) {
+            empty = 1;
+        }
+    }
+    if (empty) { *lo = 1.0; *hi = 0.0; return 1; }
+    *lo = l;
+    *hi = h;
+    return 1;
+}
+
+static void load_tet(const double *verts, const int32_t *tets, int64_t i, double v[4][3]) {
+    for (int k = 0; k < 4; ++k) {
+        const double *p = verts + 3 * (int64_t)tets[4 * i + k];
+        v[k][0] = p[0]; v[k][1] = p[1]; v[k][2] = p[2];
+    }
+}
+
+/* a_ij for one (ray, tet) pair; also returns the parameter interval. */
+double oracle_tet_chord(const double v_flat[12], const double S[3], const double P[3],
+                        double *t_lo, double *t_hi) {
+    double v[4][3], d[3], lo, hi;
+    int planar;
+    memcpy(v, v_flat, sizeof(v));
+    sub3(P, S, d);
+    if (!tet_clip(v, S, d, NULL, &lo, &hi, &planar)) { *t_lo = 0; *t_hi = 0; return 0.0; }
+    *t_lo = lo;
+    *t_hi = hi;
+    return hi > lo ? (hi - lo) * sqrt(dot3(d, d)) : 0.0;
+}
+
+/* Neumaier compensated accumulator */
+typedef struct { double s, c; } nsum;
+static void nadd(nsum *a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+static double nval(const nsum *a) { return a->s + a->c; }
+
+/* ---------------------------------------------------------------- threading */
+
+typedef struct {
+    const double *verts;
+    const int32_t *tets;
+    int64_t nt;
+    int C;
+    /* rays: explicit (S, P arrays) or cone-beam (geom + optional index list) */
+    const double *S, *P;
+    const double *W;      /* per-ray side vectors for one-sided limits, or NULL */
+    const cone_geom *geom;
+    const int64_t *ray_idx;
+    int64_t ray_begin, ray_end;
+    /* forward */
+    const double *mu;
+    double *out;
+    /* backward */
+    const double *y;
+    double *acc;          /* per-thread [nt * C] (nsum pairs when compensated) */
+    nsum *nacc;
+    /* backward over a tet subset, all rays */
+    const int64_t *tet_idx;
+    int64_t tet_begin, tet_end, nrays_all;
+    /* trace */
+    int64_t max_visits;
+    int32_t *tr_tet;
+    double *tr_lo, *tr_hi;
+    int64_t *tr_count;
+    double *tr_margin;
+    int32_t *tr_planar;
+} job;
+
+static void get_ray(const job *jb, int64_t k, double S[3], double P[3]) {
+    if (jb->geom) {
+        int64_t j = jb->ray_idx ? jb->ray_idx[k] : k;
+        cone_ray(jb->geom, j, S, P);
+    } else {
+        memcpy(S, jb->S + 3 * k, 3 * sizeof(double));
+        memcpy(P, jb->P + 3 * k, 3 * sizeof(double));
+    }
+}
+
+static int run_threads(void *(*fn)(void *), job *jobs, int nthreads) {
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    if (!th) return -1;
+    for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, fn, &jobs[i]);
+    for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+    free(th);
+    return 0;
+}
+
+static void split(int64_t n, int nthreads, int i, int64_t *b, int64_t *e) {
+    *b = n * i / nthreads;
+    *e = n * (i + 1) / nthreads;
+}
+
+/* ------------------------------------------------------------ Eq. 2 forward */
+
+static void *fwd_worker(void *arg) {
+    job *jb = (job *)arg;
+    nsum acc[16];
+    for (int64_t k = jb->ray_begin; k < jb->ray_end; ++k) {
+        double S[3], P[3], d[3];
+        get_ray(jb, k, S, P);
+        sub3(P, S, d);
+        const double *w = jb->W ? jb->W + 3 * k : NULL;
+        double len = sqrt(dot3(d, d));
+        for (int c = 0; c < jb->C; ++c) acc[c].s = acc[c].c = 0.0;
+        for (int64_t i = 0; i < jb->nt; ++i) {
+            double v[4][3], lo, hi;
+            int planar;
+            load_tet(jb->verts, jb->tets, i, v);
+            if (!tet_clip(v, S, d, w, &lo, &hi, &planar) || !(hi > lo)) continue;
+            double a = (hi - lo) * len;
+            for (int c = 0; c < jb->C; ++c) nadd(&acc[c], a * jb->mu[i * jb->C + c]);
+        }
+        for (int c = 0; c < jb->C; ++c) jb->out[k * jb->C + c] = nval(&acc[c]);
+    }
+    return NULL;
+}
+
+static int forward_common(job *proto, int64_t nrays, int nthreads) {
+    if (proto->C < 1 || proto->C > 16) return -2;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nrays && nrays > 0) nthreads = (int)nrays;
+    job *jobs = (job *)calloc((size_t)nthreads, sizeof(job));
+    if (!jobs) return -1;
+    for (int i = 0; i < nthreads; ++i) {
+        jobs[i] = *proto;
+        split(nrays, nthreads, i, &jobs[i].ray_begin, &jobs[i].ray_end);
+    }
+    int rc = run_threads(fwd_worker, jobs, nthreads);
+    free(jobs);
+    return rc;
+}
+
+/* b = A mu for explicit rays (S, P: [nrays][3]); mu: [nt][C]; out: [nrays][C].
+ * W: NULL, or per-ray side directions [nrays][3] selecting one-sided limits for
+ * rays that lie in a face plane (see tet_clip). */
+int oracle_forward_rays(const double *verts, int64_t nv, const int32_t *tets, int64_t nt,
+                        const double *mu, int C, const double *S, const double *P,
+                        const double *W, int64_t nrays, double *out, int nthreads) {
+    (void)nv;
+    job p;
+    memset(&p, 0, sizeof(p));
+    p.verts = verts; p.tets = tets; p.nt = nt; p.C = C; p.S = S; p.P = P; p.W = W;
+    p.mu = mu; p.out = out;
+    return forward_common(&p, nrays, nthreads);
+}
+
+/* b = A mu for cone-beam rays; ray_idx selects rays (NULL: all na*nv*nu, in order). */
+int oracle_forward_cone(const double *verts, int64_t nv_, const int32_t *tets, int64_t nt,
+                        const double *mu, int C, double dso, double dsd, int64_t nu, int64_t nv,
+                        double du, double dv, const double *angles, int64_t na,
+                        const int64_t *ray_idx, int64_t nsel, double *out, int nthreads) {
+    (void)nv_;
+    cone_geom g = {dso, dsd, du, dv, nu, nv, na, angles};
+    job p;
+    memset(&p, 0, sizeof(p));
+    p.verts = verts; p.tets = tets; p.nt = nt; p.C = C; p.geom = &g; p.ray_idx = ray_idx;
+    p.mu = mu; p.out = out;
+    int64_t n = ray_idx ? nsel : na * nv * nu;
+    return forward_common(&p, n, nthreads);
+}
+
+/* ----------------------------------------------------------- Eq. 3 backward */
+
+static void *bwd_rays_worker(void *arg) {
+    job *jb = (job *)arg;
+    for (int64_t k = jb->ray_begin; k < jb->ray_end; ++k) {
+        double S[3], P[3], d[3];
+        get_ray(jb, k, S, P);
+        sub3(P, S, d);
+        const double *w = jb->W ? jb->W + 3 * k : NULL;
+        double len = sqrt(dot3(d, d));
+        for (int64_t i = 0; i < jb->nt; ++i) {
+            double v[4][3], lo, hi;
+            int planar;
+            load_tet(jb->verts, jb->tets, i, v);
+            if (!tet_clip(v, S, d, w, &lo, &hi, &planar) || !(hi > lo)) continue;
+            double a = (hi - lo) * len;
+            for (int c = 0; c < jb->C; ++c) nadd(&jb->nacc[i * jb->C + c], a * jb->y[k * jb->C + c]);
+        }
+    }
+    return NULL;
+}
+
+static int backward_rays_common(job *proto, int64_t nrays, double *out, int nthreads) {
+    if (proto->C < 1 || proto->C > 16) return -2;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nrays && nrays > 0) nthreads = (int)nrays;
+    int64_t m = proto->nt * proto->C;
+    job *jobs = (job *)calloc((size_t)nthreads, sizeof(job));
+    nsum *bufs = (nsum *)calloc((size_t)(m * nthreads), sizeof(nsum));
+    if (!jobs || !bufs) { free(jobs); free(bufs); return -1; }
+    for (int i = 0; i < nthreads; ++i) {
+        jobs[i] = *proto;
+        jobs[i].nacc = bufs + (int64_t)i * m;
+        split(nrays, nthreads, i, &jobs[i].ray_begin, &jobs[i].ray_end);
+    }
+    int rc = run_threads(bwd_rays_worker, jobs, nthreads);
+    for (int64_t q = 0; q < m; ++q) {
+        nsum s = {0.0, 0.0};
+        for (int i = 0; i < nthreads; ++i) {
+            nadd(&s, bufs[(int64_t)i * m + q].s);
+            nadd(&s, bufs[(int64_t)i * m + q].c);
+        }
+        out[q] = nval(&s);
+    }
+    free(jobs);
+    free(bufs);
+    return rc;
+}
+
+/* x = A^T y for explicit rays; y: [nrays][C]; out: [nt][C] (overwritten); W as above. */
+int oracle_backward_rays(const double *verts, int64_t nv, const int32_t *tets, int64_t nt,
+                         const double *y, int C, const double *S, const double *P,
+                         const double *W, int64_t nrays, double *out, int nthreads) {
+    (void)nv;
+    job p;
+    memset(&p, 0, sizeof(p));
+    p.verts = verts; p.tets = tets; p.nt = nt; p.C = C; p.S = S; p.P = P; p.W = W; p.y = y;
+    return backward_rays_common(&p, nrays, out, nthreads);
+}
+
+/* x = A^T y for all cone-beam rays; y: [na][nv][nu][C]; out: [nt][C]. */
+int oracle_backward_cone(const double *verts, int64_t nv_, const int32_t *tets, int64_t nt,
+                         const double *y, int C, double dso, double dsd, int64_t nu, int64_t nv,
+                         double du, double dv, const double *angles, int64_t na, double *out,
+                         int nthreads) {
+    (void)nv_;
+    cone_geom g = {dso, dsd, du, dv, nu, nv, na, angles};
+    job p;
+    memset(&p, 0, sizeof(p));
+    p.verts = verts; p.tets = tets; p.nt = nt; p.C = C; p.geom = &g; p.y = y;
+    return backward_rays_common(&p, na * nv * nu, out, nthreads);
+}
+
+/* x_i = sum_j a_ij y_j for a subset of tets, over all cone-beam rays. */
+static void *bwd_subset_worker(void *arg) {
+    job *jb = (job *)arg;
+    for (int64_t q = jb->tet_begin; q < jb->tet_end; ++q) {
+        int64_t i = jb->tet_idx[q];
+        double v[4][3];
+        load_tet(jb->verts, jb->tets, i, v);
+        nsum acc[16];
+        for (int c = 0; c < jb->C; ++c) acc[c].s = acc[c].c = 0.0;
+        for (int64_t j = 0; j < jb->nrays_all; ++j) {
+            double S[3], P[3], d[3], lo, hi;
+            int planar;
+            cone_ray(jb->geom, j, S, P);
+            sub3(P, S, d);
+            if (!tet_clip(v, S, d, NULL, &lo, &hi, &planar) || !(hi > lo)) continue;
+            double a = (hi - lo) * sqrt(dot3(d, d));
+            for (int c = 0; c < jb->C; ++c) nadd(&acc[c], a * jb->y[j * jb->C + c]);
+        }
+        for (int c = 0; c < jb->C; ++c) jb->out[q * jb->C + c] = nval(&acc[c]);
+    }
+    return NULL;
+}
+
+int oracle_backward_cone_subset(const double *verts, int64_t nv_, const int32_t *tets, int64_t nt,
+                                const double *y, int C, double dso, double dsd, int64_t nu,
+                                int64_t nv, double du, double dv, const double *angles, int64_t na,
+                                const int64_t *tet_idx, int64_t nsel, double *out, int nthreads) {
+    (void)nv_;
+    (void)nt;
+    if (C < 1 || C > 16) return -2;
+    cone_geom g = {dso, dsd, du, dv, nu, nv, na, angles};
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nsel && nsel > 0) nthreads = (int)nsel;
+    job *jobs = (job *)calloc((size_t)nthreads, sizeof(job));
+    if (!jobs) return -1;
+    for (int i = 0; i < nthreads; ++i) {
+        memset(&jobs[i], 0, sizeof(job));
+        jobs[i].verts = verts; jobs[i].tets = tets; jobs[i].C = C; jobs[i].geom = &g;
+        jobs[i].y = y; jobs[i].out = out; jobs[i].tet_idx = tet_idx;
+        jobs[i].nrays_all = na * nv * nu;
+        split(nsel, nthreads, i, &jobs[i].tet_begin, &jobs[i].tet_end);
+    }
+    int rc = run_threads(bwd_subset_worker, jobs, nthreads);
+    free(jobs);
+    return rc;
+}
+
+/* ---------------------------------------------------------------- traces */
+
+typedef struct { double lo, hi; int32_t tet; } visit;
+
+static int visit_cmp(const void *a, const void *b) {
+    const visit *x = (const visit *)a, *y = (const visit *)b;
+    if (x->lo < y->lo) return -1;
+    if (x->lo > y->lo) return 1;
+    if (x->hi < y->hi) return -1;
+    if (x->hi > y->hi) return 1;
+    return (x->tet > y->tet) - (x->tet < y->tet);
+}
+
+static void *trace_worker(void *arg) {
+    job *jb = (job *)arg;
+    int64_t cap = 64;
+    visit *vs = (visit *)malloc(sizeof(visit) * (size_t)cap);
+    for (int64_t k = jb->ray_begin; k < jb->ray_end; ++k) {
+        double S[3], P[3], d[3];
+        get_ray(jb, k, S, P);
+        sub3(P, S, d);
+        const double *w = jb->W ? jb->W + 3 * k : NULL;
+        double len = sqrt(dot3(d, d));
+        int64_t n = 0;
+        double margin = INFINITY;
+        int planar_any = 0;
+        for (int64_t i = 0; i < jb->nt; ++i) {
+            double v[4][3], lo, hi;
+            int planar;
+            load_tet(jb->verts, jb->tets, i, v);
+            if (!tet_clip(v, S, d, w, &lo, &hi, &planar)) continue;
+            if (planar) planar_any = 1;
+            double m = fabs(hi - lo) * len;
+            if (m < margin) margin = m;
+            if (!(hi > lo)) continue;
+            if (n == cap) {
+                cap *= 2;
+                vs = (visit *)realloc(vs, sizeof(visit) * (size_t)cap);
+            }
+            vs[n].lo = lo; vs[n].hi = hi; vs[n].tet = (int32_t)i;
+            ++n;
+        }
+        qsort(vs, (size_t)n, sizeof(visit), visit_cmp);
+        int64_t m = n < jb->max_visits ? n : jb->max_visits;
+        for (int64_t q = 0; q < m; ++q) {
+            jb->tr_tet[k * jb->max_visits + q] = vs[q].tet;
+            jb->tr_lo[k * jb->max_visits + q] = vs[q].lo;
+            jb->tr_hi[k * jb->max_visits + q] = vs[q].hi;
+        }
+        jb->tr_count[k] = n;
+        jb->tr_margin[k] = margin;
+        jb->tr_planar[k] = planar_any;
+    }
+    free(vs);
+    return NULL;
+}
+
+/*
+ * Row j of A for explicit rays: the tets with a_ij > 0 sorted by entry
+ * parameter, with their parameter intervals.  out_count[j] is the full count
+ * (entries beyond max_visits are dropped).  out_margin[j] is the smallest
+ * |hi - lo| * |P - S| over all tets whose clipped interval is near-empty or
+ * non-empty: a small margin flags a ray that grazes an edge or vertex.
+ * out_planar[j] is 1 when the ray runs exactly inside some face plane.
+ */
+int oracle_trace_rays(const double *verts, int64_t nv, const int32_t *tets, int64_t nt,
+                      const double *S, const double *P, int64_t nrays, int64_t max_visits,
+                      int32_t *out_tet, double *out_lo, double *out_hi, int64_t *out_count,
+                      double *out_margin, int32_t *out_planar, int nthreads) {
+    (void)nv;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nrays && nrays > 0) nthreads = (int)nrays;
+    job *jobs = (job *)calloc((size_t)nthreads, sizeof(job));
+    if (!jobs) return -1;
+    for (int i = 0; i < nthreads; ++i) {
+        memset(&jobs[i], 0, sizeof(job));
+        jobs[i].verts = verts; jobs[i].tets = tets; jobs[i].nt = nt; jobs[i].S = S; jobs[i].P = P;
+        jobs[i].max_visits = max_visits; jobs[i].tr_tet = out_tet; jobs[i].tr_lo = out_lo;
+        jobs[i].tr_hi = out_hi; jobs[i].tr_count = out_count; jobs[i].tr_margin = out_margin;
+        jobs[i].tr_planar = out_planar;
+        split(nrays, nthreads, i, &jobs[i].ray_begin, &jobs[i].ray_end);
+    }
+    int rc = run_threads(trace_worker, jobs, nthreads);
+    free(jobs);
+    return rc;
+}
