@@ -1,0 +1,229 @@
+/*
+ * tetproj.h -- C ABI of the GB300 tetrahedral-mesh CT projectors.
+ *
+ * The library computes the two operators every CT reconstruction algorithm
+ * needs on a tetrahedral image basis (Sec. II-A of Biguri et al., "Numerically
+ * robust tetrahedron-based tomographic forward and backward projectors on
+ * parallel architectures"):
+ *
+ *   Eq. 1   A x = b + e,  a_ij = length of the intersection of ray j and tet i
+ *   Eq. 2   forward projection   b_j = sum_i a_ij mu_i
+ *   Eq. 3   backprojection       x_i = sum_j a_ij y_j     (the exact adjoint A^T)
+ *
+ * A is never stored: each call walks every ray through the mesh, tet to tet
+ * across shared faces (Alg. 2), starting from the boundary face where the ray
+ * enters (Sec. II-E, here found through a bounding-volume hierarchy over the
+ * boundary faces).  Exit faces are decided by exact-sign orientation
+ * predicates with a symbolic tie-break, so no ray can leak or loop.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ * - A ray is the half-line X(t) = S + t (P - S), t >= 0, from a source S through
+ *   a point P (a detector pixel centre).  S must lie outside the mesh.
+ * - Cone-beam geometry (circular orbit about z, flat detector): for angle theta
+ *   S = (dso cos, dso sin, 0), detector centre C = S - dsd (cos, sin, 0),
+ *   u axis U = (-sin, cos, 0), v axis V = (0, 0, 1), pixel centre
+ *   P = C + u U + v V with u = (iu - (nu-1)/2) du, v = (iv - (nv-1)/2) dv.
+ *   Ray index j = (a * nv + iv) * nu + iu.
+ * - Layouts: mu / mu_out are [nt][C] in the user's tet order; projections are
+ *   [nangles][nv][nu][C]; explicit rays take src/dst as [n][3] FP64.
+ * - Element type: float for TETPROJ_FILTERED, double for TETPROJ_PLAIN_FP64.
+ *   C (channels, several attenuation maps sharing one traversal) is 1 or 4.
+ * - Every data pointer passed to forward/backward/trace is a DEVICE pointer
+ *   owned by the caller.  Host pointers appear only in the *_create calls and
+ *   in the *_host helpers.  `stream` is a cudaStream_t (NULL = legacy stream).
+ * - Compute calls are asynchronous and ordered on `stream`; they never
+ *   synchronise and never allocate, except that the first forward/backward on a
+ *   mesh with a given (precision, channels) allocates the mesh's workspace
+ *   (tetproj_mesh_reserve does that up front, e.g. before CUDA-graph capture).
+ *   Argument errors are returned immediately.  Errors met on the device (a walk
+ *   that exceeds max_steps, a source inside the mesh) are recorded in the
+ *   mesh's counters and reported by tetproj_mesh_stats_read.
+ * - Calls on the same mesh share its workspace and counters: issue them on one
+ *   stream (or order them with events).
+ */
+#ifndef TETPROJ_H
+#define TETPROJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tetproj_status;
+
+#define TETPROJ_OK 0
+#define TETPROJ_ERR_ARG 1             /* invalid argument (NULL, size, option)      */
+#define TETPROJ_ERR_INDEX 2           /* vertex index out of range or repeated        */
+#define TETPROJ_ERR_DEGENERATE_TET 3  /* zero-volume tet (exact orientation = 0)      */
+#define TETPROJ_ERR_NONMANIFOLD 4     /* face shared by >2 tets, overlapping tets     */
+#define TETPROJ_ERR_NONCONVEX 5       /* boundary surface not convex (Sec. II-D)      */
+#define TETPROJ_ERR_CUDA 6            /* a CUDA runtime call failed                   */
+#define TETPROJ_ERR_OOM 7             /* device or host allocation failed             */
+#define TETPROJ_ERR_RAY_LIMIT 8       /* a walk exceeded max_steps (device-side)      */
+#define TETPROJ_ERR_TIMEOUT 9         /* a bounded device wait gave up (device-side)  */
+#define TETPROJ_ERR_SOURCE_INSIDE 10  /* a ray source lies inside the mesh (device)   */
+#define TETPROJ_ERR_TOO_LARGE 11      /* mesh or problem exceeds a documented limit   */
+
+/* precision modes */
+#define TETPROJ_FILTERED 0   /* FP32 data; FP32 predicates with a forward error bound,
+                                FP64 / exact / symbolic fallback; Kahan FP32 sums     */
+#define TETPROJ_PLAIN_FP64 1 /* FP64 data, predicates (FP64 filter + exact), sums, atomics */
+
+/* pixel order inside a ray tile */
+#define TETPROJ_ORDER_ROW 0
+#define TETPROJ_ORDER_MORTON 1
+
+/* backprojection scatter */
+#define TETPROJ_SCATTER_ATOMIC 0  /* one atomic add per segment                     */
+#define TETPROJ_SCATTER_WARP 1    /* lanes of a warp on the same tet merge first     */
+
+typedef struct tetproj_mesh tetproj_mesh;
+typedef struct tetproj_geometry tetproj_geometry;
+
+typedef struct tetproj_options {
+    int32_t precision; /* TETPROJ_FILTERED (default) or TETPROJ_PLAIN_FP64            */
+    int32_t channels;  /* C: 1 (default) or 4                                          */
+    int32_t tile_u;    /* ray tile width in pixels: 1..32, power of two (default 8)    */
+    int32_t tile_v;    /* ray tile height: tile_u*tile_v in {32,64,128,256,512}        */
+    int32_t order;     /* TETPROJ_ORDER_MORTON (default) or TETPROJ_ORDER_ROW          */
+    int32_t scatter;   /* TETPROJ_SCATTER_ATOMIC (default) or TETPROJ_SCATTER_WARP     */
+    int32_t max_steps; /* walk step limit per ray; 0 = 64 + 16*ceil(nt^(1/3))          */
+    int32_t flags;     /* reserved, must be 0                                          */
+} tetproj_options;
+
+typedef struct tetproj_stats {
+    int64_t rays;        /* rays launched                                              */
+    int64_t hits;        /* rays that entered the mesh                                 */
+    int64_t segments;    /* tet visits (walk steps), zero-length visits included       */
+    int64_t fp64_filter; /* edge predicates the FP32 filter could not decide           */
+    int64_t exact;       /* ... that the FP64 filter could not decide either           */
+    int64_t sos;         /* ... that were exactly zero (symbolic tie-break used)        */
+    int64_t bvh_nodes;   /* BVH boxes tested by entry searches                         */
+    int64_t bvh_faces;   /* boundary faces tested by entry searches                    */
+    int32_t error;       /* first device-side error code, 0 if none                    */
+    int32_t error_count; /* rays that hit a device-side error                          */
+} tetproj_stats;
+
+typedef struct tetproj_mesh_info {
+    int64_t nt, nv;          /* tets, vertices                                         */
+    int64_t nboundary;       /* boundary faces                                         */
+    int64_t nbvh_nodes;      /* BVH nodes                                              */
+    int64_t nflipped;        /* input tets that were negatively oriented (re-ordered)  */
+    int64_t device_bytes;    /* device memory held by the mesh (records, BVH, workspace) */
+    double bbox[6];          /* xmin, ymin, zmin, xmax, ymax, zmax                     */
+} tetproj_mesh_info;
+
+/* Fills *opt with the defaults listed above. */
+void tetproj_default_options(tetproj_options *opt);
+
+/* Static description of a status code (never NULL). */
+const char *tetproj_status_string(tetproj_status s);
+
+/* ---------------------------------------------------------------- meshes --
+ * tetproj_mesh_create: builds the device mesh from HOST arrays (Sec. II-B, the
+ * element/neighbour graph, and Sec. II-E, the boundary list and search tree).
+ *   vertices: [nv][3] FP64;  tets: [nt][4] int32 vertex indices (any orientation).
+ * Copies its inputs; the caller may free them on return.  Validates the mesh
+ * (indices, zero-volume tets, faces shared by more than two tets or by two tets
+ * on the same side, convexity of the boundary), re-orders each tet's vertices
+ * to positive orientation, builds face adjacency, renumbers tets along a 3-D
+ * Hilbert curve of their centroids, builds the boundary-face BVH and uploads
+ * everything with synchronous copies on the current device.  Limits:
+ * nt < 2^29, nv < 2^31, |coordinates| < 1e9.  On error *out is NULL. */
+tetproj_status tetproj_mesh_create(const double *vertices, int64_t nv, const int32_t *tets,
+                                   int64_t nt, tetproj_mesh **out);
+
+/* Frees the mesh and its device memory (synchronises the device first). */
+tetproj_status tetproj_mesh_destroy(tetproj_mesh *mesh);
+
+tetproj_status tetproj_mesh_get_info(const tetproj_mesh *mesh, tetproj_mesh_info *out);
+
+/* Allocates the mesh's workspace for (precision, channels) now instead of on
+ * the first compute call.  Synchronous. */
+tetproj_status tetproj_mesh_reserve(tetproj_mesh *mesh, int32_t precision, int32_t channels);
+
+/* Host-only topology of a mesh, in the user's tet order (no device needed):
+ * adj_out [nt][4]: tet across the face opposite local vertex k of the INPUT
+ * tet, or -1 on the boundary; *nboundary_out: boundary face count;
+ * *nflipped_out: negatively oriented input tets.  Same validation as create. */
+tetproj_status tetproj_mesh_topology_host(const double *vertices, int64_t nv,
+                                          const int32_t *tets, int64_t nt, int32_t *adj_out,
+                                          int64_t *nboundary_out, int64_t *nflipped_out);
+
+/* Zeroes / reads the mesh's device counters (read synchronises `stream`). */
+tetproj_status tetproj_mesh_stats_reset(tetproj_mesh *mesh, void *stream);
+tetproj_status tetproj_mesh_stats_read(tetproj_mesh *mesh, void *stream, tetproj_stats *out);
+
+/* -------------------------------------------------------------- geometry --
+ * Circular cone-beam scan (Alg. 2 launches one ray per detector pixel; the
+ * paper's experiments use equidistant angles over a circular trajectory).
+ *   dso: source to rotation axis; dsd: source to detector (> dso);
+ *   nu, nv: detector pixels; du, dv: pixel pitch; angles: HOST [nangles] rad.
+ * Per-angle frames are computed on the host in FP64 and uploaded. */
+tetproj_status tetproj_geometry_create(double dso, double dsd, int32_t nu, int32_t nv, double du,
+                                       double dv, const double *angles, int32_t nangles,
+                                       tetproj_geometry **out);
+tetproj_status tetproj_geometry_destroy(tetproj_geometry *geo);
+
+/* Writes the endpoints (S, P) of the rays with the given indices (device
+ * int64 [n]; NULL = rays 0..n-1) into device src/dst [n][3] FP64. */
+tetproj_status tetproj_geometry_rays(const tetproj_geometry *geo, const int64_t *ray_idx,
+                                     int64_t n, double *src, double *dst, void *stream);
+
+/* ------------------------------------------------------------- operators --
+ * tetproj_forward (Eq. 2): proj[a][iv][iu][c] = sum_i a_ij mu[i][c].
+ *   mu: device [nt][C]; proj: device [nangles][nv][nu][C] (overwritten).
+ * tetproj_backward (Eq. 3): mu_out[i][c] = sum_j a_ij proj[j][c] (overwritten).
+ * opt may be NULL (defaults).  Both are exact adjoints of each other up to
+ * floating-point rounding. */
+tetproj_status tetproj_forward(const tetproj_mesh *mesh, const tetproj_geometry *geo,
+                               const void *mu, void *proj, const tetproj_options *opt,
+                               void *stream);
+tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry *geo,
+                                const void *proj, void *mu_out, const tetproj_options *opt,
+                                void *stream);
+
+/* The same operators for explicit rays src[j] -> dst[j] (device [n][3] FP64):
+ * out[j][c] = sum_i a_ij mu[i][c];  mu_out[i][c] = sum_j a_ij y[j][c]. */
+tetproj_status tetproj_forward_rays(const tetproj_mesh *mesh, const double *src,
+                                    const double *dst, int64_t nrays, const void *mu, void *out,
+                                    const tetproj_options *opt, void *stream);
+tetproj_status tetproj_backward_rays(const tetproj_mesh *mesh, const double *src,
+                                     const double *dst, int64_t nrays, const void *y,
+                                     void *mu_out, const tetproj_options *opt, void *stream);
+
+/* Row j of A for explicit rays: the tets visited, in order, with their chord
+ * lengths a_ij (zero-length visits at edges/vertices included).
+ *   out_tet: device int32 [n][max_visits] user tet ids; out_len: device FP64
+ *   [n][max_visits]; out_count: device int32 [n] visits (may exceed max_visits;
+ *   entries past max_visits are not written).  opt->precision selects the walk. */
+tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, const double *dst,
+                                  int64_t nrays, int32_t max_visits, int32_t *out_tet,
+                                  double *out_len, int32_t *out_count,
+                                  const tetproj_options *opt, void *stream);
+
+/* ------------------------------------------------------------ predicates --
+ * Sign of the side product det[P - S, p - S, q - S] of the line S->P and the
+ * edge p->q (the test behind each of the four triangle tests of Sec. II-C),
+ * evaluated by the library's cascade: FP32 with a forward error bound, then
+ * FP64 with an error bound, then exact expansion arithmetic, then the
+ * symbolic perturbation of the line (S + (e, e^2, e^4), P + (e^8, e^16, e^32),
+ * e -> 0+) when the exact value is zero.  sign[k] in {-1, +1} (0 only if
+ * p == q); stage[k]: 0 FP32, 1 FP64, 2 exact, 3 symbolic.
+ * _host: host arrays, runs on the CPU.  _device: device arrays, on `stream`. */
+tetproj_status tetproj_side_host(const double *S, const double *P, const double *p,
+                                 const double *q, int64_t n, int8_t *sign, int8_t *stage);
+tetproj_status tetproj_side_device(const double *S, const double *P, const double *p,
+                                   const double *q, int64_t n, int8_t *sign, int8_t *stage,
+                                   void *stream);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t tetproj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TETPROJ_H */

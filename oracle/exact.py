@@ -241,3 +241,28 @@ def kuhn_crossings(n: int, S, P):
                 if t0 < t < t1:
                     ts.add(t)
     return 1 + len(ts), False
+
+
+def _int_scale(vals):
+    """Exact integers m_k with vals[k] = m_k * 2^E for a common E (all finite doubles)."""
+    import math
+    parts = []
+    for v in vals:
+        m, e = math.frexp(v)  # v = m * 2^e, 0.5 <= |m| < 1
+        parts.append((int(m * (1 << 53)), e - 53))
+    E = min(e for _, e in parts)
+    return [m << (e - E) for m, e in parts]
+
+
+def side_sign_int(S, P, p, q) -> int:
+    """Exact sign of det[P - S, p - S, q - S] with Python integers (fast path
+    for large test batches; same value as side())."""
+    vals = [float(x) for x in (*S, *P, *p, *q)]
+    I = _int_scale(vals)
+    s, Pp, pp, qq = I[0:3], I[3:6], I[6:9], I[9:12]
+    a = [Pp[i] - s[i] for i in range(3)]
+    b = [pp[i] - s[i] for i in range(3)]
+    c = [qq[i] - s[i] for i in range(3)]
+    det = (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
+           + a[2] * (b[0] * c[1] - b[1] * c[0]))
+    return (det > 0) - (det < 0)

@@ -1,0 +1,348 @@
+"""GB300-native tetrahedral-mesh CT projectors (thin Python binding).
+
+The compute lives in ``libtetproj.so`` (CUDA, sm_103a) behind the C ABI of
+``include/tetproj.h``.  This module only marshals arguments: torch tensors
+provide device memory and the current CUDA stream.  There is no CPU
+fallback: every call raises if the library or a CUDA device is missing.
+
+Operators (Biguri et al., Sec. II-A):
+    forward   b_j = sum_i a_ij mu_i      (Eq. 2)
+    backward  x_i = sum_j a_ij y_j       (Eq. 3, the exact adjoint)
+with a_ij the length of ray j inside tet i (Eq. 1).  float32 tensors select
+the filtered-precision path, float64 tensors the plain FP64 path.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (FILTERED, ORDER_MORTON, ORDER_ROW, PLAIN_FP64, SCATTER_ATOMIC, SCATTER_WARP,
+                   Options, TetprojError, check)
+
+__all__ = ["Mesh", "Geometry", "forward", "backward", "forward_rays", "backward_rays",
+           "trace_rays", "side_signs_host", "side_signs_device", "TetProject", "make_options",
+           "FILTERED", "PLAIN_FP64", "ORDER_ROW", "ORDER_MORTON", "SCATTER_ATOMIC",
+           "SCATTER_WARP", "TetprojError", "library_path"]
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_options(precision=FILTERED, channels=1, tile=(8, 8), order=ORDER_MORTON,
+                 scatter=SCATTER_ATOMIC, max_steps=0) -> Options:
+    o = Options()
+    _lib.load().tetproj_default_options(ctypes.byref(o))
+    o.precision = precision
+    o.channels = channels
+    o.tile_u, o.tile_v = tile
+    o.order = order
+    o.scatter = scatter
+    o.max_steps = max_steps
+    return o
+
+
+class Mesh:
+    """A convex tetrahedral mesh uploaded to the current CUDA device.
+
+    vertices: [nv, 3] float64; tets: [nt, 4] int vertex indices (any
+    orientation).  Validation, adjacency, Hilbert renumbering and the boundary
+    BVH are built by ``tetproj_mesh_create``."""
+
+    def __init__(self, vertices, tets):
+        L = _lib.load()
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        t = np.ascontiguousarray(tets, dtype=np.int32)
+        if v.ndim != 2 or v.shape[1] != 3 or t.ndim != 2 or t.shape[1] != 4:
+            raise ValueError("vertices must be [nv,3] and tets [nt,4]")
+        h = ctypes.c_void_p()
+        check(L.tetproj_mesh_create(v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0],
+                                    ctypes.byref(h)), "tetproj_mesh_create")
+        self._h = h
+        self.nt = int(t.shape[0])
+        self.nv = int(v.shape[0])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = _lib.MeshInfo()
+        check(_lib.load().tetproj_mesh_get_info(self._h, ctypes.byref(i)), "tetproj_mesh_get_info")
+        d = {k: getattr(i, k) for k, _ in i._fields_ if k != "bbox"}
+        d["bbox"] = list(i.bbox)
+        return d
+
+    def reserve(self, precision=FILTERED, channels=1):
+        check(_lib.load().tetproj_mesh_reserve(self._h, precision, channels), "tetproj_mesh_reserve")
+
+    def stats_reset(self):
+        check(_lib.load().tetproj_mesh_stats_reset(self._h, _stream()), "tetproj_mesh_stats_reset")
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        check(_lib.load().tetproj_mesh_stats_read(self._h, _stream(), ctypes.byref(s)),
+              "tetproj_mesh_stats_read")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().tetproj_mesh_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def topology_host(vertices, tets):
+    """(adjacency [nt,4] in input order, nboundary, nflipped), computed on the CPU."""
+    L = _lib.load()
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    t = np.ascontiguousarray(tets, dtype=np.int32)
+    adj = np.empty_like(t)
+    nb = ctypes.c_int64()
+    nf = ctypes.c_int64()
+    check(L.tetproj_mesh_topology_host(v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0],
+                                       adj.ctypes.data, ctypes.byref(nb), ctypes.byref(nf)),
+          "tetproj_mesh_topology_host")
+    return adj, nb.value, nf.value
+
+
+class Geometry:
+    """Circular cone-beam scan (see include/tetproj.h for the convention)."""
+
+    def __init__(self, dso, dsd, nu, nv, du, dv, angles):
+        L = _lib.load()
+        a = np.ascontiguousarray(angles, dtype=np.float64)
+        h = ctypes.c_void_p()
+        check(L.tetproj_geometry_create(float(dso), float(dsd), int(nu), int(nv), float(du),
+                                        float(dv), a.ctypes.data, a.size, ctypes.byref(h)),
+              "tetproj_geometry_create")
+        self._h = h
+        self.nu, self.nv, self.nangles = int(nu), int(nv), int(a.size)
+        self.dso, self.dsd, self.du, self.dv = float(dso), float(dsd), float(du), float(dv)
+
+    @classmethod
+    def from_cone(cls, g):
+        """From any object with dso, dsd, nu, nv, du, dv, angles attributes."""
+        return cls(g.dso, g.dsd, g.nu, g.nv, g.du, g.dv, g.angles)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nrays(self) -> int:
+        return self.nangles * self.nv * self.nu
+
+    @property
+    def shape(self):
+        return (self.nangles, self.nv, self.nu)
+
+    def rays(self, idx=None, n=None):
+        """Device (src, dst) [n, 3] float64 for ray indices (device int64 tensor) or 0..n-1."""
+        torch = _torch()
+        if idx is not None:
+            idx = idx.to(device="cuda", dtype=torch.int64).contiguous()
+            n = idx.numel()
+        n = self.nrays if n is None else int(n)
+        src = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        dst = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        check(_lib.load().tetproj_geometry_rays(self._h, None if idx is None else _ptr(idx), n,
+                                                _ptr(src), _ptr(dst), _stream()),
+              "tetproj_geometry_rays")
+        return src, dst
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().tetproj_geometry_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _precision_of(t):
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return FILTERED
+    if t.dtype == torch.float64:
+        return PLAIN_FP64
+    raise TypeError("tensors must be float32 (filtered path) or float64 (plain FP64 path)")
+
+
+def _check_cuda(t, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _opts(precision, channels, options):
+    o = make_options(precision=precision, channels=channels) if options is None else options
+    o.precision = precision
+    o.channels = channels
+    return o
+
+
+def forward(mesh: Mesh, geo: Geometry, mu, out=None, options: Options | None = None):
+    """proj[a, iv, iu(, c)] = sum_i a_ij mu[i(, c)]  (Eq. 2)."""
+    torch = _torch()
+    _check_cuda(mu, "mu")
+    C = 1 if mu.dim() == 1 else mu.shape[1]
+    if mu.shape[0] != mesh.nt:
+        raise ValueError("mu must have nt rows")
+    prec = _precision_of(mu)
+    shape = geo.shape + ((C,) if mu.dim() == 2 else ())
+    if out is None:
+        out = torch.empty(shape, dtype=mu.dtype, device=mu.device)
+    _check_cuda(out, "out")
+    o = _opts(prec, C, options)
+    check(_lib.load().tetproj_forward(mesh.handle, geo.handle, _ptr(mu), _ptr(out),
+                                      ctypes.byref(o), _stream()), "tetproj_forward")
+    return out
+
+
+def backward(mesh: Mesh, geo: Geometry, proj, out=None, options: Options | None = None):
+    """mu_out[i(, c)] = sum_j a_ij proj[j(, c)]  (Eq. 3)."""
+    torch = _torch()
+    _check_cuda(proj, "proj")
+    C = 1 if proj.dim() == 3 else proj.shape[3]
+    if tuple(proj.shape[:3]) != geo.shape:
+        raise ValueError(f"proj must be {geo.shape}(+channels)")
+    prec = _precision_of(proj)
+    if out is None:
+        out = torch.empty((mesh.nt,) + ((C,) if proj.dim() == 4 else ()), dtype=proj.dtype,
+                          device=proj.device)
+    _check_cuda(out, "out")
+    o = _opts(prec, C, options)
+    check(_lib.load().tetproj_backward(mesh.handle, geo.handle, _ptr(proj), _ptr(out),
+                                       ctypes.byref(o), _stream()), "tetproj_backward")
+    return out
+
+
+def forward_rays(mesh: Mesh, src, dst, mu, out=None, options: Options | None = None):
+    torch = _torch()
+    for t, n in ((src, "src"), (dst, "dst"), (mu, "mu")):
+        _check_cuda(t, n)
+    n = src.shape[0]
+    C = 1 if mu.dim() == 1 else mu.shape[1]
+    prec = _precision_of(mu)
+    if out is None:
+        out = torch.empty((n,) + ((C,) if mu.dim() == 2 else ()), dtype=mu.dtype, device=mu.device)
+    o = _opts(prec, C, options)
+    check(_lib.load().tetproj_forward_rays(mesh.handle, _ptr(src), _ptr(dst), n, _ptr(mu),
+                                           _ptr(out), ctypes.byref(o), _stream()),
+          "tetproj_forward_rays")
+    return out
+
+
+def backward_rays(mesh: Mesh, src, dst, y, out=None, options: Options | None = None):
+    torch = _torch()
+    for t, n in ((src, "src"), (dst, "dst"), (y, "y")):
+        _check_cuda(t, n)
+    C = 1 if y.dim() == 1 else y.shape[1]
+    prec = _precision_of(y)
+    if out is None:
+        out = torch.empty((mesh.nt,) + ((C,) if y.dim() == 2 else ()), dtype=y.dtype,
+                          device=y.device)
+    o = _opts(prec, C, options)
+    check(_lib.load().tetproj_backward_rays(mesh.handle, _ptr(src), _ptr(dst), src.shape[0],
+                                            _ptr(y), _ptr(out), ctypes.byref(o), _stream()),
+          "tetproj_backward_rays")
+    return out
+
+
+def trace_rays(mesh: Mesh, src, dst, max_visits=512, precision=FILTERED,
+               options: Options | None = None):
+    """Row j of A per ray: (tets [n, max_visits] user ids, lengths, counts)."""
+    torch = _torch()
+    _check_cuda(src, "src")
+    _check_cuda(dst, "dst")
+    n = src.shape[0]
+    tets = torch.full((n, max_visits), -1, dtype=torch.int32, device="cuda")
+    lens = torch.zeros((n, max_visits), dtype=torch.float64, device="cuda")
+    cnt = torch.zeros((n,), dtype=torch.int32, device="cuda")
+    o = _opts(precision, 1, options)
+    check(_lib.load().tetproj_trace_rays(mesh.handle, _ptr(src), _ptr(dst), n, max_visits,
+                                         _ptr(tets), _ptr(lens), _ptr(cnt), ctypes.byref(o),
+                                         _stream()), "tetproj_trace_rays")
+    return tets, lens, cnt
+
+
+def side_signs_host(S, P, p, q):
+    """(sign, stage) of det[P-S, p-S, q-S] via the library's cascade, on the CPU."""
+    L = _lib.load()
+    arrs = [np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) for x in (S, P, p, q)]
+    n = arrs[0].shape[0]
+    sign = np.zeros(n, np.int8)
+    stage = np.zeros(n, np.int8)
+    check(L.tetproj_side_host(*[a.ctypes.data for a in arrs], n, sign.ctypes.data,
+                              stage.ctypes.data), "tetproj_side_host")
+    return sign, stage
+
+
+def side_signs_device(S, P, p, q):
+    """Same cascade evaluated by a CUDA kernel (inputs: device [n,3] float64)."""
+    torch = _torch()
+    n = S.shape[0]
+    sign = torch.zeros(n, dtype=torch.int8, device="cuda")
+    stage = torch.zeros(n, dtype=torch.int8, device="cuda")
+    check(_lib.load().tetproj_side_device(_ptr(S), _ptr(P), _ptr(p), _ptr(q), n, _ptr(sign),
+                                          _ptr(stage), _stream()), "tetproj_side_device")
+    return sign, stage
+
+
+def _autograd_cls():
+    torch = _torch()
+
+    class _TetProject(torch.autograd.Function):
+        """proj = A mu with backward g -> A^T g (the hand-written backprojection)."""
+
+        @staticmethod
+        def forward(ctx, mu, mesh, geo, options):
+            ctx.mesh, ctx.geo, ctx.options = mesh, geo, options
+            return forward(mesh, geo, mu.contiguous(), options=options)
+
+        @staticmethod
+        def backward(ctx, g):
+            gmu = backward(ctx.mesh, ctx.geo, g.contiguous(), options=ctx.options)
+            return gmu, None, None, None
+
+    return _TetProject
+
+
+_TP = None
+
+
+class TetProject:
+    """``TetProject.apply(mu, mesh, geo, options=None)``: differentiable A mu."""
+
+    @staticmethod
+    def apply(mu, mesh, geo, options=None):
+        global _TP
+        if _TP is None:
+            _TP = _autograd_cls()
+        return _TP.apply(mu, mesh, geo, options)

@@ -1,0 +1,498 @@
+// api.cu -- the extern "C" boundary declared in include/tetproj.h.
+//
+// Host-side glue only: argument checks, ownership of device memory, the
+// user-order <-> Hilbert-order permutations around each walk, and launch
+// configuration.  Every step of the projection itself runs in kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/tetproj.h"
+#include "kernels.cuh"
+#include "mesh_build.h"
+
+using namespace tp;
+
+struct tetproj_mesh {
+    int device = 0;
+    TetRec32 *rec32 = nullptr;
+    TetRec64 *rec64 = nullptr;
+    BvhNode *bvh = nullptr;
+    BFace32 *bfaces = nullptr;
+    int32_t *perm = nullptr;
+    DevCounters *counters = nullptr;
+    int64_t nt = 0, nv = 0, nb = 0, nnodes = 0, nflipped = 0;
+    int32_t root = 0;
+    float radius = 0.f;
+    double bbox[6] = {0, 0, 0, 0, 0, 0};
+    // workspace per [precision][channels==4]: tet-ordered operand / accumulator
+    void *ws[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t ws_bytes[2][2] = {{0, 0}, {0, 0}};
+    int64_t base_bytes = 0;
+};
+
+struct tetproj_geometry {
+    int device = 0;
+    AngleFrame *frames = nullptr;
+    int32_t nu = 0, nv = 0, na = 0;
+    double du = 0, dv = 0, dso = 0, dsd = 0;
+};
+
+static tetproj_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return TETPROJ_OK;
+    if (e == cudaErrorMemoryAllocation) return TETPROJ_ERR_OOM;
+    return TETPROJ_ERR_CUDA;
+}
+#define TP_CUDA(x)                                         \
+    do {                                                   \
+        cudaError_t _e = (x);                              \
+        if (_e != cudaSuccess) return cuda_status(_e);     \
+    } while (0)
+
+template <typename T>
+static cudaError_t upload(T **dst, const std::vector<T> &src) {
+    *dst = nullptr;
+    if (src.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)dst, src.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+extern "C" {
+
+int32_t tetproj_version(void) { return 100; }
+
+void tetproj_default_options(tetproj_options *o) {
+    if (!o) return;
+    o->precision = TETPROJ_FILTERED;
+    o->channels = 1;
+    o->tile_u = 8;
+    o->tile_v = 8;
+    o->order = TETPROJ_ORDER_MORTON;
+    o->scatter = TETPROJ_SCATTER_ATOMIC;
+    o->max_steps = 0;
+    o->flags = 0;
+}
+
+const char *tetproj_status_string(tetproj_status s) {
+    switch (s) {
+        case TETPROJ_OK: return "ok";
+        case TETPROJ_ERR_ARG: return "invalid argument";
+        case TETPROJ_ERR_INDEX: return "vertex index out of range or repeated in a tet";
+        case TETPROJ_ERR_DEGENERATE_TET: return "zero-volume tet";
+        case TETPROJ_ERR_NONMANIFOLD: return "non-manifold mesh (face shared by >2 tets or overlapping tets)";
+        case TETPROJ_ERR_NONCONVEX: return "mesh boundary is not convex (or mesh not connected)";
+        case TETPROJ_ERR_CUDA: return "CUDA runtime error";
+        case TETPROJ_ERR_OOM: return "out of memory";
+        case TETPROJ_ERR_RAY_LIMIT: return "a ray walk exceeded max_steps or met an inconsistent tet";
+        case TETPROJ_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case TETPROJ_ERR_SOURCE_INSIDE: return "a ray source lies inside the mesh";
+        case TETPROJ_ERR_TOO_LARGE: return "size exceeds a documented limit";
+        default: return "unknown status";
+    }
+}
+
+static void mesh_free(tetproj_mesh *m) {
+    if (!m) return;
+    cudaFree(m->rec32);
+    cudaFree(m->rec64);
+    cudaFree(m->bvh);
+    cudaFree(m->bfaces);
+    cudaFree(m->perm);
+    cudaFree(m->counters);
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) cudaFree(m->ws[i][j]);
+    delete m;
+}
+
+tetproj_status tetproj_mesh_create(const double *vertices, int64_t nv, const int32_t *tets,
+                                   int64_t nt, tetproj_mesh **out) {
+    if (!out) return TETPROJ_ERR_ARG;
+    *out = nullptr;
+    HostMesh H;
+    tetproj_status st;
+    try {
+        st = build_host_mesh(vertices, nv, tets, nt, H);
+    } catch (const std::bad_alloc &) {
+        return TETPROJ_ERR_OOM;
+    }
+    if (st != TETPROJ_OK) return st;
+    tetproj_mesh *m = new (std::nothrow) tetproj_mesh();
+    if (!m) return TETPROJ_ERR_OOM;
+    cudaGetDevice(&m->device);
+    m->nt = H.nt;
+    m->nv = H.nv;
+    m->nb = H.nb;
+    m->nnodes = (int64_t)H.bvh.size();
+    m->nflipped = H.nflipped;
+    m->root = H.root;
+    m->radius = H.radius;
+    std::memcpy(m->bbox, H.bbox, sizeof(m->bbox));
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = upload(&m->rec32, H.rec32);
+    if (e == cudaSuccess) e = upload(&m->rec64, H.rec64);
+    if (e == cudaSuccess) e = upload(&m->bvh, H.bvh);
+    if (e == cudaSuccess) e = upload(&m->bfaces, H.bfaces);
+    if (e == cudaSuccess) e = upload(&m->perm, H.perm);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m->counters, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMemset(m->counters, 0, sizeof(DevCounters));
+    if (e != cudaSuccess) {
+        mesh_free(m);
+        return cuda_status(e);
+    }
+    m->base_bytes = (int64_t)(H.rec32.size() * sizeof(TetRec32) + H.rec64.size() * sizeof(TetRec64) +
+                              H.bvh.size() * sizeof(BvhNode) + H.bfaces.size() * sizeof(BFace32) +
+                              H.perm.size() * sizeof(int32_t) + sizeof(DevCounters));
+    *out = m;
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_mesh_destroy(tetproj_mesh *m) {
+    if (!m) return TETPROJ_ERR_ARG;
+    cudaDeviceSynchronize();
+    mesh_free(m);
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_mesh_get_info(const tetproj_mesh *m, tetproj_mesh_info *o) {
+    if (!m || !o) return TETPROJ_ERR_ARG;
+    o->nt = m->nt;
+    o->nv = m->nv;
+    o->nboundary = m->nb;
+    o->nbvh_nodes = m->nnodes;
+    o->nflipped = m->nflipped;
+    int64_t b = m->base_bytes;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) b += m->ws_bytes[i][j];
+    o->device_bytes = b;
+    std::memcpy(o->bbox, m->bbox, sizeof(o->bbox));
+    return TETPROJ_OK;
+}
+
+static tetproj_status ensure_ws(tetproj_mesh *m, int precision, int channels) {
+    int pi = precision == TETPROJ_PLAIN_FP64 ? 1 : 0, ci = channels == 4 ? 1 : 0;
+    if (m->ws[pi][ci]) return TETPROJ_OK;
+    int64_t bytes = m->nt * channels * (pi ? 8 : 4);
+    void *p = nullptr;
+    TP_CUDA(cudaMalloc(&p, (size_t)bytes));
+    m->ws[pi][ci] = p;
+    m->ws_bytes[pi][ci] = bytes;
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_mesh_reserve(tetproj_mesh *m, int32_t precision, int32_t channels) {
+    if (!m || (precision != TETPROJ_FILTERED && precision != TETPROJ_PLAIN_FP64) ||
+        (channels != 1 && channels != 4))
+        return TETPROJ_ERR_ARG;
+    return ensure_ws(m, precision, channels);
+}
+
+tetproj_status tetproj_mesh_topology_host(const double *V, int64_t nv, const int32_t *T,
+                                          int64_t nt, int32_t *adj_out, int64_t *nboundary,
+                                          int64_t *nflipped) {
+    try {
+        return topology_host(V, nv, T, nt, adj_out, nboundary, nflipped);
+    } catch (const std::bad_alloc &) {
+        return TETPROJ_ERR_OOM;
+    }
+}
+
+tetproj_status tetproj_mesh_stats_reset(tetproj_mesh *m, void *stream) {
+    if (!m) return TETPROJ_ERR_ARG;
+    TP_CUDA(cudaMemsetAsync(m->counters, 0, sizeof(DevCounters), (cudaStream_t)stream));
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_mesh_stats_read(tetproj_mesh *m, void *stream, tetproj_stats *o) {
+    if (!m || !o) return TETPROJ_ERR_ARG;
+    DevCounters c;
+    TP_CUDA(cudaMemcpyAsync(&c, m->counters, sizeof(c), cudaMemcpyDeviceToHost,
+                            (cudaStream_t)stream));
+    TP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    o->rays = (int64_t)c.rays;
+    o->hits = (int64_t)c.hits;
+    o->segments = (int64_t)c.segments;
+    o->fp64_filter = (int64_t)c.fp64;
+    o->exact = (int64_t)c.exact;
+    o->sos = (int64_t)c.sos;
+    o->bvh_nodes = (int64_t)c.bvh_nodes;
+    o->bvh_faces = (int64_t)c.bvh_faces;
+    o->error = c.error;
+    o->error_count = c.error_count;
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_geometry_create(double dso, double dsd, int32_t nu, int32_t nv, double du,
+                                       double dv, const double *angles, int32_t nangles,
+                                       tetproj_geometry **out) {
+    if (!out) return TETPROJ_ERR_ARG;
+    *out = nullptr;
+    if (!angles || nu < 1 || nv < 1 || nangles < 1 || !(dso > 0) || !(dsd > dso) || !(du > 0) ||
+        !(dv > 0))
+        return TETPROJ_ERR_ARG;
+    if ((int64_t)nu * nv * nangles >= (int64_t(1) << 40)) return TETPROJ_ERR_TOO_LARGE;
+    std::vector<AngleFrame> F(nangles);
+    for (int a = 0; a < nangles; ++a) {
+        double c = std::cos(angles[a]), s = std::sin(angles[a]);
+        AngleFrame &f = F[a];
+        f.S[0] = dso * c;
+        f.S[1] = dso * s;
+        f.S[2] = 0.0;
+        f.C[0] = f.S[0] - dsd * c;
+        f.C[1] = f.S[1] - dsd * s;
+        f.C[2] = 0.0;
+        f.U[0] = -s;
+        f.U[1] = c;
+        f.U[2] = 0.0;
+        f.V[0] = 0.0;
+        f.V[1] = 0.0;
+        f.V[2] = 1.0;
+    }
+    tetproj_geometry *g = new (std::nothrow) tetproj_geometry();
+    if (!g) return TETPROJ_ERR_OOM;
+    cudaGetDevice(&g->device);
+    g->nu = nu;
+    g->nv = nv;
+    g->na = nangles;
+    g->du = du;
+    g->dv = dv;
+    g->dso = dso;
+    g->dsd = dsd;
+    cudaError_t e = upload(&g->frames, F);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_status(e);
+    }
+    *out = g;
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_geometry_destroy(tetproj_geometry *g) {
+    if (!g) return TETPROJ_ERR_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(g->frames);
+    delete g;
+    return TETPROJ_OK;
+}
+
+static GeoView geo_view(const tetproj_geometry *g) {
+    GeoView v;
+    v.frames = g->frames;
+    v.nu = g->nu;
+    v.nv = g->nv;
+    v.na = g->na;
+    v.du = g->du;
+    v.dv = g->dv;
+    return v;
+}
+
+tetproj_status tetproj_geometry_rays(const tetproj_geometry *g, const int64_t *idx, int64_t n,
+                                     double *src, double *dst, void *stream) {
+    if (!g || n < 0 || (n > 0 && (!src || !dst))) return TETPROJ_ERR_ARG;
+    TP_CUDA(launch_geometry_rays(geo_view(g), idx, n, src, dst, (cudaStream_t)stream));
+    return TETPROJ_OK;
+}
+
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+static tetproj_status check_opts(const tetproj_options *in, tetproj_options &o) {
+    if (in) o = *in;
+    else tetproj_default_options(&o);
+    if (o.precision != TETPROJ_FILTERED && o.precision != TETPROJ_PLAIN_FP64) return TETPROJ_ERR_ARG;
+    if (o.channels != 1 && o.channels != 4) return TETPROJ_ERR_ARG;
+    auto pow2 = [](int v) { return v >= 1 && v <= 32 && (v & (v - 1)) == 0; };
+    if (!pow2(o.tile_u) || !pow2(o.tile_v)) return TETPROJ_ERR_ARG;
+    int t = o.tile_u * o.tile_v;
+    if (t < 32 || t > 256) return TETPROJ_ERR_ARG;
+    if (o.order != TETPROJ_ORDER_ROW && o.order != TETPROJ_ORDER_MORTON) return TETPROJ_ERR_ARG;
+    if (o.scatter != TETPROJ_SCATTER_ATOMIC && o.scatter != TETPROJ_SCATTER_WARP)
+        return TETPROJ_ERR_ARG;
+    if (o.max_steps < 0 || o.flags != 0) return TETPROJ_ERR_ARG;
+    return TETPROJ_OK;
+}
+
+static KParams base_params(const tetproj_mesh *m, const tetproj_options &o) {
+    KParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.m.rec32 = m->rec32;
+    p.m.rec64 = m->rec64;
+    p.m.bvh = m->bvh;
+    p.m.bfaces = m->bfaces;
+    p.m.perm = m->perm;
+    p.m.nt = m->nt;
+    p.m.nb = m->nb;
+    p.m.nnodes = m->nnodes;
+    p.m.root = m->root;
+    p.m.radius = m->radius;
+    p.m.counters = m->counters;
+    p.tu = o.tile_u;
+    p.tv = o.tile_v;
+    p.log_tu = ilog2(o.tile_u);
+    p.log_tv = ilog2(o.tile_v);
+    p.morton = o.order == TETPROJ_ORDER_MORTON;
+    p.scatter = o.scatter;
+    int64_t cb = (int64_t)std::ceil(std::cbrt((double)m->nt));
+    int64_t def = 64 + 16 * cb;
+    int64_t ms = o.max_steps > 0 ? o.max_steps : def;
+    if (ms > m->nt + 1) ms = m->nt + 1;
+    p.max_steps = (int32_t)ms;
+    p.smem_nodes = (int32_t)(m->nnodes < 64 ? m->nnodes : 64);
+    return p;
+}
+
+static void set_cone(KParams &p, const tetproj_geometry *g) {
+    p.src_kind = 0;
+    p.g = geo_view(g);
+    p.tiles_u = (g->nu + p.tu - 1) / p.tu;
+    p.tiles_v = (g->nv + p.tv - 1) / p.tv;
+    p.nrays = (int64_t)g->na * g->nu * g->nv;
+}
+
+static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
+                                  const void *mu, void *out, cudaStream_t s) {
+    tetproj_status st = ensure_ws(m, o.precision, o.channels);
+    if (st != TETPROJ_OK) return st;
+    void *ws = m->ws[o.precision == TETPROJ_PLAIN_FP64][o.channels == 4];
+    int f64 = o.precision == TETPROJ_PLAIN_FP64;
+    TP_CUDA(launch_gather_perm(m->perm, m->nt, o.channels, f64, mu, ws, s));
+    p.in = ws;
+    p.out = out;
+    TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_FWD, s));
+    return TETPROJ_OK;
+}
+
+static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
+                                   const void *y, void *mu_out, cudaStream_t s) {
+    tetproj_status st = ensure_ws(m, o.precision, o.channels);
+    if (st != TETPROJ_OK) return st;
+    void *ws = m->ws[o.precision == TETPROJ_PLAIN_FP64][o.channels == 4];
+    int f64 = o.precision == TETPROJ_PLAIN_FP64;
+    TP_CUDA(cudaMemsetAsync(ws, 0, (size_t)m->ws_bytes[f64][o.channels == 4], s));
+    p.in = y;
+    p.out = ws;
+    TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s));
+    TP_CUDA(launch_scatter_perm(m->perm, m->nt, o.channels, f64, ws, mu_out, s));
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_forward(const tetproj_mesh *mesh, const tetproj_geometry *geo,
+                               const void *mu, void *proj, const tetproj_options *opt,
+                               void *stream) {
+    if (!mesh || !geo || !mu || !proj) return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
+    KParams p = base_params(m, o);
+    set_cone(p, geo);
+    return run_forward(m, p, o, mu, proj, (cudaStream_t)stream);
+}
+
+tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry *geo,
+                                const void *proj, void *mu_out, const tetproj_options *opt,
+                                void *stream) {
+    if (!mesh || !geo || !proj || !mu_out) return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
+    KParams p = base_params(m, o);
+    set_cone(p, geo);
+    return run_backward(m, p, o, proj, mu_out, (cudaStream_t)stream);
+}
+
+tetproj_status tetproj_forward_rays(const tetproj_mesh *mesh, const double *src,
+                                    const double *dst, int64_t nrays, const void *mu, void *out,
+                                    const tetproj_options *opt, void *stream) {
+    if (!mesh || nrays < 0 || (nrays > 0 && (!src || !dst || !mu || !out))) return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    if (nrays == 0) return TETPROJ_OK;
+    tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
+    KParams p = base_params(m, o);
+    p.src_kind = 1;
+    p.rsrc = src;
+    p.rdst = dst;
+    p.nrays = nrays;
+    return run_forward(m, p, o, mu, out, (cudaStream_t)stream);
+}
+
+tetproj_status tetproj_backward_rays(const tetproj_mesh *mesh, const double *src,
+                                     const double *dst, int64_t nrays, const void *y,
+                                     void *mu_out, const tetproj_options *opt, void *stream) {
+    if (!mesh || nrays < 0 || !mu_out || (nrays > 0 && (!src || !dst || !y)))
+        return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
+    KParams p = base_params(m, o);
+    p.src_kind = 1;
+    p.rsrc = src;
+    p.rdst = dst;
+    p.nrays = nrays;
+    if (nrays == 0) {
+        TP_CUDA(cudaMemsetAsync(mu_out, 0,
+                                (size_t)(m->nt * o.channels *
+                                         (o.precision == TETPROJ_PLAIN_FP64 ? 8 : 4)),
+                                (cudaStream_t)stream));
+        return TETPROJ_OK;
+    }
+    return run_backward(m, p, o, y, mu_out, (cudaStream_t)stream);
+}
+
+tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, const double *dst,
+                                  int64_t nrays, int32_t max_visits, int32_t *out_tet,
+                                  double *out_len, int32_t *out_count,
+                                  const tetproj_options *opt, void *stream) {
+    if (!mesh || nrays < 0 || max_visits < 0 ||
+        (nrays > 0 && (!src || !dst || !out_count || (max_visits > 0 && (!out_tet || !out_len)))))
+        return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    if (nrays == 0) return TETPROJ_OK;
+    tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
+    KParams p = base_params(m, o);
+    p.src_kind = 1;
+    p.rsrc = src;
+    p.rdst = dst;
+    p.nrays = nrays;
+    p.tr_tet = out_tet;
+    p.tr_len = out_len;
+    p.tr_count = out_count;
+    p.max_visits = max_visits;
+    TP_CUDA(launch_walk(p, o.precision, 1, MODE_TRACE, (cudaStream_t)stream));
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_side_host(const double *S, const double *P, const double *p,
+                                 const double *q, int64_t n, int8_t *sign, int8_t *stage) {
+    if (n < 0 || (n > 0 && (!S || !P || !p || !q || !sign || !stage))) return TETPROJ_ERR_ARG;
+    for (int64_t k = 0; k < n; ++k) {
+        auto ld = [k](const double *a) { return mk(a[3 * k], a[3 * k + 1], a[3 * k + 2]); };
+        int st = 0;
+        int s = side_sign_cascade(ld(S), ld(P), ld(p), ld(q), &st);
+        sign[k] = (int8_t)s;
+        stage[k] = (int8_t)st;
+    }
+    return TETPROJ_OK;
+}
+
+tetproj_status tetproj_side_device(const double *S, const double *P, const double *p,
+                                   const double *q, int64_t n, int8_t *sign, int8_t *stage,
+                                   void *stream) {
+    if (n < 0 || (n > 0 && (!S || !P || !p || !q || !sign || !stage))) return TETPROJ_ERR_ARG;
+    TP_CUDA(launch_side_device(S, P, p, q, n, sign, stage, (cudaStream_t)stream));
+    return TETPROJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,881 @@
+// kernels.cu -- the per-ray hot path: ray generation, boundary entry search,
+// tet-to-tet walk with exact-sign exit decisions, forward accumulation,
+// backprojection scatter and row tracing.
+//
+// Paper map: Alg. 2 (robust ray propagation: one thread per detector pixel,
+// l = |R2 - R1|, sum += l (t2 - t1) mu, step to the neighbour across the face
+// where t2 happened, stop at -1), Sec. II-E (initialisation: the first tet is
+// found through a search tree over boundary elements, depth first, keeping
+// the earliest hit), Sec. II-F (pixels in small square blocks; backprojection
+// launched like the projection with atomic adds).
+//
+// What differs from the paper's kernels (which target Pascal):
+// * exit faces come from the signs of three side products per step (the three
+//   edges from the new vertex), decided exactly (predicates.cuh), instead of
+//   four Moeller-Trumbore tests with a growing epsilon;
+// * the entry face is THE boundary face the (perturbed) line crosses inward:
+//   for a convex mesh it is unique, so the BVH search stops at the first hit;
+// * a step reads one 64-byte record (four FP32 vertices + packed neighbours);
+//   the entry point of the next tet is carried in registers as a point, and a
+//   segment length is (X_out - X_in).d/|d| with X_out from barycentric weights
+//   given by the side products (no absolute t, so lengths keep relative
+//   accuracy near the origin of fine regions);
+// * every warp runs its 32 rays in lock-step (the loop condition is a warp
+//   vote), which makes warp-level aggregation of backprojection atomics legal.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "../../include/tetproj.h"
+#include "kernels.cuh"
+
+namespace tp {
+
+#define FULL_MASK 0xffffffffu
+
+struct LocalCnt {
+    unsigned rays, hits, segs, fp64, exact, sos, nodes, faces;
+};
+
+__device__ __forceinline__ void report_error(DevCounters *C, int code) {
+    atomicCAS(&C->error, 0, code);
+    atomicAdd(&C->error_count, 1);
+}
+
+__device__ __forceinline__ void flush_counters(DevCounters *C, const LocalCnt &c) {
+    unsigned v[8] = {c.rays, c.hits, c.segs, c.fp64, c.exact, c.sos, c.nodes, c.faces};
+    unsigned long long *dst[8] = {&C->rays, &C->hits, &C->segments, &C->fp64,
+                                  &C->exact, &C->sos, &C->bvh_nodes, &C->bvh_faces};
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        unsigned s = __reduce_add_sync(FULL_MASK, v[k]);
+        if (lane == 0 && s) atomicAdd(dst[k], (unsigned long long)s);
+    }
+}
+
+// ------------------------------------------------------------------ rays
+
+__device__ __forceinline__ void cone_ray(const GeoView &g, int a, int iv, int iu, d3 &S, d3 &P) {
+    const AngleFrame *F = g.frames + a;
+    double u = ((double)iu - 0.5 * (double)(g.nu - 1)) * g.du;
+    double v = ((double)iv - 0.5 * (double)(g.nv - 1)) * g.dv;
+    S = mk(__ldg(&F->S[0]), __ldg(&F->S[1]), __ldg(&F->S[2]));
+    P.x = (__ldg(&F->C[0]) + u * __ldg(&F->U[0])) + v * __ldg(&F->V[0]);
+    P.y = (__ldg(&F->C[1]) + u * __ldg(&F->U[1])) + v * __ldg(&F->V[1]);
+    P.z = (__ldg(&F->C[2]) + u * __ldg(&F->U[2])) + v * __ldg(&F->V[2]);
+}
+
+__device__ __forceinline__ void load_ray(const KParams &p, int64_t ray, d3 &S, d3 &P) {
+    if (p.src_kind == 0) {
+        int iu = (int)(ray % p.g.nu);
+        int64_t r2 = ray / p.g.nu;
+        int iv = (int)(r2 % p.g.nv);
+        int a = (int)(r2 / p.g.nv);
+        cone_ray(p.g, a, iv, iu, S, P);
+    } else {
+        const double *s = p.rsrc + 3 * ray, *d = p.rdst + 3 * ray;
+        S = mk(__ldg(s), __ldg(s + 1), __ldg(s + 2));
+        P = mk(__ldg(d), __ldg(d + 1), __ldg(d + 2));
+    }
+}
+
+__device__ __forceinline__ void morton_local(int t, int bx, int by, int &x, int &y) {
+    x = 0;
+    y = 0;
+    int ix = 0, iy = 0, bit = 0;
+    while (ix < bx || iy < by) {
+        if (ix < bx) { x |= ((t >> bit) & 1) << ix; ++ix; ++bit; }
+        if (iy < by) { y |= ((t >> bit) & 1) << iy; ++iy; ++bit; }
+    }
+}
+
+__device__ __forceinline__ bool thread_ray(const KParams &p, int64_t &ray) {
+    if (p.src_kind == 0) {
+        int lu, lv;
+        int t = threadIdx.x;
+        if (p.morton) morton_local(t, p.log_tu, p.log_tv, lu, lv);
+        else { lu = t & (p.tu - 1); lv = t >> p.log_tu; }
+        int64_t b = blockIdx.x;
+        int tid_u = (int)(b % p.tiles_u);
+        int64_t rest = b / p.tiles_u;
+        int tid_v = (int)(rest % p.tiles_v);
+        int a = (int)(rest / p.tiles_v);
+        int iu = tid_u * p.tu + lu, iv = tid_v * p.tv + lv;
+        if (iu >= p.g.nu || iv >= p.g.nv || a >= p.g.na) return false;
+        ray = ((int64_t)a * p.g.nv + iv) * p.g.nu + iu;
+        return true;
+    }
+    ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    return ray < p.nrays;
+}
+
+// ---------------------------------------------------------- vector helpers
+
+__device__ __forceinline__ f3 f3add(const f3 &a, const f3 &b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 f3axpy(float s, const f3 &x, const f3 &y) {
+    return {fmaf(s, x.x, y.x), fmaf(s, x.y, y.y), fmaf(s, x.z, y.z)};
+}
+__device__ __forceinline__ d3 d3axpy(double s, const d3 &x, const d3 &y) {
+    return {fma(s, x.x, y.x), fma(s, x.y, y.y), fma(s, x.z, y.z)};
+}
+__device__ __forceinline__ float side_val32(const Filt32Ray &r, const f3 &y, const f3 &z) {
+    return dotf(crossf(r.d, sub(y, r.S)), sub(z, y));
+}
+__device__ __forceinline__ int sel4(const int4 &v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ d3 rec64_vertex(const TetRec64 *r, int k) {
+    return mk(__ldg(&r->v[3 * k]), __ldg(&r->v[3 * k + 1]), __ldg(&r->v[3 * k + 2]));
+}
+__device__ __forceinline__ int exit_rule(int sa, int sb, int sc) {
+    if (sb > 0 && sc < 0) return 0;
+    if (sc > 0 && sa < 0) return 1;
+    if (sa > 0 && sb < 0) return 2;
+    return -1;
+}
+
+// ------------------------------------------------ robust (FP64+) fallbacks
+//
+// Used by both walks when a fast sign is uncertain.  They reload the exact
+// FP64 inputs, finish the cascade, and compute the crossing point in FP64
+// from barycentric weights; weights whose side product is exactly zero are 0,
+// and a face whose three side products are exactly zero (the line lies in its
+// plane) is crossed, in the limit of the perturbed line, at t = 1, i.e. at P.
+
+// exact-or-symbolic sign of side(S,P,p,q) once the FP64 filter is known to be
+// uncertain; *zero = 1 when the exact value is 0.
+__device__ __noinline__ int side_exact_or_sos(const d3 &S, const d3 &P, const d3 &p, const d3 &q,
+                                              int *zero, DevCounters *C) {
+    atomicAdd(&C->exact, 1ull);
+    int s = side_exact_sign(S, P, p, q);
+    if (s != 0) { *zero = 0; return s; }
+    atomicAdd(&C->sos, 1ull);
+    *zero = 1;
+    return side_sos_sign(S, P, p, q);
+}
+
+// Exit decision of one step in FP64.  known[j] != 0: sign already certain.
+// Returns the exit index x (0..2 in face-triple order) or -1; X receives the
+// exit point.
+__device__ __noinline__ int step_robust(const KParams *p, int64_t ray, int h, int f,
+                                        const int known[3], d3 *X) {
+    d3 S, P;
+    load_ray(*p, ray, S, P);
+    DevCounters *C = p->m.counters;
+    const TetRec64 *r = p->m.rec64 + h;
+    int ia, ib, ic;
+    face_triple(f, ia, ib, ic);
+    d3 n = rec64_vertex(r, f);
+    d3 k[3] = {rec64_vertex(r, ia), rec64_vertex(r, ib), rec64_vertex(r, ic)};
+    d3 d = sub(P, S);
+    Filt64Vert Vn = filt64_vert(S, d, n);
+    double val[3];
+    int sg[3], zero[3];
+    for (int j = 0; j < 3; ++j) {
+        int s = filt64_side(Vn, k[j], val[j]);
+        zero[j] = 0;
+        if (known[j] != 0) {
+            sg[j] = known[j];
+        } else if (s != 0) {
+            sg[j] = s;
+        } else {
+            sg[j] = side_exact_or_sos(S, P, n, k[j], &zero[j], C);
+        }
+    }
+    int x = exit_rule(sg[0], sg[1], sg[2]);
+    if (x < 0) return -1;
+    int y = (x + 1) % 3, z = (x + 2) % 3;
+    double wy = zero[z] ? 0.0 : fmax(0.0, -val[z]);
+    double wz = zero[y] ? 0.0 : fmax(0.0, val[y]);
+    Filt64Vert Vy = filt64_vert(S, d, k[y]);
+    double vn;
+    int sn = filt64_side(Vy, k[z], vn);
+    double wn = fmax(0.0, vn);
+    if (sn == 0) {
+        int zz;
+        side_exact_or_sos(S, P, k[y], k[z], &zz, C);
+        if (zz) wn = 0.0;
+    }
+    double W = wn + wy + wz;
+    if (W == 0.0) {
+        *X = P;
+    } else {
+        double iw = 1.0 / W;
+        d3 t = d3axpy(wy * iw, sub(k[y], n), n);
+        *X = d3axpy(wz * iw, sub(k[z], n), t);
+    }
+    return x;
+}
+
+// Entry test of boundary face (h, f) in FP64 (+exact, symbolic).  known[j]:
+// certain signs of side(a->b), side(b->c), side(c->a) or 0.  Returns 1 if the
+// line enters the tet through the face, with the entry point in X.
+__device__ __noinline__ int entry_robust(const KParams *p, int64_t ray, int h, int f,
+                                         const int known[3], d3 *X, int count_fp64) {
+    d3 S, P;
+    load_ray(*p, ray, S, P);
+    DevCounters *C = p->m.counters;
+    const TetRec64 *r = p->m.rec64 + h;
+    int ia, ib, ic;
+    face_triple(f, ia, ib, ic);
+    d3 v[3] = {rec64_vertex(r, ia), rec64_vertex(r, ib), rec64_vertex(r, ic)};
+    d3 d = sub(P, S);
+    double val[3];
+    int zero[3];
+    for (int j = 0; j < 3; ++j) {  // side(v_j -> v_{j+1})
+        Filt64Vert Vj = filt64_vert(S, d, v[j]);
+        int s = filt64_side(Vj, v[(j + 1) % 3], val[j]);
+        zero[j] = 0;
+        if (known[j] != 0) {
+            s = known[j];
+        } else {
+            if (count_fp64) atomicAdd(&C->fp64, 1ull);
+            if (s == 0) s = side_exact_or_sos(S, P, v[j], v[(j + 1) % 3], &zero[j], C);
+        }
+        if (s < 0) return 0;
+    }
+    // weights: w_a = side(b->c) = val[1], w_b = side(c->a) = val[2], w_c = side(a->b) = val[0]
+    double wa = zero[1] ? 0.0 : fmax(0.0, val[1]);
+    double wb = zero[2] ? 0.0 : fmax(0.0, val[2]);
+    double wc = zero[0] ? 0.0 : fmax(0.0, val[0]);
+    double W = wa + wb + wc;
+    if (W == 0.0) {
+        *X = P;
+    } else {
+        double iw = 1.0 / W;
+        d3 t = d3axpy(wb * iw, sub(v[1], v[0]), v[0]);
+        *X = d3axpy(wc * iw, sub(v[2], v[0]), t);
+    }
+    return 1;
+}
+
+// ------------------------------------------------------------- BVH search
+//
+// Depth-first, nearer child first, over boxes rounded outward to FP32 and
+// widened per ray by 16u(|S| + mesh radius), with a relative slack on the
+// interval test, so no box holding a face the exact line crosses is culled.
+// The top `smem_nodes` nodes (breadth-first numbering) come from shared memory.
+
+__device__ __forceinline__ bool slab(const float4 &lo, const float4 &hi, const f3 &S, const f3 &inv,
+                                     float m, float &tn) {
+    float tx0 = (lo.x - m - S.x) * inv.x, tx1 = (hi.x + m - S.x) * inv.x;
+    float ty0 = (lo.y - m - S.y) * inv.y, ty1 = (hi.y + m - S.y) * inv.y;
+    float tz0 = (lo.z - m - S.z) * inv.z, tz1 = (hi.z + m - S.z) * inv.z;
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
+    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+    tn = tmin;
+    return tmin <= tmax + 1e-5f * fabsf(tmax) + 1e-7f && tmax >= -1e-6f;
+}
+
+__device__ __forceinline__ f3 safe_inv(const f3 &d) {
+    auto s = [](float x) { return fabsf(x) < 1e-30f ? (x < 0.f ? -1e30f : 1e30f) : 1.f / x; };
+    return {s(d.x), s(d.y), s(d.z)};
+}
+
+// Generic DFS; FaceTest(q, found) tests boundary face q and returns true to stop.
+template <class FaceTest>
+__device__ __forceinline__ void bvh_search(const MeshView &m, const BvhNode *snodes, int nsm,
+                                           const f3 &S, const f3 &inv, float margin,
+                                           LocalCnt &cnt, FaceTest &&test) {
+    int stack[48];
+    int sp = 0;
+    int code = m.root;
+    while (true) {
+        if (code >= 0) {
+            BvhNode n;
+            if (code < nsm) {
+                n = snodes[code];
+            } else {
+                const float4 *g = reinterpret_cast<const float4 *>(m.bvh + code);
+                n.lmin = __ldg(g);
+                n.lmax = __ldg(g + 1);
+                n.rmin = __ldg(g + 2);
+                n.rmax = __ldg(g + 3);
+            }
+            cnt.nodes += 2;
+            float tl, tr;
+            bool hl = slab(n.lmin, n.lmax, S, inv, margin, tl);
+            bool hr = slab(n.rmin, n.rmax, S, inv, margin, tr);
+            int cl = __float_as_int(n.lmin.w), cr = __float_as_int(n.rmin.w);
+            if (hl && hr) {
+                if (tl <= tr) { code = cl; if (sp < 48) stack[sp++] = cr; }
+                else { code = cr; if (sp < 48) stack[sp++] = cl; }
+                continue;
+            }
+            if (hl) { code = cl; continue; }
+            if (hr) { code = cr; continue; }
+        } else {
+            int first = (~code) >> 3, count = (~code) & 7;
+            for (int q = first; q < first + count; ++q) {
+                ++cnt.faces;
+                if (test(q)) return;
+            }
+        }
+        if (sp == 0) return;
+        code = stack[--sp];
+    }
+}
+
+// ======================================================= filtered FP32 walk
+
+template <int C, int MODE>
+__global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KParams p) {
+    extern __shared__ float4 smem[];
+    const int nsm = p.smem_nodes;
+    for (int i = threadIdx.x; i < nsm * 4; i += blockDim.x)
+        smem[i] = __ldg(reinterpret_cast<const float4 *>(p.m.bvh) + i);
+    __syncthreads();
+    const BvhNode *snodes = reinterpret_cast<const BvhNode *>(smem);
+
+    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t ray = 0;
+    const bool valid = thread_ray(p, ray);
+    Filt32Ray fr;
+    f3 dhat = {0.f, 0.f, 0.f}, Xin = {0.f, 0.f, 0.f};
+    int h = 0, f = 0, err = 0, steps = 0, nvis = 0;
+    bool alive = false;
+    float acc[C], comp[C], yv[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) { acc[c] = 0.f; comp[c] = 0.f; yv[c] = 0.f; }
+
+    if (valid) {
+        cnt.rays = 1;
+        d3 S, P;
+        load_ray(p, ray, S, P);
+        fr = filt32_ray(S, P);
+        float il = rsqrtf(dotf(fr.d, fr.d));
+        dhat = {fr.d.x * il, fr.d.y * il, fr.d.z * il};
+        f3 inv = safe_inv(fr.d);
+        float smax = fmaxf(fmaxf(fr.Sabs.x, fr.Sabs.y), fr.Sabs.z);
+        float margin = 16.f * 5.9604645e-8f * (smax + p.m.radius);
+        bvh_search(p.m, snodes, nsm, fr.S, inv, margin, cnt, [&](int q) -> bool {
+            const float4 *g = reinterpret_cast<const float4 *>(p.m.bfaces + q);
+            float4 A = __ldg(g), B = __ldg(g + 1), Cc = __ldg(g + 2);
+            f3 a = {A.x, A.y, A.z}, b = {B.x, B.y, B.z}, c = {Cc.x, Cc.y, Cc.z};
+            float sab, sbc, sca;
+            int gab = filt32_side(filt32_vert(fr, a), b, sab);
+            if (gab < 0) return false;
+            int gbc = filt32_side(filt32_vert(fr, b), c, sbc);
+            if (gbc < 0) return false;
+            int gca = filt32_side(filt32_vert(fr, c), a, sca);
+            if (gca < 0) return false;
+            int hf = __float_as_int(A.w);
+            if (gab > 0 && gbc > 0 && gca > 0) {
+                float iw = 1.f / (sab + sbc + sca);
+                Xin = f3axpy(sca * iw, sub(b, a), f3axpy(sab * iw, sub(c, a), a));
+            } else {
+                int known[3] = {gab, gbc, gca};
+                d3 X;
+                if (!entry_robust(&p, ray, hf >> 2, hf & 3, known, &X, 1)) return false;
+                Xin = tof(X);
+            }
+            h = hf >> 2;
+            f = hf & 3;
+            alive = true;
+            return true;
+        });
+        if (alive) {
+            cnt.hits = 1;
+            // the entry must lie ahead of the source (source outside the mesh)
+            if (dotf(sub(Xin, fr.S), fr.d) < -1e-5f * dotf(fr.d, fr.d)) {
+                err = TETPROJ_ERR_SOURCE_INSIDE;
+                alive = false;
+            }
+        }
+        if (MODE == MODE_BWD && alive) {
+            const float *y = reinterpret_cast<const float *>(p.in) + ray * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) yv[c] = __ldg(y + c);
+        }
+    }
+
+    flush_counters(p.m.counters, cnt);
+    cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    const TetRec32 *rec = p.m.rec32;
+    const float *mu = reinterpret_cast<const float *>(p.in);
+    float *accbuf = reinterpret_cast<float *>(p.out);
+    const int lane = threadIdx.x & 31;
+
+    while (__any_sync(FULL_MASK, alive)) {
+        const bool did = alive;
+        const int hcur = h;
+        float len = 0.f;
+        if (alive) {
+            const float4 *g = reinterpret_cast<const float4 *>(rec + h);
+            float4 q0 = __ldg(g), q1 = __ldg(g + 1), q2 = __ldg(g + 2);
+            int4 adj = __ldg(reinterpret_cast<const int4 *>(g + 3));
+            float muv[C];
+            if (MODE == MODE_FWD) {
+                if (C == 4) {
+                    float4 m4 = __ldg(reinterpret_cast<const float4 *>(mu) + h);
+                    muv[0] = m4.x; muv[1 % C] = m4.y; muv[2 % C] = m4.z; muv[3 % C] = m4.w;
+                } else {
+                    muv[0] = __ldg(mu + h);
+                }
+            }
+            f3 v0 = {q0.x, q0.y, q0.z}, v1 = {q0.w, q1.x, q1.y};
+            f3 v2 = {q1.z, q1.w, q2.x}, v3 = {q2.y, q2.z, q2.w};
+            f3 n, a, b, c;
+            if (f == 0) { n = v0; a = v1; b = v3; c = v2; }
+            else if (f == 1) { n = v1; a = v0; b = v2; c = v3; }
+            else if (f == 2) { n = v2; a = v0; b = v3; c = v1; }
+            else { n = v3; a = v0; b = v1; c = v2; }
+            Filt32Vert Vn = filt32_vert(fr, n);
+            float sa, sb, sc;
+            int ga = filt32_side(Vn, a, sa);
+            int gb = filt32_side(Vn, b, sb);
+            int gc = filt32_side(Vn, c, sc);
+            int x;
+            f3 Xout;
+            if ((ga != 0) & (gb != 0) & (gc != 0)) {
+                f3 y, z;
+                float wy, wz;
+                x = exit_rule(ga, gb, gc);
+                if (x == 0) { y = b; z = c; wy = -sc; wz = sb; }
+                else if (x == 1) { y = c; z = a; wy = -sa; wz = sc; }
+                else { y = a; z = b; wy = -sb; wz = sa; }
+                float wn = fmaxf(side_val32(fr, y, z), 0.f);
+                float iw = 1.f / (wn + wy + wz);
+                Xout = f3axpy(wz * iw, sub(z, n), f3axpy(wy * iw, sub(y, n), n));
+            } else {
+                cnt.fp64 += (ga == 0) + (gb == 0) + (gc == 0);
+                int known[3] = {ga, gb, gc};
+                d3 X;
+                x = step_robust(&p, ray, h, f, known, &X);
+                Xout = tof(X);
+            }
+            ++cnt.segs;
+            if (x < 0) {
+                err = TETPROJ_ERR_RAY_LIMIT;
+                alive = false;
+            } else {
+                int ia, ib, ic;
+                face_triple(f, ia, ib, ic);
+                int loc = x == 0 ? ia : (x == 1 ? ib : ic);
+                int nxt = sel4(adj, loc);
+                len = dotf(sub(Xout, Xin), dhat);
+                if (MODE == MODE_FWD) {
+#pragma unroll
+                    for (int cc = 0; cc < C; ++cc) {  // Kahan
+                        float yk = muv[cc] * len - comp[cc];
+                        float t = acc[cc] + yk;
+                        comp[cc] = (t - acc[cc]) - yk;
+                        acc[cc] = t;
+                    }
+                }
+                if (MODE == MODE_TRACE) {
+                    if (nvis < p.max_visits) {
+                        p.tr_tet[ray * p.max_visits + nvis] = __ldg(p.m.perm + h);
+                        p.tr_len[ray * p.max_visits + nvis] = (double)len;
+                    }
+                    ++nvis;
+                }
+                Xin = Xout;
+                if (nxt < 0) {
+                    alive = false;
+                } else {
+                    h = nxt >> 2;
+                    f = nxt & 3;
+                    if (++steps >= p.max_steps) {
+                        err = TETPROJ_ERR_RAY_LIMIT;
+                        alive = false;
+                    }
+                }
+            }
+        }
+        if (MODE == MODE_BWD) {
+            if (p.scatter == TETPROJ_SCATTER_WARP) {
+                unsigned peers = __match_any_sync(FULL_MASK, did ? hcur : -1 - lane);
+                if (did) {
+                    float v[C];
+#pragma unroll
+                    for (int cc = 0; cc < C; ++cc) v[cc] = len * yv[cc];
+                    if (__popc(peers) > 1) {
+                        float s[C];
+#pragma unroll
+                        for (int cc = 0; cc < C; ++cc) s[cc] = 0.f;
+                        unsigned mm = peers;
+                        while (mm) {
+                            int src = __ffs(mm) - 1;
+                            mm &= mm - 1;
+#pragma unroll
+                            for (int cc = 0; cc < C; ++cc) s[cc] += __shfl_sync(peers, v[cc], src);
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < C; ++cc) v[cc] = s[cc];
+                    }
+                    if (lane == __ffs(peers) - 1) {
+                        if (C == 4)
+                            atomicAdd(reinterpret_cast<float4 *>(accbuf) + hcur,
+                                      make_float4(v[0], v[1 % C], v[2 % C], v[3 % C]));
+                        else
+                            atomicAdd(accbuf + hcur, v[0]);
+                    }
+                }
+            } else if (did) {
+                if (C == 4)
+                    atomicAdd(reinterpret_cast<float4 *>(accbuf) + hcur,
+                              make_float4(len * yv[0], len * yv[1 % C], len * yv[2 % C],
+                                          len * yv[3 % C]));
+                else
+                    atomicAdd(accbuf + hcur, len * yv[0]);
+            }
+        }
+    }
+
+    if (valid) {
+        if (MODE == MODE_FWD) {
+            float *o = reinterpret_cast<float *>(p.out) + ray * C;
+            if (C == 4) {
+                float4 r4 = err ? make_float4(NAN, NAN, NAN, NAN)
+                                : make_float4(acc[0], acc[1 % C], acc[2 % C], acc[3 % C]);
+                *reinterpret_cast<float4 *>(o) = r4;
+            } else {
+                o[0] = err ? NAN : acc[0];
+            }
+        }
+        if (MODE == MODE_TRACE) p.tr_count[ray] = err ? -1 : nvis;
+        if (err) report_error(p.m.counters, err);
+    }
+    flush_counters(p.m.counters, cnt);
+}
+
+// ========================================================= plain FP64 walk
+
+// FP64 sign of side(n->k) for the plain path: FP64 filter, then exact/SoS.
+__device__ __forceinline__ int side64_plain(const Filt64Vert &Vn, const d3 &k, double &val,
+                                            int &zero) {
+    zero = 0;
+    return filt64_side(Vn, k, val);
+}
+
+template <int C, int MODE>
+__global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams p) {
+    extern __shared__ float4 smem[];
+    const int nsm = p.smem_nodes;
+    for (int i = threadIdx.x; i < nsm * 4; i += blockDim.x)
+        smem[i] = __ldg(reinterpret_cast<const float4 *>(p.m.bvh) + i);
+    __syncthreads();
+    const BvhNode *snodes = reinterpret_cast<const BvhNode *>(smem);
+
+    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t ray = 0;
+    const bool valid = thread_ray(p, ray);
+    d3 S = {0, 0, 0}, d = {0, 0, 0}, dhat = {0, 0, 0}, Xin = {0, 0, 0};
+    int h = 0, f = 0, err = 0, steps = 0, nvis = 0;
+    bool alive = false;
+    double acc[C], yv[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) { acc[c] = 0.0; yv[c] = 0.0; }
+
+    if (valid) {
+        cnt.rays = 1;
+        d3 P;
+        load_ray(p, ray, S, P);
+        d = sub(P, S);
+        double il = 1.0 / sqrt(dotd(d, d));
+        dhat = {d.x * il, d.y * il, d.z * il};
+        f3 S32 = tof(S), d32 = tof(d);
+        f3 inv = safe_inv(d32);
+        float smax = fmaxf(fmaxf(fabsf(S32.x), fabsf(S32.y)), fabsf(S32.z));
+        float margin = 16.f * 5.9604645e-8f * (smax + p.m.radius);
+        bvh_search(p.m, snodes, nsm, S32, inv, margin, cnt, [&](int q) -> bool {
+            int hf = __float_as_int(__ldg(reinterpret_cast<const float *>(p.m.bfaces + q) + 3));
+            int hh = hf >> 2, ff = hf & 3;
+            const TetRec64 *r = p.m.rec64 + hh;
+            int ia, ib, ic;
+            face_triple(ff, ia, ib, ic);
+            d3 v[3] = {rec64_vertex(r, ia), rec64_vertex(r, ib), rec64_vertex(r, ic)};
+            double val[3];
+            int known[3];
+            bool unsure = false;
+            for (int j = 0; j < 3; ++j) {
+                int s = filt64_side(filt64_vert(S, d, v[j]), v[(j + 1) % 3], val[j]);
+                if (s < 0) return false;
+                known[j] = s;
+                unsure |= (s == 0);
+            }
+            if (!unsure) {
+                double W = val[0] + val[1] + val[2], iw = 1.0 / W;
+                Xin = d3axpy(val[0] * iw, sub(v[2], v[0]), d3axpy(val[2] * iw, sub(v[1], v[0]), v[0]));
+            } else {
+                d3 X;
+                if (!entry_robust(&p, ray, hh, ff, known, &X, 0)) return false;
+                Xin = X;
+            }
+            h = hh;
+            f = ff;
+            alive = true;
+            return true;
+        });
+        if (alive) {
+            cnt.hits = 1;
+            if (dotd(sub(Xin, S), d) < -1e-12 * dotd(d, d)) {
+                err = TETPROJ_ERR_SOURCE_INSIDE;
+                alive = false;
+            }
+        }
+        if (MODE == MODE_BWD && alive) {
+            const double *y = reinterpret_cast<const double *>(p.in) + ray * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) yv[c] = __ldg(y + c);
+        }
+    }
+
+    flush_counters(p.m.counters, cnt);
+    cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    const double *mu = reinterpret_cast<const double *>(p.in);
+    double *accbuf = reinterpret_cast<double *>(p.out);
+    const int lane = threadIdx.x & 31;
+
+    while (__any_sync(FULL_MASK, alive)) {
+        const bool did = alive;
+        const int hcur = h;
+        double len = 0.0;
+        if (alive) {
+            const TetRec64 *r = p.m.rec64 + h;
+            const double2 *g = reinterpret_cast<const double2 *>(r);
+            double2 e0 = __ldg(g), e1 = __ldg(g + 1), e2 = __ldg(g + 2);
+            double2 e3 = __ldg(g + 3), e4 = __ldg(g + 4), e5 = __ldg(g + 5);
+            int4 adj = __ldg(reinterpret_cast<const int4 *>(g + 6));
+            d3 v0 = {e0.x, e0.y, e1.x}, v1 = {e1.y, e2.x, e2.y};
+            d3 v2 = {e3.x, e3.y, e4.x}, v3 = {e4.y, e5.x, e5.y};
+            double muv[C];
+            if (MODE == MODE_FWD) {
+#pragma unroll
+                for (int cc = 0; cc < C; ++cc) muv[cc] = __ldg(mu + (int64_t)h * C + cc);
+            }
+            d3 n, a, b, c;
+            if (f == 0) { n = v0; a = v1; b = v3; c = v2; }
+            else if (f == 1) { n = v1; a = v0; b = v2; c = v3; }
+            else if (f == 2) { n = v2; a = v0; b = v3; c = v1; }
+            else { n = v3; a = v0; b = v1; c = v2; }
+            Filt64Vert Vn = filt64_vert(S, d, n);
+            double sa, sb, sc;
+            int ga = filt64_side(Vn, a, sa);
+            int gb = filt64_side(Vn, b, sb);
+            int gc = filt64_side(Vn, c, sc);
+            int x;
+            d3 Xout;
+            if ((ga != 0) & (gb != 0) & (gc != 0)) {
+                d3 y, z;
+                double wy, wz;
+                x = exit_rule(ga, gb, gc);
+                if (x == 0) { y = b; z = c; wy = -sc; wz = sb; }
+                else if (x == 1) { y = c; z = a; wy = -sa; wz = sc; }
+                else { y = a; z = b; wy = -sb; wz = sa; }
+                double vn;
+                filt64_side(filt64_vert(S, d, y), z, vn);
+                double wn = fmax(vn, 0.0);
+                double iw = 1.0 / (wn + wy + wz);
+                Xout = d3axpy(wz * iw, sub(z, n), d3axpy(wy * iw, sub(y, n), n));
+            } else {
+                int known[3] = {ga, gb, gc};
+                x = step_robust(&p, ray, h, f, known, &Xout);
+            }
+            ++cnt.segs;
+            if (x < 0) {
+                err = TETPROJ_ERR_RAY_LIMIT;
+                alive = false;
+            } else {
+                int ia, ib, ic;
+                face_triple(f, ia, ib, ic);
+                int loc = x == 0 ? ia : (x == 1 ? ib : ic);
+                int nxt = sel4(adj, loc);
+                len = dotd(sub(Xout, Xin), dhat);
+                if (MODE == MODE_FWD) {
+#pragma unroll
+                    for (int cc = 0; cc < C; ++cc) acc[cc] = fma(muv[cc], len, acc[cc]);
+                }
+                if (MODE == MODE_TRACE) {
+                    if (nvis < p.max_visits) {
+                        p.tr_tet[ray * p.max_visits + nvis] = __ldg(&r->extra.x);
+                        p.tr_len[ray * p.max_visits + nvis] = len;
+                    }
+                    ++nvis;
+                }
+                Xin = Xout;
+                if (nxt < 0) {
+                    alive = false;
+                } else {
+                    h = nxt >> 2;
+                    f = nxt & 3;
+                    if (++steps >= p.max_steps) {
+                        err = TETPROJ_ERR_RAY_LIMIT;
+                        alive = false;
+                    }
+                }
+            }
+        }
+        if (MODE == MODE_BWD) {
+            if (p.scatter == TETPROJ_SCATTER_WARP) {
+                unsigned peers = __match_any_sync(FULL_MASK, did ? hcur : -1 - lane);
+                if (did) {
+                    double v[C];
+#pragma unroll
+                    for (int cc = 0; cc < C; ++cc) v[cc] = len * yv[cc];
+                    if (__popc(peers) > 1) {
+                        double s[C];
+#pragma unroll
+                        for (int cc = 0; cc < C; ++cc) s[cc] = 0.0;
+                        unsigned mm = peers;
+                        while (mm) {
+                            int src = __ffs(mm) - 1;
+                            mm &= mm - 1;
+#pragma unroll
+                            for (int cc = 0; cc < C; ++cc) s[cc] += __shfl_sync(peers, v[cc], src);
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < C; ++cc) v[cc] = s[cc];
+                    }
+                    if (lane == __ffs(peers) - 1) {
+#pragma unroll
+                        for (int cc = 0; cc < C; ++cc) atomicAdd(accbuf + (int64_t)hcur * C + cc, v[cc]);
+                    }
+                }
+            } else if (did) {
+#pragma unroll
+                for (int cc = 0; cc < C; ++cc)
+                    atomicAdd(accbuf + (int64_t)hcur * C + cc, len * yv[cc]);
+            }
+        }
+    }
+
+    if (valid) {
+        if (MODE == MODE_FWD) {
+            double *o = reinterpret_cast<double *>(p.out) + ray * C;
+#pragma unroll
+            for (int cc = 0; cc < C; ++cc) o[cc] = err ? NAN : acc[cc];
+        }
+        if (MODE == MODE_TRACE) p.tr_count[ray] = err ? -1 : nvis;
+        if (err) report_error(p.m.counters, err);
+    }
+    flush_counters(p.m.counters, cnt);
+}
+
+// ============================================================ small kernels
+
+template <typename T>
+__global__ void k_gather_perm(const int32_t *__restrict__ perm, int64_t nt, int C,
+                              const T *__restrict__ src, T *__restrict__ dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt * C) return;
+    int64_t h = i / C;
+    int c = (int)(i - h * C);
+    dst[i] = src[(int64_t)__ldg(perm + h) * C + c];
+}
+template <typename T>
+__global__ void k_scatter_perm(const int32_t *__restrict__ perm, int64_t nt, int C,
+                               const T *__restrict__ src, T *__restrict__ dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt * C) return;
+    int64_t h = i / C;
+    int c = (int)(i - h * C);
+    dst[(int64_t)__ldg(perm + h) * C + c] = src[i];
+}
+
+__global__ void k_geometry_rays(GeoView g, const int64_t *idx, int64_t n, double *src,
+                                double *dst) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t j = idx ? idx[k] : k;
+    int iu = (int)(j % g.nu);
+    int64_t r2 = j / g.nu;
+    int iv = (int)(r2 % g.nv);
+    int a = (int)(r2 / g.nv);
+    if (a < 0 || a >= g.na) return;
+    d3 S, P;
+    cone_ray(g, a, iv, iu, S, P);
+    src[3 * k] = S.x; src[3 * k + 1] = S.y; src[3 * k + 2] = S.z;
+    dst[3 * k] = P.x; dst[3 * k + 1] = P.y; dst[3 * k + 2] = P.z;
+}
+
+__global__ void k_side(const double *S, const double *P, const double *p, const double *q,
+                       int64_t n, int8_t *sign, int8_t *stage) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    auto ld = [](const double *a, int64_t k) { return mk(a[3 * k], a[3 * k + 1], a[3 * k + 2]); };
+    int st = 0;
+    int s = side_sign_cascade(ld(S, k), ld(P, k), ld(p, k), ld(q, k), &st);
+    sign[k] = (int8_t)s;
+    stage[k] = (int8_t)st;
+}
+
+// ================================================================ launchers
+
+template <int C, int MODE>
+static cudaError_t launch_mode(const KParams &p, int precision, dim3 grid, dim3 block,
+                               size_t smem, cudaStream_t stream) {
+    if (precision == TETPROJ_FILTERED) k_walk32<C, MODE><<<grid, block, smem, stream>>>(p);
+    else k_walk64<C, MODE><<<grid, block, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
+                        cudaStream_t stream) {
+    int64_t nblocks;
+    int threads;
+    if (p.src_kind == 0) {
+        threads = p.tu * p.tv;
+        nblocks = (int64_t)p.g.na * p.tiles_u * p.tiles_v;
+    } else {
+        threads = 128;
+        nblocks = (p.nrays + threads - 1) / threads;
+    }
+    if (nblocks <= 0) return cudaSuccess;
+    if (nblocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)nblocks), block(threads);
+    size_t smem = (size_t)p.smem_nodes * sizeof(BvhNode);
+    if (mode == MODE_FWD) {
+        return channels == 4 ? launch_mode<4, MODE_FWD>(p, precision, grid, block, smem, stream)
+                             : launch_mode<1, MODE_FWD>(p, precision, grid, block, smem, stream);
+    }
+    if (mode == MODE_BWD) {
+        return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, grid, block, smem, stream)
+                             : launch_mode<1, MODE_BWD>(p, precision, grid, block, smem, stream);
+    }
+    return launch_mode<1, MODE_TRACE>(p, precision, grid, block, smem, stream);
+}
+
+cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, int f64,
+                               const void *src_user, void *dst_h, cudaStream_t stream) {
+    int64_t n = nt * channels;
+    int64_t blocks = (n + 255) / 256;
+    if (f64)
+        k_gather_perm<double><<<(unsigned)blocks, 256, 0, stream>>>(
+            perm, nt, channels, (const double *)src_user, (double *)dst_h);
+    else
+        k_gather_perm<float><<<(unsigned)blocks, 256, 0, stream>>>(
+            perm, nt, channels, (const float *)src_user, (float *)dst_h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_perm(const int32_t *perm, int64_t nt, int channels, int f64,
+                                const void *src_h, void *dst_user, cudaStream_t stream) {
+    int64_t n = nt * channels;
+    int64_t blocks = (n + 255) / 256;
+    if (f64)
+        k_scatter_perm<double><<<(unsigned)blocks, 256, 0, stream>>>(
+            perm, nt, channels, (const double *)src_h, (double *)dst_user);
+    else
+        k_scatter_perm<float><<<(unsigned)blocks, 256, 0, stream>>>(
+            perm, nt, channels, (const float *)src_h, (float *)dst_user);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geometry_rays(const GeoView &g, const int64_t *idx, int64_t n, double *src,
+                                 double *dst, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    k_geometry_rays<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(g, idx, n, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_side_device(const double *S, const double *P, const double *p,
+                               const double *q, int64_t n, int8_t *sign, int8_t *stage,
+                               cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    k_side<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(S, P, p, q, n, sign, stage);
+    return cudaGetLastError();
+}
+
+}  // namespace tp

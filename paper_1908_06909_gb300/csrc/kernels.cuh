@@ -1,0 +1,49 @@
+// kernels.cuh -- launch interface between the C ABI (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tetproj_internal.h"
+
+namespace tp {
+
+enum { MODE_FWD = 0, MODE_BWD = 1, MODE_TRACE = 2 };
+
+struct KParams {
+    MeshView m;
+    // ray source: cone-beam tiles (src_kind 0) or explicit rays (1)
+    int32_t src_kind;
+    GeoView g;
+    const double *rsrc;
+    const double *rdst;
+    int64_t nrays;
+    // ray tiles
+    int32_t tu, tv, log_tu, log_tv, tiles_u, tiles_v, morton;
+    // operands (Hilbert-ordered tet data; ray-ordered projection data)
+    const void *in;   // FWD: mu_h [nt][C]; BWD: y [nrays][C]
+    void *out;        // FWD: proj [nrays][C]; BWD: acc_h [nt][C]
+    // trace outputs
+    int32_t *tr_tet;
+    double *tr_len;
+    int32_t *tr_count;
+    int32_t max_visits;
+    int32_t max_steps;
+    int32_t scatter;
+    int32_t smem_nodes;
+};
+
+// one launch of the walk; returns a cudaError_t
+cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
+                        cudaStream_t stream);
+cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, int f64,
+                               const void *src_user, void *dst_h, cudaStream_t stream);
+cudaError_t launch_scatter_perm(const int32_t *perm, int64_t nt, int channels, int f64,
+                                const void *src_h, void *dst_user, cudaStream_t stream);
+cudaError_t launch_geometry_rays(const GeoView &g, const int64_t *idx, int64_t n, double *src,
+                                 double *dst, cudaStream_t stream);
+cudaError_t launch_side_device(const double *S, const double *P, const double *p,
+                               const double *q, int64_t n, int8_t *sign, int8_t *stage,
+                               cudaStream_t stream);
+
+}  // namespace tp

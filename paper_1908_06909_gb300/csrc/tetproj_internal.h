@@ -1,0 +1,93 @@
+// tetproj_internal.h -- data layout shared by the host builder and the kernels.
+//
+// Device mesh (Sec. II-B: "each element contains nD+1 nodes and nD+1 ordered
+// neighbour indexes"), stored as structure-of-arrays records indexed by the
+// tet's position h along a 3-D Hilbert curve of tet centroids:
+//
+//   TetRec32  64 B  the four vertices in FP32 (12 floats, three float4) and the
+//                   packed neighbours adj[k] = (h' << 2) | k' across the face
+//                   opposite local vertex k (k' = that face's index in h'),
+//                   or -1 on the boundary.  One walk step reads exactly these
+//                   two 32-byte sectors.
+//   TetRec64 128 B  the same vertices in FP64 (exact inputs of the predicate
+//                   fallback and of the FP64 path), adj, and the user's tet id.
+//
+// Each tet's local vertices are positively oriented: orient3d(v0,v1,v2,v3) > 0.
+// Face f is opposite v_f; FACE_TRIPLE[f] lists its vertices so that
+// orient3d(a, b, c, v_f) > 0 (v_f on the positive side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "predicates.cuh"
+
+namespace tp {
+
+struct __align__(16) TetRec32 {
+    float4 q0;  // v0.x v0.y v0.z v1.x
+    float4 q1;  // v1.y v1.z v2.x v2.y
+    float4 q2;  // v2.z v3.x v3.y v3.z
+    int4 adj;
+};
+static_assert(sizeof(TetRec32) == 64, "TetRec32 must be 64 bytes");
+
+struct __align__(16) TetRec64 {
+    double v[12];  // v0..v3 xyz
+    int4 adj;
+    int4 extra;    // x: user tet id
+};
+static_assert(sizeof(TetRec64) == 128, "TetRec64 must be 128 bytes");
+
+// Boundary face, FP32 copy in FACE_TRIPLE order; a.w holds the int bits of
+// (h << 2) | f.
+struct __align__(16) BFace32 {
+    float4 a, b, c;
+};
+
+// Binary BVH node holding both children's boxes (one 64-byte load tests two
+// boxes).  child >= 0: internal node index; child < 0: leaf ~(first << 3 | count).
+struct __align__(16) BvhNode {
+    float4 lmin;  // xyz, w = bits of left child code
+    float4 lmax;  // xyz, w unused
+    float4 rmin;  // xyz, w = bits of right child code
+    float4 rmax;
+};
+
+struct AngleFrame {
+    double S[3], C[3], U[3], V[3];
+};
+
+struct DevCounters {
+    unsigned long long rays, hits, segments, fp64, exact, sos, bvh_nodes, bvh_faces;
+    int error;
+    int error_count;
+    int pad[2];
+};
+
+struct MeshView {
+    const TetRec32 *rec32;
+    const TetRec64 *rec64;
+    const BvhNode *bvh;
+    const BFace32 *bfaces;
+    const int32_t *perm;  // h -> user tet id
+    int64_t nt, nb, nnodes;
+    int32_t root;         // root code (0, or a leaf code for tiny meshes)
+    float radius;         // max |coordinate| over all vertices
+    DevCounters *counters;
+};
+
+struct GeoView {
+    const AngleFrame *frames;
+    int32_t nu, nv, na;
+    double du, dv;
+};
+
+TP_HD void face_triple(int f, int &a, int &b, int &c) {
+    // f0: (1,3,2) f1: (0,2,3) f2: (0,3,1) f3: (0,1,2)
+    a = (f == 0) ? 1 : 0;
+    b = (f == 0) ? 3 : (f == 1 ? 2 : (f == 2 ? 3 : 1));
+    c = (f == 0) ? 2 : (f == 1 ? 3 : (f == 2 ? 1 : 2));
+}
+
+}  // namespace tp

@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (relative to the magnitude sum sum_i a_ij |mu_i| per ray, or
+sum_j a_ij |y_j| per tet): 1e-12 for the plain FP64 path, 1e-5 for the
+filtered FP32 path.  Rays lying in a face plane have two valid integrals
+(the one-sided limits); the GPU value must lie between them (+- tol).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from oracle import exact
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def tp():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    assert torch.cuda.is_available()
+    import paper_1908_06909_gb300 as tp
+    return tp
+
+
+def _dt(prec):
+    import torch
+    return torch.float64 if prec == "f64" else torch.float32
+
+
+def _side_dir(seed, n):
+    rng = np.random.default_rng(seed)
+    w = rng.normal(size=(n, 3))
+    return w / np.linalg.norm(w, axis=1, keepdims=True)
+
+
+class C1Data:
+    def __init__(self, tp):
+        self.w = W.config1()
+        w = self.w
+        self.mesh = tp.Mesh(w.verts, w.tets)
+        self.geo = tp.Geometry.from_cone(w.geom)
+        self.S, self.P = oracle.cone_rays(w.geom)
+        tt, lo, hi, cnt, margin, planar = oracle.trace_rays(w.verts, w.tets, self.S, self.P,
+                                                            max_visits=128)
+        self.tr = (tt, lo, hi, cnt, margin, planar)
+        self.planar = planar
+        self.b = oracle.forward_cone(w.verts, w.tets, w.mu, w.geom)
+        self.scale = oracle.forward_cone(w.verts, w.tets, np.abs(w.mu), w.geom)
+        idx = np.nonzero(planar)[0]
+        wdir = _side_dir(3, idx.size)
+        self.lim = np.stack([
+            oracle.forward_rays(w.verts, w.tets, w.mu, self.S[idx], self.P[idx], side=wdir),
+            oracle.forward_rays(w.verts, w.tets, w.mu, self.S[idx], self.P[idx], side=-wdir)])
+        self.planar_idx = idx
+
+
+@pytest.fixture(scope="module")
+def c1(tp):
+    return C1Data(tp)
+
+
+def _check_rays(got, want, scale, planar_idx, lim, tol):
+    got = np.asarray(got, dtype=np.float64).reshape(-1)
+    ok = np.ones(got.size, bool)
+    ok[planar_idx] = False
+    err = np.abs(got[ok] - want[ok])
+    bound = tol * np.maximum(scale[ok], 1e-300)
+    assert np.all(err <= bound), f"max rel err {np.max(err / np.maximum(scale[ok], 1e-300)):.3e}"
+    if planar_idx.size:
+        g = got[planar_idx]
+        lo, hi = lim.min(axis=0), lim.max(axis=0)
+        slack = tol * np.maximum(scale[planar_idx], 1e-300)
+        assert np.all((g >= lo - slack) & (g <= hi + slack))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_forward_c1(tp, c1, prec):
+    import torch
+    mu = torch.tensor(c1.w.mu, dtype=_dt(prec), device="cuda")
+    c1.mesh.stats_reset()
+    proj = tp.forward(c1.mesh, c1.geo, mu)
+    torch.cuda.synchronize()
+    assert proj.shape == (32, 64, 64)
+    assert c1.planar_idx.size > 0  # C1 contains rays lying in Kuhn face planes
+    _check_rays(proj.double().cpu().numpy(), c1.b, c1.scale, c1.planar_idx, c1.lim, TOL[prec])
+    st = c1.mesh.stats()
+    assert st["error"] == 0 and st["rays"] == 131072
+    assert st["hits"] == int((c1.scale > 0).sum())
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_backward_c1(tp, c1, prec):
+    import torch
+    rng = np.random.default_rng(31)
+    y = rng.uniform(0, 1, size=c1.geo.nrays)
+    y[c1.planar_idx] = 0.0  # per-tet values of in-plane rays are ambiguous
+    want = oracle.backward_cone(c1.w.verts, c1.w.tets, y, c1.w.geom)
+    scale = want  # y >= 0
+    yt = torch.tensor(y.reshape(c1.geo.shape), dtype=_dt(prec), device="cuda")
+    got = tp.backward(c1.mesh, c1.geo, yt).double().cpu().numpy()
+    err = np.abs(got - want)
+    assert np.all(err <= TOL[prec] * np.maximum(scale, 1e-300) + 1e-300), err.max()
+    assert (want > 0).sum() > 2000
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_closed_form_chord(tp, c1, prec):
+    import torch
+    one = torch.ones(c1.mesh.nt, dtype=_dt(prec), device="cuda")
+    got = tp.forward(c1.mesh, c1.geo, one).double().cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(4)
+    for k in rng.choice(got.size, 3000, replace=False):
+        iv = exact.cube_interval(c1.S[k], c1.P[k])
+        d = c1.P[k] - c1.S[k]
+        want = 0.0 if iv is None else float(iv[1] - iv[0]) * float(np.sqrt(d @ d))
+        assert abs(got[k] - want) <= TOL[prec] * max(want, 1e-3), (k, got[k], want)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_visit_sequences(tp, c1, prec):
+    """Identical tet-visit sequences on non-degenerate rays."""
+    import torch
+    tt, lo, hi, cnt, margin, planar = c1.tr
+    rng = np.random.default_rng(5)
+    cand = np.nonzero((margin > 1e-9) & (~planar) & (cnt > 0))[0]
+    sel = rng.choice(cand, 3000, replace=False)
+    src = torch.tensor(c1.S[sel], device="cuda")
+    dst = torch.tensor(c1.P[sel], device="cuda")
+    gt, gl, gc = tp.trace_rays(c1.mesh, src, dst, max_visits=128,
+                               precision=tp.FILTERED if prec == "f32" else tp.PLAIN_FP64)
+    gt, gl, gc = gt.cpu().numpy(), gl.cpu().numpy(), gc.cpu().numpy()
+    dlen = np.linalg.norm(c1.P[sel] - c1.S[sel], axis=1)
+    for r, k in enumerate(sel):
+        n = cnt[k]
+        assert gc[r] == n, (k, gc[r], n)
+        assert np.array_equal(gt[r, :n], tt[k, :n])
+        want = (hi[k, :n] - lo[k, :n]) * dlen[r]
+        assert np.all(np.abs(gl[r, :n] - want) <= (1e-12 if prec == "f64" else 2e-6) * 4)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_adjoint_identity(tp, c1, prec):
+    import torch
+    g = torch.Generator("cuda").manual_seed(7)
+    x = torch.rand(c1.mesh.nt, dtype=_dt(prec), device="cuda", generator=g) - 0.5
+    y = torch.rand(c1.geo.shape, dtype=_dt(prec), device="cuda", generator=g) - 0.5
+    Ax = tp.forward(c1.mesh, c1.geo, x)
+    Aty = tp.backward(c1.mesh, c1.geo, y)
+    lhs = float((Ax.double() * y.double()).sum())
+    rhs = float((x.double() * Aty.double()).sum())
+    mag = float((tp.forward(c1.mesh, c1.geo, x.abs()).double() * y.double().abs()).sum())
+    assert abs(lhs - rhs) <= TOL[prec] * mag
+
+
+def test_geometry_rays_bit_exact(tp, c1):
+    import torch
+    src, dst = c1.geo.rays()
+    assert np.array_equal(src.cpu().numpy(), c1.S)
+    assert np.array_equal(dst.cpu().numpy(), c1.P)
+    idx = torch.tensor([0, 5, 131071, 4096], device="cuda")
+    s2, d2 = c1.geo.rays(idx)
+    assert np.array_equal(d2.cpu().numpy(), c1.P[[0, 5, 131071, 4096]])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_channels_and_rays_api(tp, c1, prec):
+    import torch
+    rng = np.random.default_rng(8)
+    mu4 = rng.uniform(size=(c1.mesh.nt, 4))
+    m4 = torch.tensor(mu4, dtype=_dt(prec), device="cuda")
+    p4 = tp.forward(c1.mesh, c1.geo, m4)
+    for c in range(4):
+        p1 = tp.forward(c1.mesh, c1.geo, m4[:, c].contiguous())
+        assert torch.allclose(p4[..., c], p1, rtol=TOL[prec], atol=1e-30)
+    y4 = torch.tensor(rng.uniform(size=c1.geo.shape + (4,)), dtype=_dt(prec), device="cuda")
+    b4 = tp.backward(c1.mesh, c1.geo, y4)
+    for c in (0, 3):
+        b1 = tp.backward(c1.mesh, c1.geo, y4[..., c].contiguous())
+        assert torch.allclose(b4[:, c], b1, rtol=10 * TOL[prec], atol=1e-12)
+    # explicit-ray API on the same rays equals the cone-beam call
+    src, dst = c1.geo.rays()
+    mu = m4[:, 0].contiguous()
+    pr = tp.forward_rays(c1.mesh, src, dst, mu)
+    pc = tp.forward(c1.mesh, c1.geo, mu).reshape(-1)
+    assert torch.allclose(pr, pc, rtol=TOL[prec], atol=1e-30)
+    yr = torch.rand(src.shape[0], dtype=_dt(prec), device="cuda")
+    br = tp.backward_rays(c1.mesh, src, dst, yr)
+    bc = tp.backward(c1.mesh, c1.geo, yr.reshape(c1.geo.shape))
+    assert torch.allclose(br, bc, rtol=10 * TOL[prec], atol=1e-12)
+
+
+def test_side_device_matches_host(tp):
+    import torch
+    rng = np.random.default_rng(9)
+    n = 30000
+    p = rng.uniform(-1, 1, size=(n, 3))
+    q = p + rng.normal(size=(n, 3)) * 10.0 ** rng.uniform(-5, -1, size=(n, 1))
+    X = p + rng.uniform(-0.5, 1.5, size=(n, 1)) * (q - p)
+    S = rng.uniform(-4, 4, size=(n, 3))
+    P = S + 2 * (X - S) + 10.0 ** rng.uniform(-16, -2, size=(n, 1)) * rng.normal(size=(n, 3))
+    # exact zeros too: rays aimed at p
+    P[:3000] = p[:3000]
+    hs, hst = tp.side_signs_host(S, P, p, q)
+    T = lambda a: torch.tensor(a, device="cuda")
+    ds, dst = tp.side_signs_device(T(S), T(P), T(p), T(q))
+    assert np.array_equal(ds.cpu().numpy(), hs)
+    assert np.array_equal(dst.cpu().numpy(), hst)
+    assert (hst == 3).sum() >= 3000
+
+
+def _one_sided(verts, tets, mu, S, P, seed):
+    wdir = _side_dir(seed, S.shape[0])
+    return np.stack([oracle.forward_rays(verts, tets, mu, S, P, side=wdir),
+                     oracle.forward_rays(verts, tets, mu, S, P, side=-wdir)])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_adversarial_rays_small(tp, prec):
+    """Rays aimed exactly at vertices, edge midpoints and face points of a
+    cubic-mapped Kuhn 8^3 mesh: values equal the oracle (or lie between the
+    one-sided limits for rays inside a face plane); no walk fails."""
+    import torch
+    verts, tets = W.kuhn_cube(8)
+    verts = W.cubic_map(verts)
+    rng = W.rng_for(2, 9)
+    mu = rng.uniform(size=tets.shape[0])
+    S, T, kind = W.adversarial_rays(verts, tets, 8, 3000, rng)
+    mesh = tp.Mesh(verts, tets)
+    _, _, _, _, margin, planar = oracle.trace_rays(verts, tets, S, T, max_visits=4)
+    want = oracle.forward_rays(verts, tets, mu, S, T)
+    scale = want
+    pidx = np.nonzero(planar)[0]
+    lim = _one_sided(verts, tets, mu, S[pidx], T[pidx], 11)
+    mesh.stats_reset()
+    got = tp.forward_rays(mesh, torch.tensor(S, device="cuda"), torch.tensor(T, device="cuda"),
+                          torch.tensor(mu, dtype=_dt(prec), device="cuda"))
+    st = mesh.stats()
+    assert st["error"] == 0 and st["error_count"] == 0
+    assert st["sos"] > 0  # exact zeros were met and resolved symbolically
+    _check_rays(got.double().cpu().numpy(), want, scale, pidx, lim, TOL[prec])
+    assert (margin < 1e-12).sum() > 1000  # the set really is degenerate
+
+
+def test_errors_reported(tp, c1):
+    import torch
+    mu = torch.ones(c1.mesh.nt, dtype=torch.float32, device="cuda")
+    o = tp.make_options(max_steps=2)
+    c1.mesh.stats_reset()
+    proj = tp.forward(c1.mesh, c1.geo, mu, options=o)
+    st = c1.mesh.stats()
+    assert st["error"] == tp._lib.ERR_RAY_LIMIT and st["error_count"] > 0
+    assert torch.isnan(proj).any()
+    # a source inside the mesh is reported
+    c1.mesh.stats_reset()
+    src = torch.tensor([[0.01, 0.02, 0.03]], dtype=torch.float64, device="cuda")
+    dst = torch.tensor([[3.0, 0.5, 0.2]], dtype=torch.float64, device="cuda")
+    tp.forward_rays(c1.mesh, src, dst, mu)
+    st = c1.mesh.stats()
+    assert st["error"] == tp._lib.ERR_SOURCE_INSIDE
+    c1.mesh.stats_reset()
+
+
+def test_empty_and_single_tet(tp):
+    import torch
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    T = np.array([[0, 2, 1, 3]])
+    mesh = tp.Mesh(V, T)
+    e = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    mu = torch.tensor([2.0], dtype=torch.float64, device="cuda")
+    assert tp.forward_rays(mesh, e, e, mu).numel() == 0
+    out = tp.backward_rays(mesh, e, e, torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert out.shape == (1,) and float(out[0]) == 0.0
+    rows = []
+    for line in open(__file__.replace("test_gpu_parity.py", "golden/single_tet_chords.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append([float(x) for x in line.split()])
+    rows = np.array(rows)
+    ok = rows[:, 0] + rows[:, 1] + rows[:, 2] > 1.0 + 1e-9  # sources outside the tet
+    ok |= (rows[:, 0:3] < 0).any(axis=1)
+    rows = rows[ok]
+    src = torch.tensor(rows[:, 0:3], device="cuda")
+    dst = torch.tensor(rows[:, 3:6], device="cuda")
+    for dt, tol in ((torch.float64, 1e-14), (torch.float32, 1e-6)):
+        got = tp.forward_rays(mesh, src, dst, mu.to(dt)).double().cpu().numpy()
+        assert np.allclose(got, 2.0 * rows[:, 6], rtol=tol, atol=tol)
