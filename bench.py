@@ -115,6 +115,10 @@ def build_workload(args):
         return W.config2()
     if args.workload == "kuhn24":   # small case for quick runs
         return W.config2(n_cells=24, det=128, pitch=0.05, nangles=32)
+    if args.workload == "kuhn64":   # 1.57M tets, 256^2 x 180 (11.8M rays)
+        return W.config2(n_cells=64, det=256, pitch=0.025, nangles=180)
+    if args.workload == "kuhn64s":  # same mesh, 30 angles: profiler-sized launches
+        return W.config2(n_cells=64, det=256, pitch=0.025, nangles=30)
     raise SystemExit(f"unknown workload {args.workload}")
 
 

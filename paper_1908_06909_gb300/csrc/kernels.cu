@@ -119,7 +119,7 @@ __device__ __forceinline__ d3 d3axpy(double s, const d3 &x, const d3 &y) {
     return {fma(s, x.x, y.x), fma(s, x.y, y.y), fma(s, x.z, y.z)};
 }
 __device__ __forceinline__ float side_val32(const Filt32Ray &r, const f3 &y, const f3 &z) {
-    return dotf(crossf(r.d, sub(y, r.S)), sub(z, y));
+    return dotf(crossf(r.d, sub(y, r.O)), sub(z, y));
 }
 __device__ __forceinline__ int sel4(const int4 &v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
@@ -346,9 +346,10 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
         float il = rsqrtf(dotf(fr.d, fr.d));
         dhat = {fr.d.x * il, fr.d.y * il, fr.d.z * il};
         f3 inv = safe_inv(fr.d);
-        float smax = fmaxf(fmaxf(fr.Sabs.x, fr.Sabs.y), fr.Sabs.z);
+        f3 S32 = tof(S);
+        float smax = fmaxf(fmaxf(fabsf(S32.x), fabsf(S32.y)), fabsf(S32.z));
         float margin = 16.f * 5.9604645e-8f * (smax + p.m.radius);
-        bvh_search(p.m, snodes, nsm, fr.S, inv, margin, cnt, [&](int q) -> bool {
+        bvh_search(p.m, snodes, nsm, S32, inv, margin, cnt, [&](int q) -> bool {
             const float4 *g = reinterpret_cast<const float4 *>(p.m.bfaces + q);
             float4 A = __ldg(g), B = __ldg(g + 1), Cc = __ldg(g + 2);
             f3 a = {A.x, A.y, A.z}, b = {B.x, B.y, B.z}, c = {Cc.x, Cc.y, Cc.z};
@@ -376,8 +377,9 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
         });
         if (alive) {
             cnt.hits = 1;
-            // the entry must lie ahead of the source (source outside the mesh)
-            if (dotf(sub(Xin, fr.S), fr.d) < -1e-5f * dotf(fr.d, fr.d)) {
+            // the entry must lie ahead of the source (source outside the mesh):
+            // t_in = 1/2 + (X_in - O).d / |d|^2 >= 0
+            if (dotf(sub(Xin, fr.O), fr.d) < -(0.5f + 1e-5f) * dotf(fr.d, fr.d)) {
                 err = TETPROJ_ERR_SOURCE_INSIDE;
                 alive = false;
             }

@@ -86,19 +86,25 @@ TP_HD double dotd(const d3 &a, const d3 &b) { return fma(a.x, b.x, fma(a.y, b.y,
 
 // ------------------------------------------------------------------ FP32 stage
 //
-// For one ray (S, P) and one vertex n shared by three edges n->k, the walk
-// computes  w = d32 x (n32 - S32)  once and  side(n->k) ~ w . (k32 - n32).
-// Error analysis (u = 2^-24, RN; d32 = fl32(fl64(P - S)), x32 = fl32(x)):
-//   |side32 - side| <= u [ (7.05 X + Y) . |e| + 1.01 X . (|k| + |n|) ] + O(u^2)
-// with X = |d| x |a|, Y = |d| x (|a| + 1.01 (|n| + |S|)), a = n - S, e = k - n
-// (all computed FP32 values; x here is the abs-cross above).  The terms are:
-// 3.01u|w|.|e| for the dot with FMAs, 2.01u X.|e| for the FMA cross, and the
-// propagated input errors |dd| <= 1.01u|d|, |da| <= u(|a| + 1.01|n| + 1.01|S|),
-// |de| <= u(|e| + 1.01|k| + 1.01|n|) through the trilinear form.  The constant
-// below is 2^-24 * 1.0234, covering the O(u^2) terms and the rounding of the
-// bound itself (non-negative terms, ~10 operations).
+// side(S, P, p, q) = det[D, p - O, q - p] for ANY point O of the ray line
+// (D = P - S); the FP32 stage uses the midpoint O = (S + P)/2, which keeps
+// |p - O| ~ the object size instead of the source distance.  For one vertex n
+// shared by three edges n->k the walk computes  w = d32 x (n32 - O32)  once and
+// side(n->k) ~ w . (k32 - n32).  Error analysis (u = 2^-24, round to nearest;
+// d32 = fl32(fl64(P - S)), O32 = fl32(fl64(S + P)/2), x32 = fl32(x)):
+//   |side32 - side| <= u [ Z1 . |e| + Z2 . (|k| + |n|) ] + O(u^2)
+//   Z1 = 3.02 X + Y + 4.01 |w|,   Z2 = 1.01 |w| + 1e-6 (X + Y)
+// with a = n - O, e = k - n, X = |d| x |a| and Y = |d| x Ma, where x is the
+// cross product of absolute values and Ma = |a| + 1.01 (|n| + |O|) +
+// 1e-8 (|S| + |P|) bounds |a32 - (n - O)| / u.  Terms: 3.01u|w|.|e| for the
+// FMA dot, 2.01u X.|e| for the FMA cross, and the input errors |dd| <=
+// 1.01u|d|, |da| <= u Ma, |de| <= u(|e| + 1.01|k| + 1.01|n|) pushed through the
+// trilinear form; the de term multiplies |D x A| <= |w| + u(3.02 X + Y), whence
+// |w| (small when n is near the ray) and the 1e-6 (X + Y) guard in Z2.  The
+// constant is 2^-24 * 1.0234: it covers the O(u^2) terms and the rounding of
+// the bound itself (non-negative terms, ~10 operations).
 struct Filt32Ray {
-    f3 S, d, Sabs, dabs;
+    f3 O, d, Oeff, dabs;  // Oeff = 1.01|O| + 1e-8 (|S| + |P|)
 };
 struct Filt32Vert {
     f3 n, nabs, w, Z1, Z2;
@@ -108,9 +114,13 @@ struct Filt32Vert {
 
 TP_HD Filt32Ray filt32_ray(const d3 &S, const d3 &P) {
     Filt32Ray r;
-    r.S = tof(S);
+    d3 O = {(S.x + P.x) * 0.5, (S.y + P.y) * 0.5, (S.z + P.z) * 0.5};
+    r.O = tof(O);
     r.d = tof(sub(P, S));
-    r.Sabs = fabs3(r.S);
+    f3 Oa = fabs3(r.O);
+    r.Oeff = {fmaf(1.01f, Oa.x, 1e-8f * (float)(fabs(S.x) + fabs(P.x))),
+              fmaf(1.01f, Oa.y, 1e-8f * (float)(fabs(S.y) + fabs(P.y))),
+              fmaf(1.01f, Oa.z, 1e-8f * (float)(fabs(S.z) + fabs(P.z)))};
     r.dabs = fabs3(r.d);
     return r;
 }
@@ -118,15 +128,18 @@ TP_HD Filt32Vert filt32_vert(const Filt32Ray &r, const f3 &n) {
     Filt32Vert v;
     v.n = n;
     v.nabs = fabs3(n);
-    f3 a = sub(n, r.S);
+    f3 a = sub(n, r.O);
     v.w = crossf(r.d, a);
     f3 aabs = fabs3(a);
     f3 X = abscrossf(r.dabs, aabs);
-    f3 Ma = {fmaf(1.01f, v.nabs.x + r.Sabs.x, aabs.x), fmaf(1.01f, v.nabs.y + r.Sabs.y, aabs.y),
-             fmaf(1.01f, v.nabs.z + r.Sabs.z, aabs.z)};
+    f3 Ma = {fmaf(1.01f, v.nabs.x, aabs.x + r.Oeff.x), fmaf(1.01f, v.nabs.y, aabs.y + r.Oeff.y),
+             fmaf(1.01f, v.nabs.z, aabs.z + r.Oeff.z)};
     f3 Y = abscrossf(r.dabs, Ma);
-    v.Z1 = {fmaf(7.05f, X.x, Y.x), fmaf(7.05f, X.y, Y.y), fmaf(7.05f, X.z, Y.z)};
-    v.Z2 = {1.01f * X.x, 1.01f * X.y, 1.01f * X.z};
+    f3 wa = fabs3(v.w);
+    v.Z1 = {fmaf(3.02f, X.x, fmaf(4.01f, wa.x, Y.x)), fmaf(3.02f, X.y, fmaf(4.01f, wa.y, Y.y)),
+            fmaf(3.02f, X.z, fmaf(4.01f, wa.z, Y.z))};
+    v.Z2 = {fmaf(1.01f, wa.x, 1e-6f * (X.x + Y.x)), fmaf(1.01f, wa.y, 1e-6f * (X.y + Y.y)),
+            fmaf(1.01f, wa.z, 1e-6f * (X.z + Y.z))};
     return v;
 }
 // side(n->k): value, and certain sign (+1/-1) or 0 when the bound is not met

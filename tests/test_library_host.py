@@ -159,3 +159,24 @@ def test_topology_validation_errors(tp):
     assert code(vd, np.array([[0, 1, 2, 3], [4, 5, 6, 7]])) == _lib.ERR_NONCONVEX
     # single tet is a valid convex mesh
     assert code(vd[:4], np.array([[0, 1, 2, 3]])) == 0
+
+
+def test_fp32_filter_sound_near_threshold(tp):
+    """Cases packed around the FP32 filter's decision threshold (ray-edge
+    distances 1e-9..1e-4 of the edge length, walk-like magnitudes): every
+    FP32-certain answer equals the exact sign."""
+    rng = np.random.default_rng(23)
+    n = 60000
+    p = rng.uniform(-1, 1, size=(n, 3))
+    L = 10.0 ** rng.uniform(-4.5, -0.5, size=(n, 1))
+    q = p + rng.normal(size=(n, 3)) * L
+    X = p + rng.uniform(-0.2, 1.2, size=(n, 1)) * (q - p)
+    ang = rng.uniform(0, 2 * np.pi, size=n)
+    S = np.stack([4 * np.cos(ang), 4 * np.sin(ang), rng.uniform(-0.3, 0.3, n)], axis=1)
+    off = rng.normal(size=(n, 3))
+    P = S + 2.0 * (X - S) + off * L * 10.0 ** rng.uniform(-9, -4, size=(n, 1))
+    sign, stage = tp.side_signs_host(S, P, p, q)
+    fp32 = np.nonzero(stage == 0)[0]
+    assert fp32.size > 3000 and (stage != 0).sum() > 5000
+    for k in fp32:
+        assert sign[k] == exact.side_sign_int(S[k], P[k], p[k], q[k]), k
