@@ -19,7 +19,8 @@
  * Conventions shared by all calls
  * -------------------------------
  * - A ray is the half-line X(t) = S + t (P - S), t >= 0, from a source S through
- *   a point P (a detector pixel centre).  S must lie outside the mesh.
+ *   a point P (a detector pixel centre).  S may lie anywhere (inside the mesh
+ *   too: only the part of the line with t >= 0 is integrated).
  * - Cone-beam geometry (circular orbit about z, flat detector): for angle theta
  *   S = (dso cos, dso sin, 0), detector centre C = S - dsd (cos, sin, 0),
  *   u axis U = (-sin, cos, 0), v axis V = (0, 0, 1), pixel centre
@@ -37,8 +38,8 @@
  *   mesh with a given (precision, channels) allocates the mesh's workspace
  *   (tetproj_mesh_reserve does that up front, e.g. before CUDA-graph capture).
  *   Argument errors are returned immediately.  Errors met on the device (a walk
- *   that exceeds max_steps, a source inside the mesh) are recorded in the
- *   mesh's counters and reported by tetproj_mesh_stats_read.
+ *   that exceeds max_steps) are recorded in the mesh's counters and reported
+ *   by tetproj_mesh_stats_read; the affected outputs are NaN.
  * - Calls on the same mesh share its workspace and counters: issue them on one
  *   stream (or order them with events).
  */
@@ -63,7 +64,7 @@ typedef int32_t tetproj_status;
 #define TETPROJ_ERR_OOM 7             /* device or host allocation failed             */
 #define TETPROJ_ERR_RAY_LIMIT 8       /* a walk exceeded max_steps (device-side)      */
 #define TETPROJ_ERR_TIMEOUT 9         /* a bounded device wait gave up (device-side)  */
-#define TETPROJ_ERR_SOURCE_INSIDE 10  /* a ray source lies inside the mesh (device)   */
+#define TETPROJ_ERR_SOURCE_INSIDE 10  /* reserved (sources inside the mesh are supported) */
 #define TETPROJ_ERR_TOO_LARGE 11      /* mesh or problem exceeds a documented limit   */
 
 /* precision modes */

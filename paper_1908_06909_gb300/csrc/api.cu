@@ -31,8 +31,16 @@ struct tetproj_mesh {
     // workspace per [precision][channels==4]: tet-ordered operand / accumulator
     void *ws[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int64_t ws_bytes[2][2] = {{0, 0}, {0, 0}};
+    // deferral queue of the filtered walk (see kernels.cu)
+    int64_t *q_ray = nullptr;
+    int32_t *q_skip = nullptr;
+    unsigned long long *q_count = nullptr;
+    int64_t q_cap = 0;
     int64_t base_bytes = 0;
 };
+
+// Largest deferral queue (entries); launches over more rays are chunked.
+static const int64_t kQueueMax = int64_t(1) << 24;
 
 struct tetproj_geometry {
     int device = 0;
@@ -105,6 +113,9 @@ static void mesh_free(tetproj_mesh *m) {
     cudaFree(m->counters);
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) cudaFree(m->ws[i][j]);
+    cudaFree(m->q_ray);
+    cudaFree(m->q_skip);
+    cudaFree(m->q_count);
     delete m;
 }
 
@@ -164,7 +175,7 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *m, tetproj_mesh_info *o
     o->nboundary = m->nb;
     o->nbvh_nodes = m->nnodes;
     o->nflipped = m->nflipped;
-    int64_t b = m->base_bytes;
+    int64_t b = m->base_bytes + m->q_cap * 12 + (m->q_count ? 8 : 0);
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) b += m->ws_bytes[i][j];
     o->device_bytes = b;
@@ -183,11 +194,30 @@ static tetproj_status ensure_ws(tetproj_mesh *m, int precision, int channels) {
     return TETPROJ_OK;
 }
 
+// Deferral queue able to hold one launch chunk of up to min(nrays, kQueueMax) rays.
+static tetproj_status ensure_queue(tetproj_mesh *m, int64_t nrays) {
+    int64_t need = nrays < kQueueMax ? nrays : kQueueMax;
+    need = ((need + 4095) / 4096) * 4096;
+    if (m->q_cap >= need && m->q_count) return TETPROJ_OK;
+    cudaFree(m->q_ray);
+    cudaFree(m->q_skip);
+    m->q_ray = nullptr;
+    m->q_skip = nullptr;
+    m->q_cap = 0;
+    TP_CUDA(cudaMalloc((void **)&m->q_ray, (size_t)need * sizeof(int64_t)));
+    TP_CUDA(cudaMalloc((void **)&m->q_skip, (size_t)need * sizeof(int32_t)));
+    if (!m->q_count) TP_CUDA(cudaMalloc((void **)&m->q_count, sizeof(unsigned long long)));
+    m->q_cap = need;
+    return TETPROJ_OK;
+}
+
 tetproj_status tetproj_mesh_reserve(tetproj_mesh *m, int32_t precision, int32_t channels) {
     if (!m || (precision != TETPROJ_FILTERED && precision != TETPROJ_PLAIN_FP64) ||
         (channels != 1 && channels != 4))
         return TETPROJ_ERR_ARG;
-    return ensure_ws(m, precision, channels);
+    tetproj_status st = ensure_ws(m, precision, channels);
+    if (st == TETPROJ_OK && precision == TETPROJ_FILTERED) st = ensure_queue(m, kQueueMax);
+    return st;
 }
 
 tetproj_status tetproj_mesh_topology_host(const double *V, int64_t nv, const int32_t *T,
@@ -355,9 +385,21 @@ static void set_cone(KParams &p, const tetproj_geometry *g) {
     p.nrays = (int64_t)g->na * g->nu * g->nv;
 }
 
+static tetproj_status attach_queue(tetproj_mesh *m, KParams &p, const tetproj_options &o) {
+    if (o.precision != TETPROJ_FILTERED) return TETPROJ_OK;
+    tetproj_status st = ensure_queue(m, p.nrays);
+    if (st != TETPROJ_OK) return st;
+    p.q_ray = m->q_ray;
+    p.q_skip = m->q_skip;
+    p.q_count = m->q_count;
+    p.q_cap = m->q_cap;
+    return TETPROJ_OK;
+}
+
 static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
                                   const void *mu, void *out, cudaStream_t s) {
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
+    if (st == TETPROJ_OK) st = attach_queue(m, p, o);
     if (st != TETPROJ_OK) return st;
     void *ws = m->ws[o.precision == TETPROJ_PLAIN_FP64][o.channels == 4];
     int f64 = o.precision == TETPROJ_PLAIN_FP64;
@@ -371,6 +413,7 @@ static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_opt
 static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
                                    const void *y, void *mu_out, cudaStream_t s) {
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
+    if (st == TETPROJ_OK) st = attach_queue(m, p, o);
     if (st != TETPROJ_OK) return st;
     void *ws = m->ws[o.precision == TETPROJ_PLAIN_FP64][o.channels == 4];
     int f64 = o.precision == TETPROJ_PLAIN_FP64;
@@ -470,6 +513,8 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
     p.tr_len = out_len;
     p.tr_count = out_count;
     p.max_visits = max_visits;
+    st = attach_queue(m, p, o);
+    if (st != TETPROJ_OK) return st;
     TP_CUDA(launch_walk(p, o.precision, 1, MODE_TRACE, (cudaStream_t)stream));
     return TETPROJ_OK;
 }

@@ -95,7 +95,7 @@ __device__ __forceinline__ bool thread_ray(const KParams &p, int64_t &ray) {
         int t = threadIdx.x;
         if (p.morton) morton_local(t, p.log_tu, p.log_tv, lu, lv);
         else { lu = t & (p.tu - 1); lv = t >> p.log_tu; }
-        int64_t b = blockIdx.x;
+        int64_t b = (int64_t)blockIdx.x + p.block_offset;
         int tid_u = (int)(b % p.tiles_u);
         int64_t rest = b / p.tiles_u;
         int tid_v = (int)(rest % p.tiles_v);
@@ -105,7 +105,7 @@ __device__ __forceinline__ bool thread_ray(const KParams &p, int64_t &ray) {
         ray = ((int64_t)a * p.g.nv + iv) * p.g.nu + iu;
         return true;
     }
-    ray = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    ray = ((int64_t)blockIdx.x + p.block_offset) * blockDim.x + threadIdx.x;
     return ray < p.nrays;
 }
 
@@ -144,7 +144,7 @@ __device__ __forceinline__ int exit_rule(int sa, int sb, int sc) {
 
 // exact-or-symbolic sign of side(S,P,p,q) once the FP64 filter is known to be
 // uncertain; *zero = 1 when the exact value is 0.
-__device__ __noinline__ int side_exact_or_sos(const d3 &S, const d3 &P, const d3 &p, const d3 &q,
+__device__ __noinline__ int side_exact_or_sos(const d3 S, const d3 P, const d3 p, const d3 q,
                                               int *zero, DevCounters *C) {
     atomicAdd(&C->exact, 1ull);
     int s = side_exact_sign(S, P, p, q);
@@ -254,6 +254,8 @@ __device__ __noinline__ int entry_robust(const KParams *p, int64_t ray, int h, i
 // Depth-first, nearer child first, over boxes rounded outward to FP32 and
 // widened per ray by 16u(|S| + mesh radius), with a relative slack on the
 // interval test, so no box holding a face the exact line crosses is culled.
+// The whole LINE is searched (no t >= 0 cut): a source inside the mesh enters
+// through a face behind it, and the walk then clips its segments at t = 0.
 // The top `smem_nodes` nodes (breadth-first numbering) come from shared memory.
 
 __device__ __forceinline__ bool slab(const float4 &lo, const float4 &hi, const f3 &S, const f3 &inv,
@@ -264,7 +266,7 @@ __device__ __forceinline__ bool slab(const float4 &lo, const float4 &hi, const f
     float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
     float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
     tn = tmin;
-    return tmin <= tmax + 1e-5f * fabsf(tmax) + 1e-7f && tmax >= -1e-6f;
+    return tmin <= tmax + 1e-5f * fabsf(tmax) + 1e-7f;
 }
 
 __device__ __forceinline__ f3 safe_inv(const f3 &d) {
@@ -317,34 +319,58 @@ __device__ __forceinline__ void bvh_search(const MeshView &m, const BvhNode *sno
 }
 
 // ======================================================= filtered FP32 walk
+//
+// Two kernels share one body.  The FAST kernel (ROBUST = false) takes only
+// decisions the FP32 filter certifies; a ray that meets an undecided side
+// product (or an undecided entry face) is appended to the deferral queue with
+// the number of segments it has already produced, and stops.  The fast kernel
+// therefore contains no call to the FP64 / exact / symbolic stages and fits in
+// 64 registers without spilling.  The RESUME kernel (ROBUST = true) re-walks
+// each queued ray from its start with the full cascade; every decision the
+// fast kernel took was exact, so the resumed walk visits the same tets in the
+// same order and simply skips the backprojection contributions (or trace
+// entries) that were already written.
 
-template <int C, int MODE>
-__global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KParams p) {
-    extern __shared__ float4 smem[];
-    const int nsm = p.smem_nodes;
-    for (int i = threadIdx.x; i < nsm * 4; i += blockDim.x)
-        smem[i] = __ldg(reinterpret_cast<const float4 *>(p.m.bvh) + i);
-    __syncthreads();
-    const BvhNode *snodes = reinterpret_cast<const BvhNode *>(smem);
+// Warp-aggregated append of (ray, skip) to the deferral queue.  All 32 lanes
+// must call it (converged).
+__device__ __forceinline__ void defer_append(const KParams &p, bool want, int64_t ray, int skip) {
+    unsigned m = __ballot_sync(FULL_MASK, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(p.q_count, (unsigned long long)__popc(m));
+    base = __shfl_sync(FULL_MASK, base, leader);
+    if (want) {
+        unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+        if (slot < (unsigned long long)p.q_cap) {
+            p.q_ray[slot] = ray;
+            p.q_skip[slot] = skip;
+        } else {
+            report_error(p.m.counters, TETPROJ_ERR_TOO_LARGE);  // host sizes chunks <= capacity
+        }
+    }
+}
 
+template <int C, int MODE, bool ROBUST>
+__device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snodes, int nsm,
+                                           int64_t ray, const bool valid, const int skip) {
     LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
-    int64_t ray = 0;
-    const bool valid = thread_ray(p, ray);
     Filt32Ray fr;
-    f3 dhat = {0.f, 0.f, 0.f}, Xin = {0.f, 0.f, 0.f};
+    f3 Xin = {0.f, 0.f, 0.f};
+    float il = 0.f;  // 1 / |d|
     int h = 0, f = 0, err = 0, steps = 0, nvis = 0;
-    bool alive = false;
+    bool alive = false, deferred = false, clip0 = false;
     float acc[C], comp[C], yv[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) { acc[c] = 0.f; comp[c] = 0.f; yv[c] = 0.f; }
 
     if (valid) {
-        cnt.rays = 1;
+        if (!ROBUST) cnt.rays = 1;
         d3 S, P;
         load_ray(p, ray, S, P);
         fr = filt32_ray(S, P);
-        float il = rsqrtf(dotf(fr.d, fr.d));
-        dhat = {fr.d.x * il, fr.d.y * il, fr.d.z * il};
+        il = rsqrtf(dotf(fr.d, fr.d));
         f3 inv = safe_inv(fr.d);
         f3 S32 = tof(S);
         float smax = fmaxf(fmaxf(fabsf(S32.x), fabsf(S32.y)), fabsf(S32.z));
@@ -364,6 +390,9 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
             if (gab > 0 && gbc > 0 && gca > 0) {
                 float iw = 1.f / (sab + sbc + sca);
                 Xin = f3axpy(sca * iw, sub(b, a), f3axpy(sab * iw, sub(c, a), a));
+            } else if (!ROBUST) {
+                deferred = true;  // undecided entry face: finish the ray robustly
+                return true;
             } else {
                 int known[3] = {gab, gbc, gca};
                 d3 X;
@@ -376,13 +405,10 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
             return true;
         });
         if (alive) {
-            cnt.hits = 1;
-            // the entry must lie ahead of the source (source outside the mesh):
-            // t_in = 1/2 + (X_in - O).d / |d|^2 >= 0
-            if (dotf(sub(Xin, fr.O), fr.d) < -(0.5f + 1e-5f) * dotf(fr.d, fr.d)) {
-                err = TETPROJ_ERR_SOURCE_INSIDE;
-                alive = false;
-            }
+            if (!ROBUST) cnt.hits = 1;
+            // entry behind the source (source inside the mesh, or the mesh behind
+            // it): t_in = 1/2 + (X_in - O).d / |d|^2 < 0, clip segments at t = 0
+            clip0 = dotf(sub(Xin, fr.O), fr.d) < -0.5f * dotf(fr.d, fr.d);
         }
         if (MODE == MODE_BWD && alive) {
             const float *y = reinterpret_cast<const float *>(p.in) + ray * C;
@@ -390,17 +416,21 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
             for (int c = 0; c < C; ++c) yv[c] = __ldg(y + c);
         }
     }
-
+    if (ROBUST) cnt.hits = (valid && alive && skip < 0) ? 1 : 0;
+    if (!ROBUST) defer_append(p, deferred, ray, -1);
     flush_counters(p.m.counters, cnt);
     cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+
     const TetRec32 *rec = p.m.rec32;
     const float *mu = reinterpret_cast<const float *>(p.in);
     float *accbuf = reinterpret_cast<float *>(p.out);
     const int lane = threadIdx.x & 31;
 
     while (__any_sync(FULL_MASK, alive)) {
-        const bool did = alive;
+        bool did = alive;
         const int hcur = h;
+        const int seg = steps;
+        bool defer_now = false;
         float len = 0.f;
         if (alive) {
             const float4 *g = reinterpret_cast<const float4 *>(rec + h);
@@ -427,8 +457,8 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
             int ga = filt32_side(Vn, a, sa);
             int gb = filt32_side(Vn, b, sb);
             int gc = filt32_side(Vn, c, sc);
-            int x;
-            f3 Xout;
+            int x = -1;
+            f3 Xout = Xin;
             if ((ga != 0) & (gb != 0) & (gc != 0)) {
                 f3 y, z;
                 float wy, wz;
@@ -439,23 +469,37 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
                 float wn = fmaxf(side_val32(fr, y, z), 0.f);
                 float iw = 1.f / (wn + wy + wz);
                 Xout = f3axpy(wz * iw, sub(z, n), f3axpy(wy * iw, sub(y, n), n));
+            } else if (!ROBUST) {
+                defer_now = true;  // counted by the resume kernel
             } else {
-                cnt.fp64 += (ga == 0) + (gb == 0) + (gc == 0);
+                if (seg >= skip) cnt.fp64 += (ga == 0) + (gb == 0) + (gc == 0);
                 int known[3] = {ga, gb, gc};
                 d3 X;
                 x = step_robust(&p, ray, h, f, known, &X);
                 Xout = tof(X);
             }
-            ++cnt.segs;
-            if (x < 0) {
+            if (defer_now) {
+                alive = false;
+                did = false;
+                deferred = true;
+            } else if (x < 0) {
                 err = TETPROJ_ERR_RAY_LIMIT;
                 alive = false;
+                did = false;
             } else {
+                if (!ROBUST || seg >= skip) ++cnt.segs;
                 int ia, ib, ic;
                 face_triple(f, ia, ib, ic);
                 int loc = x == 0 ? ia : (x == 1 ? ib : ic);
                 int nxt = sel4(adj, loc);
-                len = dotf(sub(Xout, Xin), dhat);
+                len = dotf(sub(Xout, Xin), fr.d) * il;
+                if (clip0) {  // only the part with t >= 0 counts
+                    float dd = dotf(fr.d, fr.d);
+                    float ti = 0.5f + dotf(sub(Xin, fr.O), fr.d) / dd;
+                    float to = 0.5f + dotf(sub(Xout, fr.O), fr.d) / dd;
+                    len = fmaxf(0.f, to - fmaxf(ti, 0.f)) * sqrtf(dd);
+                    clip0 = to < 0.f;
+                }
                 if (MODE == MODE_FWD) {
 #pragma unroll
                     for (int cc = 0; cc < C; ++cc) {  // Kahan
@@ -472,18 +516,20 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
                     }
                     ++nvis;
                 }
+                ++steps;
                 Xin = Xout;
                 if (nxt < 0) {
                     alive = false;
                 } else {
                     h = nxt >> 2;
                     f = nxt & 3;
-                    if (++steps >= p.max_steps) {
+                    if (steps >= p.max_steps) {
                         err = TETPROJ_ERR_RAY_LIMIT;
                         alive = false;
                     }
                 }
             }
+            if (ROBUST && seg < skip) did = false;  // already scattered by the fast kernel
         }
         if (MODE == MODE_BWD) {
             if (p.scatter == TETPROJ_SCATTER_WARP) {
@@ -523,9 +569,10 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
                     atomicAdd(accbuf + hcur, len * yv[0]);
             }
         }
+        if (!ROBUST) defer_append(p, defer_now, ray, seg);
     }
 
-    if (valid) {
+    if (valid && !deferred) {
         if (MODE == MODE_FWD) {
             float *o = reinterpret_cast<float *>(p.out) + ray * C;
             if (C == 4) {
@@ -540,6 +587,39 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
         if (err) report_error(p.m.counters, err);
     }
     flush_counters(p.m.counters, cnt);
+}
+
+__device__ __forceinline__ const BvhNode *stage_bvh_top(const KParams &p, float4 *smem) {
+    for (int i = threadIdx.x; i < p.smem_nodes * 4; i += blockDim.x)
+        smem[i] = __ldg(reinterpret_cast<const float4 *>(p.m.bvh) + i);
+    __syncthreads();
+    return reinterpret_cast<const BvhNode *>(smem);
+}
+
+template <int C, int MODE>
+__global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KParams p) {
+    extern __shared__ float4 smem[];
+    const BvhNode *snodes = stage_bvh_top(p, smem);
+    int64_t ray = 0;
+    const bool valid = thread_ray(p, ray);
+    walk32_ray<C, MODE, false>(p, snodes, p.smem_nodes, ray, valid, 0);
+}
+
+// Resume kernel: grid-stride over the queued rays (count set by k_walk32).
+template <int C, int MODE>
+__global__ void __launch_bounds__(128) k_resume32(const __grid_constant__ KParams p) {
+    extern __shared__ float4 smem[];
+    const BvhNode *snodes = stage_bvh_top(p, smem);
+    const unsigned long long n = *p.q_count;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n;
+         base += stride) {
+        const unsigned long long k = base + threadIdx.x;
+        const bool valid = k < n;
+        int64_t ray = valid ? p.q_ray[k] : 0;
+        int skip = valid ? p.q_skip[k] : 0;  // -1: deferred at the entry search
+        walk32_ray<C, MODE, true>(p, snodes, p.smem_nodes, ray, valid, skip);
+    }
 }
 
 // ========================================================= plain FP64 walk
@@ -565,7 +645,7 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
     const bool valid = thread_ray(p, ray);
     d3 S = {0, 0, 0}, d = {0, 0, 0}, dhat = {0, 0, 0}, Xin = {0, 0, 0};
     int h = 0, f = 0, err = 0, steps = 0, nvis = 0;
-    bool alive = false;
+    bool alive = false, clip0 = false;
     double acc[C], yv[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) { acc[c] = 0.0; yv[c] = 0.0; }
@@ -612,10 +692,7 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
         });
         if (alive) {
             cnt.hits = 1;
-            if (dotd(sub(Xin, S), d) < -1e-12 * dotd(d, d)) {
-                err = TETPROJ_ERR_SOURCE_INSIDE;
-                alive = false;
-            }
+            clip0 = dotd(sub(Xin, S), d) < 0.0;  // entry behind the source: clip at t = 0
         }
         if (MODE == MODE_BWD && alive) {
             const double *y = reinterpret_cast<const double *>(p.in) + ray * C;
@@ -685,6 +762,12 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
                 int loc = x == 0 ? ia : (x == 1 ? ib : ic);
                 int nxt = sel4(adj, loc);
                 len = dotd(sub(Xout, Xin), dhat);
+                if (clip0) {  // only the part with t >= 0 counts
+                    double dd = dotd(d, d);
+                    double ti = dotd(sub(Xin, S), d) / dd, to = dotd(sub(Xout, S), d) / dd;
+                    len = fmax(0.0, to - fmax(ti, 0.0)) * sqrt(dd);
+                    clip0 = to < 0.0;
+                }
                 if (MODE == MODE_FWD) {
 #pragma unroll
                     for (int cc = 0; cc < C; ++cc) acc[cc] = fma(muv[cc], len, acc[cc]);
@@ -805,12 +888,41 @@ __global__ void k_side(const double *S, const double *P, const double *p, const 
 
 // ================================================================ launchers
 
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
 template <int C, int MODE>
-static cudaError_t launch_mode(const KParams &p, int precision, dim3 grid, dim3 block,
+static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks, int threads,
                                size_t smem, cudaStream_t stream) {
-    if (precision == TETPROJ_FILTERED) k_walk32<C, MODE><<<grid, block, smem, stream>>>(p);
-    else k_walk64<C, MODE><<<grid, block, smem, stream>>>(p);
-    return cudaGetLastError();
+    KParams p = p0;
+    if (precision != TETPROJ_FILTERED) {
+        p.block_offset = 0;
+        k_walk64<C, MODE><<<(unsigned)nblocks, threads, smem, stream>>>(p);
+        return cudaGetLastError();
+    }
+    // chunks of at most q_cap rays, each followed by the resume kernel
+    int64_t chunk = p.q_cap / threads;
+    if (chunk < 1) return cudaErrorInvalidValue;
+    const unsigned rgrid = (unsigned)(4 * sm_count());
+    for (int64_t b0 = 0; b0 < nblocks; b0 += chunk) {
+        int64_t nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
+        p.block_offset = b0;
+        cudaError_t e = cudaMemsetAsync(p.q_count, 0, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return e;
+        k_walk32<C, MODE><<<(unsigned)nb, threads, smem, stream>>>(p);
+        k_resume32<C, MODE><<<rgrid, 128, smem, stream>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
@@ -826,17 +938,16 @@ cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
     }
     if (nblocks <= 0) return cudaSuccess;
     if (nblocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)nblocks), block(threads);
     size_t smem = (size_t)p.smem_nodes * sizeof(BvhNode);
     if (mode == MODE_FWD) {
-        return channels == 4 ? launch_mode<4, MODE_FWD>(p, precision, grid, block, smem, stream)
-                             : launch_mode<1, MODE_FWD>(p, precision, grid, block, smem, stream);
+        return channels == 4 ? launch_mode<4, MODE_FWD>(p, precision, nblocks, threads, smem, stream)
+                             : launch_mode<1, MODE_FWD>(p, precision, nblocks, threads, smem, stream);
     }
     if (mode == MODE_BWD) {
-        return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, grid, block, smem, stream)
-                             : launch_mode<1, MODE_BWD>(p, precision, grid, block, smem, stream);
+        return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, nblocks, threads, smem, stream)
+                             : launch_mode<1, MODE_BWD>(p, precision, nblocks, threads, smem, stream);
     }
-    return launch_mode<1, MODE_TRACE>(p, precision, grid, block, smem, stream);
+    return launch_mode<1, MODE_TRACE>(p, precision, nblocks, threads, smem, stream);
 }
 
 cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, int f64,

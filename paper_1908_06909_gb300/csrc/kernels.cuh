@@ -31,6 +31,14 @@ struct KParams {
     int32_t max_steps;
     int32_t scatter;
     int32_t smem_nodes;
+    // chunked launches: first block (cone tiles) or first block of 128 rays
+    int64_t block_offset;
+    // deferral queue of the filtered path (rays whose predicates the FP32
+    // filter could not decide); capacity >= rays per launch chunk
+    int64_t *q_ray;
+    int32_t *q_skip;          // segments already produced, or -1 (entry undecided)
+    unsigned long long *q_count;
+    int64_t q_cap;
 };
 
 // one launch of the walk; returns a cudaError_t

@@ -35,7 +35,7 @@
 //      line, so the walk follows it: no backtracking and no loops.
 //
 // All code here is __host__ __device__ so the host build can be tested on the
-// CPU against exact rationals.  Compile with FMA contraction OFF (nvcc
+// CPU against exact rationals.  Non-inlined functions take points by value.  Compile with FMA contraction OFF (nvcc
 // -fmad=false, gcc -ffp-contract=off): every fused multiply-add below is an
 // explicit fma()/fmaf() call, which the error bounds account for.
 #pragma once
@@ -96,7 +96,7 @@ TP_HD double dotd(const d3 &a, const d3 &b) { return fma(a.x, b.x, fma(a.y, b.y,
 //   Z1 = 3.02 X + Y + 4.01 |w|,   Z2 = 1.01 |w| + 1e-6 (X + Y)
 // with a = n - O, e = k - n, X = |d| x |a| and Y = |d| x Ma, where x is the
 // cross product of absolute values and Ma = |a| + 1.01 (|n| + |O|) +
-// 1e-8 (|S| + |P|) bounds |a32 - (n - O)| / u.  Terms: 3.01u|w|.|e| for the
+// 1e-8 max_i(|S_i| + |P_i|) bounds |a32 - (n - O)| / u.  Terms: 3.01u|w|.|e| for the
 // FMA dot, 2.01u X.|e| for the FMA cross, and the input errors |dd| <=
 // 1.01u|d|, |da| <= u Ma, |de| <= u(|e| + 1.01|k| + 1.01|n|) pushed through the
 // trilinear form; the de term multiplies |D x A| <= |w| + u(3.02 X + Y), whence
@@ -104,7 +104,8 @@ TP_HD double dotd(const d3 &a, const d3 &b) { return fma(a.x, b.x, fma(a.y, b.y,
 // constant is 2^-24 * 1.0234: it covers the O(u^2) terms and the rounding of
 // the bound itself (non-negative terms, ~10 operations).
 struct Filt32Ray {
-    f3 O, d, Oeff, dabs;  // Oeff = 1.01|O| + 1e-8 (|S| + |P|)
+    f3 O, d;     // midpoint and direction, rounded to FP32
+    float Oext;  // 1e-8 max_i(|S_i| + |P_i|): covers fl64 rounding of (S + P)/2
 };
 struct Filt32Vert {
     f3 n, nabs, w, Z1, Z2;
@@ -117,11 +118,8 @@ TP_HD Filt32Ray filt32_ray(const d3 &S, const d3 &P) {
     d3 O = {(S.x + P.x) * 0.5, (S.y + P.y) * 0.5, (S.z + P.z) * 0.5};
     r.O = tof(O);
     r.d = tof(sub(P, S));
-    f3 Oa = fabs3(r.O);
-    r.Oeff = {fmaf(1.01f, Oa.x, 1e-8f * (float)(fabs(S.x) + fabs(P.x))),
-              fmaf(1.01f, Oa.y, 1e-8f * (float)(fabs(S.y) + fabs(P.y))),
-              fmaf(1.01f, Oa.z, 1e-8f * (float)(fabs(S.z) + fabs(P.z)))};
-    r.dabs = fabs3(r.d);
+    double e = fmax(fmax(fabs(S.x) + fabs(P.x), fabs(S.y) + fabs(P.y)), fabs(S.z) + fabs(P.z));
+    r.Oext = 1e-8f * (float)e;
     return r;
 }
 TP_HD Filt32Vert filt32_vert(const Filt32Ray &r, const f3 &n) {
@@ -130,11 +128,12 @@ TP_HD Filt32Vert filt32_vert(const Filt32Ray &r, const f3 &n) {
     v.nabs = fabs3(n);
     f3 a = sub(n, r.O);
     v.w = crossf(r.d, a);
-    f3 aabs = fabs3(a);
-    f3 X = abscrossf(r.dabs, aabs);
-    f3 Ma = {fmaf(1.01f, v.nabs.x, aabs.x + r.Oeff.x), fmaf(1.01f, v.nabs.y, aabs.y + r.Oeff.y),
-             fmaf(1.01f, v.nabs.z, aabs.z + r.Oeff.z)};
-    f3 Y = abscrossf(r.dabs, Ma);
+    f3 aabs = fabs3(a), dabs = fabs3(r.d), Oabs = fabs3(r.O);
+    f3 X = abscrossf(dabs, aabs);
+    f3 Ma = {fmaf(1.01f, v.nabs.x + Oabs.x, aabs.x + r.Oext),
+             fmaf(1.01f, v.nabs.y + Oabs.y, aabs.y + r.Oext),
+             fmaf(1.01f, v.nabs.z + Oabs.z, aabs.z + r.Oext)};
+    f3 Y = abscrossf(dabs, Ma);
     f3 wa = fabs3(v.w);
     v.Z1 = {fmaf(3.02f, X.x, fmaf(4.01f, wa.x, Y.x)), fmaf(3.02f, X.y, fmaf(4.01f, wa.y, Y.y)),
             fmaf(3.02f, X.z, fmaf(4.01f, wa.z, Y.z))};
@@ -255,7 +254,7 @@ TP_HD int exp_minor(double x1, double y1, double x2, double y2, double *h) {
 //   side = -D4 = det3(b,c,d) - det3(a,c,d) + det3(a,b,d) - det3(a,b,c),
 //   det3(x,y,z) = x.z m(y,z) - y.z m(x,z) + z.z m(x,y),  m(x,y) = x.x y.y - y.x x.y,
 // so side is a signed sum of 12 products z * m(.,.) of exact 4-term minors.
-TP_HDN int side_exact_sign(const d3 &a, const d3 &b, const d3 &c, const d3 &d) {
+TP_HDN int side_exact_sign(const d3 a, const d3 b, const d3 c, const d3 d) {
     double m_ab[4], m_ac[4], m_ad[4], m_bc[4], m_bd[4], m_cd[4];
     int n_ab = exp_minor(a.x, b.y, b.x, a.y, m_ab);
     int n_ac = exp_minor(a.x, c.y, c.x, a.y, m_ac);
@@ -284,7 +283,7 @@ TP_HDN int side_exact_sign(const d3 &a, const d3 &b, const d3 &c, const d3 &d) {
 //   O(a, b, c) = (b_i - a_i)(c_j - a_j) - (b_j - a_j)(c_i - a_i)
 //              = m(b, c) - m(a, c) + m(a, b),  m(x, y) = x_i y_j - y_i x_j.
 TP_HD double comp(const d3 &v, int axis) { return axis == 0 ? v.x : (axis == 1 ? v.y : v.z); }
-TP_HDN int orient2d_sign(const d3 &a, const d3 &b, const d3 &c, int i, int j) {
+TP_HDN int orient2d_sign(const d3 a, const d3 b, const d3 c, int i, int j) {
     double ai = comp(a, i), aj = comp(a, j), bi = comp(b, i), bj = comp(b, j);
     double ci = comp(c, i), cj = comp(c, j);
     // FP64 filter: differences (u each), products, subtraction
@@ -305,7 +304,7 @@ TP_HDN int orient2d_sign(const d3 &a, const d3 &b, const d3 &c, int i, int j) {
 
 // Symbolic tie-break for side(S, P, p, q) == 0 exactly (see the header).
 //   O_yz = axes (1,2), O_zx = (2,0), O_xy = (0,1); (p-S)x(q-S) = (O_yz, O_zx, O_xy)(S, p, q).
-TP_HDN int side_sos_sign(const d3 &S, const d3 &P, const d3 &p, const d3 &q) {
+TP_HDN int side_sos_sign(const d3 S, const d3 P, const d3 p, const d3 q) {
     int s;
     // exponents 1, 2, 4: -(p - P) x (q - P)
     if ((s = orient2d_sign(P, p, q, 1, 2)) != 0) return -s;
@@ -326,7 +325,7 @@ TP_HDN int side_sos_sign(const d3 &S, const d3 &P, const d3 &p, const d3 &q) {
 }
 
 // FP64 filter -> exact -> symbolic.  stage: 1 FP64, 2 exact, 3 symbolic.
-TP_HDN int side_sign_robust64(const d3 &S, const d3 &P, const d3 &p, const d3 &q, int *stage) {
+TP_HDN int side_sign_robust64(const d3 S, const d3 P, const d3 p, const d3 q, int *stage) {
     d3 d = sub(P, S);
     Filt64Vert v = filt64_vert(S, d, p);
     double val;
@@ -339,7 +338,7 @@ TP_HDN int side_sign_robust64(const d3 &S, const d3 &P, const d3 &p, const d3 &q
 }
 
 // Full cascade from FP64 inputs (used by the validation entry points).
-TP_HDN int side_sign_cascade(const d3 &S, const d3 &P, const d3 &p, const d3 &q, int *stage) {
+TP_HDN int side_sign_cascade(const d3 S, const d3 P, const d3 p, const d3 q, int *stage) {
     Filt32Ray r = filt32_ray(S, P);
     Filt32Vert v = filt32_vert(r, tof(p));
     float val;
