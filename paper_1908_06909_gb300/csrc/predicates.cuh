@@ -51,6 +51,12 @@
 #define TP_HD inline
 #define TP_HDN static
 #endif
+// Expansion primitives are kept out of line on the device: with nvcc 13.0 the
+// fully inlined exact 2-D orientation of (a, a, c) returned a non-zero sign
+// (the optimiser mis-evaluated the chain of inlined expansion sums; storing
+// the intermediates, or calling the same primitives out of line, gave 0).
+// The device/host cascade comparison test guards this.
+#define TP_EXP TP_HDN
 
 namespace tp {
 
@@ -193,7 +199,7 @@ TP_HD void two_prod(double a, double b, double &p, double &e) {
 
 // h = e + f, zero-eliminating; returns |h|.  Merges by magnitude, then a chain
 // of two-sums (Fast-Expansion-Sum of the 1997 paper).  h may not alias e or f.
-TP_HD int exp_sum(int elen, const double *e, int flen, const double *f, double *h) {
+TP_EXP int exp_sum(int elen, const double *e, int flen, const double *f, double *h) {
     int i = 0, j = 0, n = 0;
     double Q;
     if (elen == 0 && flen == 0) { h[0] = 0.0; return 1; }
@@ -212,7 +218,7 @@ TP_HD int exp_sum(int elen, const double *e, int flen, const double *f, double *
     return n;
 }
 // h = b * e, zero-eliminating (Scale-Expansion); h may not alias e.
-TP_HD int exp_scale(int elen, const double *e, double b, double *h) {
+TP_EXP int exp_scale(int elen, const double *e, double b, double *h) {
     int n = 0;
     double Q, hh;
     two_prod(e[0], b, Q, hh);
@@ -232,21 +238,16 @@ TP_HD int exp_sign(int n, const double *e) {
     double v = e[n - 1];
     return (v > 0.0) - (v < 0.0);
 }
-// x1*y1 - x2*y2 exactly (<= 4 components)
-TP_HD int exp_minor(double x1, double y1, double x2, double y2, double *h) {
-    double a[2], b[2];
-    two_prod(x1, y1, a[1], a[0]);
-    two_prod(x2, y2, b[1], b[0]);
-    b[0] = -b[0];
-    b[1] = -b[1];
-    // a and b are (lo, hi) non-overlapping pairs
-    double aa[2], bb[2];
-    int na = 0, nb = 0;
-    if (a[0] != 0.0) aa[na++] = a[0];
-    if (a[1] != 0.0 || na == 0) aa[na++] = a[1];
-    if (b[0] != 0.0) bb[nb++] = b[0];
-    if (b[1] != 0.0 || nb == 0) bb[nb++] = b[1];
-    return exp_sum(na, aa, nb, bb, h);
+// x1*y1 - x2*y2 exactly (<= 4 components); the subtraction negates an input of
+// the error-free product, which is exact.
+TP_EXP int exp_minor(double x1, double y1, double x2, double y2, double *h) {
+    double ah, al, bh, bl;
+    two_prod(x1, y1, ah, al);
+    two_prod(-x2, y2, bh, bl);
+    const double aa[2] = {al, ah};
+    const double bb[2] = {bl, bh};
+    const int na = (al != 0.0) ? 2 : 1, nb = (bl != 0.0) ? 2 : 1;
+    return exp_sum(na, al != 0.0 ? aa : aa + 1, nb, bl != 0.0 ? bb : bb + 1, h);
 }
 
 // Exact sign of side(S, P, p, q) = det[P-S, p-S, q-S].
@@ -266,17 +267,18 @@ TP_HDN int side_exact_sign(const d3 a, const d3 b, const d3 c, const d3 d) {
     const double *mins[12] = {m_cd, m_bd, m_bc, m_cd, m_ad, m_ac, m_bd, m_ad, m_ab, m_bc, m_ac, m_ab};
     const int lens[12] = {n_cd, n_bd, n_bc, n_cd, n_ad, n_ac, n_bd, n_ad, n_ab, n_bc, n_ac, n_ab};
     const double coef[12] = {b.z, -c.z, d.z, -a.z, c.z, -d.z, a.z, -b.z, d.z, -a.z, b.z, -c.z};
-    double acc[2][104];
-    double prod[8];
-    int cur = 0, nacc = 1;
-    acc[0][0] = 0.0;
-    for (int k = 0; k < 12; ++k) {
-        if (coef[k] == 0.0) continue;
-        int np = exp_scale(lens[k], mins[k], coef[k], prod);
-        nacc = exp_sum(nacc, acc[cur], np, prod, acc[cur ^ 1]);
-        cur ^= 1;
+    // accumulate in two buffers alternating at compile time (no dynamic index)
+    double A[104], B[104], prod[8];
+    int nA = 1, nB = 0, np;
+    A[0] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; k += 2) {
+        np = exp_scale(lens[k], mins[k], coef[k], prod);
+        nB = exp_sum(nA, A, np, prod, B);
+        np = exp_scale(lens[k + 1], mins[k + 1], coef[k + 1], prod);
+        nA = exp_sum(nB, B, np, prod, A);
     }
-    return exp_sign(nacc, acc[cur]);
+    return exp_sign(nA, A);
 }
 
 // Exact sign of the 2-D orientation over axes (i, j):
@@ -293,10 +295,9 @@ TP_HDN int orient2d_sign(const d3 a, const d3 b, const d3 c, int i, int j) {
     if (v > B) return 1;
     if (v < -B) return -1;
     double m1[4], m2[4], m3[4], t[8], r[12];
-    int n1 = exp_minor(bi, cj, ci, bj, m1);
-    int n2 = exp_minor(ai, cj, ci, aj, m2);
-    int n3 = exp_minor(ai, bj, bi, aj, m3);
-    for (int k = 0; k < n2; ++k) m2[k] = -m2[k];
+    int n1 = exp_minor(bi, cj, ci, bj, m1);   //  m(b, c)
+    int n2 = exp_minor(ci, aj, ai, cj, m2);   // -m(a, c)
+    int n3 = exp_minor(ai, bj, bi, aj, m3);   //  m(a, b)
     int nt = exp_sum(n1, m1, n2, m2, t);
     int nr = exp_sum(nt, t, n3, m3, r);
     return exp_sign(nr, r);
