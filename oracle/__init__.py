@@ -55,6 +55,9 @@ def lib():
         L.oracle_forward_rays.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
                                           ctypes.c_int, _c_dp, _c_dp, _c_dp, ctypes.c_int64,
                                           _c_dp, ctypes.c_int]
+        L.oracle_forward_rays_range.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64,
+                                                _c_dp, ctypes.c_int, _c_dp, _c_dp, _c_dp, _c_dp,
+                                                _c_dp, ctypes.c_int64, _c_dp, ctypes.c_int]
         L.oracle_forward_cone.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
@@ -77,7 +80,7 @@ def lib():
         L.oracle_trace_rays.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
                                         _c_dp, ctypes.c_int64, ctypes.c_int64, _c_ip, _c_dp,
                                         _c_dp, _c_lp, _c_dp, _c_ip, ctypes.c_int]
-        for f in ("oracle_forward_rays", "oracle_forward_cone", "oracle_backward_rays",
+        for f in ("oracle_forward_rays", "oracle_forward_rays_range", "oracle_forward_cone", "oracle_backward_rays",
                   "oracle_backward_cone", "oracle_backward_cone_subset", "oracle_trace_rays"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -161,6 +164,45 @@ def forward_rays(verts, tets, mu, S, P, side=None, threads=None):
                                      out.ctypes.data_as(_c_dp), threads or default_threads()),
            "oracle_forward_rays")
     return out[:, 0] if np.asarray(mu).ndim == 1 else out
+
+
+def forward_rays_range(verts, tets, mu, S, P, t0, t1, side=None, threads=None):
+    """b_j restricted to parameters t in [t0_j, t1_j] (t1 may be inf)."""
+    v, vp, t, tp = _mesh(verts, tets)
+    mu2, C = _channels(mu, t.shape[0])
+    m, mp = _d(mu2)
+    s, sp = _d(S)
+    p, pp = _d(P)
+    n = s.shape[0]
+    a0, a0p = _d(np.broadcast_to(np.asarray(t0, float), (n,)))
+    a1, a1p = _d(np.broadcast_to(np.asarray(t1, float), (n,)))
+    w, wp = (None, None) if side is None else _d(side)
+    out = np.empty((n, C))
+    _check(lib().oracle_forward_rays_range(vp, v.shape[0], tp, t.shape[0], mp, C, sp, pp, wp, a0p,
+                                           a1p, n, out.ctypes.data_as(_c_dp),
+                                           threads or default_threads()),
+           "oracle_forward_rays_range")
+    return out[:, 0] if np.asarray(mu).ndim == 1 else out
+
+
+def sos_side_direction():
+    """A concrete direction ordered like the symbolic perturbation of the ray
+    source (e, e^2, e^4): its sign against a plane normal n is that of the first
+    non-zero component of n (for normals with components not below 1e-6 of the
+    leading one)."""
+    return np.array([1.0, 1e-6, 1e-12])
+
+
+def forward_rays_exact_planar(verts, tets, mu, S, P, threads=None):
+    """Integral of rays lying EXACTLY in a face plane, as the limit of the
+    symbolically perturbed line S + (e, e^2, e^4), P + (e^8, ...): on [0, 1) the
+    line sits on the side of the source perturbation, beyond t = 1 (the point P)
+    on the opposite side."""
+    n = np.asarray(S).shape[0]
+    w = np.broadcast_to(sos_side_direction(), (n, 3)).copy()
+    a = forward_rays_range(verts, tets, mu, S, P, 0.0, 1.0, side=w, threads=threads)
+    b = forward_rays_range(verts, tets, mu, S, P, 1.0, np.inf, side=-w, threads=threads)
+    return a + b
 
 
 def forward_cone(verts, tets, mu, geom, ray_idx=None, threads=None):

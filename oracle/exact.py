@@ -266,3 +266,117 @@ def side_sign_int(S, P, p, q) -> int:
     det = (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
            + a[2] * (b[0] * c[1] - b[1] * c[0]))
     return (det > 0) - (det < 0)
+
+
+class DegenerateRay(ValueError):
+    """The ray meets an edge or vertex exactly: crossing faces are not unique."""
+
+
+def ray_integral_exact(verts, tets, mu, S, P, pad=1e-9):
+    """Exact sum_i a_ij mu_i for one ray (Eq. 2) with a_ij from exact integer
+    arithmetic: each tet's crossing points come from barycentric weights given
+    by exact side products (as in plucker_interval), clipped to t >= 0.  Only
+    tets whose bounding box meets the ray (padded) are examined.  Raises
+    DegenerateRay if a crossing is not unique (a zero side product on a crossed
+    face).  Returns a float (the exact rational sum, rounded)."""
+    import math
+    import numpy as np
+    S = np.asarray(S, float)
+    P = np.asarray(P, float)
+    d = P - S
+    V = np.asarray(verts, float)[np.asarray(tets)]          # [nt, 4, 3]
+    lo = V.min(axis=1) - pad
+    hi = V.max(axis=1) + pad
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = np.where(d != 0, 1.0 / np.where(d != 0, d, 1.0), np.inf)
+        t1 = (lo - S) * inv
+        t2 = (hi - S) * inv
+    tmin = np.where(d != 0, np.minimum(t1, t2), np.where((S >= lo) & (S <= hi), -np.inf, np.inf))
+    tmax = np.where(d != 0, np.maximum(t1, t2), np.where((S >= lo) & (S <= hi), np.inf, -np.inf))
+    cand = np.nonzero((tmin.max(axis=1) <= tmax.min(axis=1) * (1 + 1e-12) + 1e-12) &
+                      (tmax.min(axis=1) >= -1e-12))[0]
+    # common integer scaling of every coordinate involved
+    vals = list(S) + list(P) + list(V[cand].reshape(-1))
+    I = _int_scale([float(x) for x in vals])
+    Si, Pi = I[0:3], I[3:6]
+    di = [Pi[k] - Si[k] for k in range(3)]
+    dd = sum(x * x for x in di)
+
+    def det(a, b, c):
+        return (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
+                + a[2] * (b[0] * c[1] - b[1] * c[0]))
+
+    total = Fr(0)
+    for q, i in enumerate(cand):
+        base = 6 + 12 * q
+        v = [I[base + 3 * k: base + 3 * k + 3] for k in range(4)]
+        rel = [[v[k][m] - Si[m] for m in range(3)] for k in range(4)]
+        o = det([v[1][m] - v[0][m] for m in range(3)], [v[2][m] - v[0][m] for m in range(3)],
+                [v[3][m] - v[0][m] for m in range(3)])
+        if o < 0:
+            rel[2], rel[3] = rel[3], rel[2]
+        t_in = t_out = None
+        for f, (ia, ib, ic) in FACE_TRIPLE.items():
+            a, b, c = rel[ia], rel[ib], rel[ic]
+            wc = det(di, a, b)
+            wa = det(di, b, c)
+            wb = det(di, c, a)
+            pos = wa > 0 and wb > 0 and wc > 0
+            neg = wa < 0 and wb < 0 and wc < 0
+            if not (pos or neg):
+                if (wa == 0 or wb == 0 or wc == 0) and \
+                        ((wa >= 0 and wb >= 0 and wc >= 0) or (wa <= 0 and wb <= 0 and wc <= 0)):
+                    if wa or wb or wc:
+                        raise DegenerateRay(int(i))
+                continue
+            W = wa + wb + wc
+            num = sum((wa * a[m] + wb * b[m] + wc * c[m]) * di[m] for m in range(3))
+            t = Fr(num, W * dd)
+            if pos:
+                t_in = t
+            else:
+                t_out = t
+        if t_in is None or t_out is None:
+            continue
+        t0 = max(t_in, Fr(0))
+        if t_out > t0:
+            total += (t_out - t0) * Fr(float(mu[i]))
+    return float(total) * math.sqrt(float(d @ d))
+
+
+def ray_in_face_plane(verts, tets, S, P, pad=1e-9):
+    """True if the line S->P lies exactly in the plane of a face of a tet whose
+    bounding box it meets (exact integer orientation tests)."""
+    import numpy as np
+    S = np.asarray(S, float)
+    P = np.asarray(P, float)
+    V = np.asarray(verts, float)[np.asarray(tets)]
+    lo = V.min(axis=1) - pad
+    hi = V.max(axis=1) + pad
+    d = P - S
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = np.where(d != 0, 1.0 / np.where(d != 0, d, 1.0), np.inf)
+        t1 = (lo - S) * inv
+        t2 = (hi - S) * inv
+    tmin = np.where(d != 0, np.minimum(t1, t2), np.where((S >= lo) & (S <= hi), -np.inf, np.inf))
+    tmax = np.where(d != 0, np.maximum(t1, t2), np.where((S >= lo) & (S <= hi), np.inf, -np.inf))
+    cand = np.nonzero(tmin.max(axis=1) <= tmax.min(axis=1) * (1 + 1e-12) + 1e-12)[0]
+    vals = list(S) + list(P) + list(V[cand].reshape(-1))
+    I = _int_scale([float(x) for x in vals])
+    Si, Pi = I[0:3], I[3:6]
+
+    def det(a, b, c):
+        return (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
+                + a[2] * (b[0] * c[1] - b[1] * c[0]))
+
+    for q in range(cand.size):
+        base = 6 + 12 * q
+        v = [I[base + 3 * k: base + 3 * k + 3] for k in range(4)]
+        for f in range(4):
+            a, b, c = [v[k] for k in range(4) if k != f]
+            e1 = [b[m] - a[m] for m in range(3)]
+            e2 = [c[m] - a[m] for m in range(3)]
+            if det(e1, e2, [Si[m] - a[m] for m in range(3)]) == 0 and \
+                    det(e1, e2, [Pi[m] - a[m] for m in range(3)]) == 0:
+                return True
+    return False

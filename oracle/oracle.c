@@ -111,9 +111,10 @@ static void cross3(const double a[3], const double b[3], double r[3]) {
  * otherwise.  That gives the one-sided limits of the integral.
  */
 #define PLANE_TOL 1e-12
-static int tet_clip(const double v[4][3], const double S[3], const double d[3],
-                    const double *w, double *lo, double *hi, int *planar) {
-    double l = 0.0, h = INFINITY;
+static int tet_clip_range(const double v[4][3], const double S[3], const double d[3],
+                          const double *w, double t0, double t1, double *lo, double *hi,
+                          int *planar) {
+    double l = t0, h = t1;
     int empty = 0;
     *planar = 0;
     double dd = sqrt(dot3(d, d));
@@ -157,6 +158,12 @@ static int tet_clip(const double v[4][3], const double S[3], const double d[3],
     return 1;
 }
 
+/* the half-line t >= 0 */
+static int tet_clip(const double v[4][3], const double S[3], const double d[3],
+                    const double *w, double *lo, double *hi, int *planar) {
+    return tet_clip_range(v, S, d, w, 0.0, INFINITY, lo, hi, planar);
+}
+
 static void load_tet(const double *verts, const int32_t *tets, int64_t i, double v[4][3]) {
     for (int k = 0; k < 4; ++k) {
         const double *p = verts + 3 * (int64_t)tets[4 * i + k];
@@ -197,6 +204,7 @@ typedef struct {
     /* rays: explicit (S, P arrays) or cone-beam (geom + optional index list) */
     const double *S, *P;
     const double *W;      /* per-ray side vectors for one-sided limits, or NULL */
+    const double *T0, *T1; /* per-ray parameter range [T0, T1] (NULL: [0, inf)) */
     const cone_geom *geom;
     const int64_t *ray_idx;
     int64_t ray_begin, ray_end;
@@ -253,13 +261,14 @@ static void *fwd_worker(void *arg) {
         get_ray(jb, k, S, P);
         sub3(P, S, d);
         const double *w = jb->W ? jb->W + 3 * k : NULL;
+        double t0 = jb->T0 ? jb->T0[k] : 0.0, t1 = jb->T1 ? jb->T1[k] : INFINITY;
         double len = sqrt(dot3(d, d));
         for (int c = 0; c < jb->C; ++c) acc[c].s = acc[c].c = 0.0;
         for (int64_t i = 0; i < jb->nt; ++i) {
             double v[4][3], lo, hi;
             int planar;
             load_tet(jb->verts, jb->tets, i, v);
-            if (!tet_clip(v, S, d, w, &lo, &hi, &planar) || !(hi > lo)) continue;
+            if (!tet_clip_range(v, S, d, w, t0, t1, &lo, &hi, &planar) || !(hi > lo)) continue;
             double a = (hi - lo) * len;
             for (int c = 0; c < jb->C; ++c) nadd(&acc[c], a * jb->mu[i * jb->C + c]);
         }
@@ -294,6 +303,20 @@ int oracle_forward_rays(const double *verts, int64_t nv, const int32_t *tets, in
     memset(&p, 0, sizeof(p));
     p.verts = verts; p.tets = tets; p.nt = nt; p.C = C; p.S = S; p.P = P; p.W = W;
     p.mu = mu; p.out = out;
+    return forward_common(&p, nrays, nthreads);
+}
+
+/* b = A mu restricted to the parameter range [T0[j], T1[j]] of each explicit
+ * ray, with optional side vectors W (see tet_clip_range). */
+int oracle_forward_rays_range(const double *verts, int64_t nv, const int32_t *tets, int64_t nt,
+                              const double *mu, int C, const double *S, const double *P,
+                              const double *W, const double *T0, const double *T1,
+                              int64_t nrays, double *out, int nthreads) {
+    (void)nv;
+    job p;
+    memset(&p, 0, sizeof(p));
+    p.verts = verts; p.tets = tets; p.nt = nt; p.C = C; p.S = S; p.P = P; p.W = W;
+    p.T0 = T0; p.T1 = T1; p.mu = mu; p.out = out;
     return forward_common(&p, nrays, nthreads);
 }
 

@@ -143,14 +143,17 @@ __device__ __forceinline__ int exit_rule(int sa, int sb, int sc) {
 // plane) is crossed, in the limit of the perturbed line, at t = 1, i.e. at P.
 
 // exact-or-symbolic sign of side(S,P,p,q) once the FP64 filter is known to be
-// uncertain; *zero = 1 when the exact value is 0.
+// uncertain; *zero = 1 when the exact value is 0, *val = the exact value to a
+// few ulps (the FP64 estimate can be all rounding error here, and the crossing
+// point of a face nearly containing the ray depends on these tiny weights).
 __device__ __noinline__ int side_exact_or_sos(const d3 S, const d3 P, const d3 p, const d3 q,
-                                              int *zero, DevCounters *C) {
+                                              int *zero, double *val, DevCounters *C) {
     atomicAdd(&C->exact, 1ull);
-    int s = side_exact_sign(S, P, p, q);
+    int s = side_exact_sign(S, P, p, q, val);
     if (s != 0) { *zero = 0; return s; }
     atomicAdd(&C->sos, 1ull);
     *zero = 1;
+    *val = 0.0;
     return side_sos_sign(S, P, p, q);
 }
 
@@ -169,32 +172,39 @@ __device__ __noinline__ int step_robust(const KParams *p, int64_t ray, int h, in
     d3 k[3] = {rec64_vertex(r, ia), rec64_vertex(r, ib), rec64_vertex(r, ic)};
     d3 d = sub(P, S);
     Filt64Vert Vn = filt64_vert(S, d, n);
-    double val[3];
+    double val[3], bnd[3];
     int sg[3], zero[3];
     for (int j = 0; j < 3; ++j) {
-        int s = filt64_side(Vn, k[j], val[j]);
+        int s = filt64_side(Vn, k[j], val[j], bnd[j]);
         zero[j] = 0;
         if (known[j] != 0) {
             sg[j] = known[j];
         } else if (s != 0) {
             sg[j] = s;
         } else {
-            sg[j] = side_exact_or_sos(S, P, n, k[j], &zero[j], C);
+            sg[j] = side_exact_or_sos(S, P, n, k[j], &zero[j], &val[j], C);
+            bnd[j] = 0.0;
         }
     }
     int x = exit_rule(sg[0], sg[1], sg[2]);
     if (x < 0) return -1;
     int y = (x + 1) % 3, z = (x + 2) % 3;
+    // weights of the exit face (n, k[y], k[z]): exact values where poorly determined
+    for (int j = y; ; j = z) {
+        if (!zero[j] && fabs(val[j]) < TP_WEIGHT_MARGIN * bnd[j])
+            side_exact_or_sos(S, P, n, k[j], &zero[j], &val[j], C);
+        if (j == z) break;
+    }
     double wy = zero[z] ? 0.0 : fmax(0.0, -val[z]);
     double wz = zero[y] ? 0.0 : fmax(0.0, val[y]);
     Filt64Vert Vy = filt64_vert(S, d, k[y]);
-    double vn;
-    int sn = filt64_side(Vy, k[z], vn);
+    double vn, bn;
+    filt64_side(Vy, k[z], vn, bn);
     double wn = fmax(0.0, vn);
-    if (sn == 0) {
+    if (fabs(vn) < TP_WEIGHT_MARGIN * bn) {
         int zz;
-        side_exact_or_sos(S, P, k[y], k[z], &zz, C);
-        if (zz) wn = 0.0;
+        side_exact_or_sos(S, P, k[y], k[z], &zz, &vn, C);
+        wn = zz ? 0.0 : fmax(0.0, vn);
     }
     double W = wn + wy + wz;
     if (W == 0.0) {
@@ -220,20 +230,26 @@ __device__ __noinline__ int entry_robust(const KParams *p, int64_t ray, int h, i
     face_triple(f, ia, ib, ic);
     d3 v[3] = {rec64_vertex(r, ia), rec64_vertex(r, ib), rec64_vertex(r, ic)};
     d3 d = sub(P, S);
-    double val[3];
+    double val[3], bnd[3];
     int zero[3];
     for (int j = 0; j < 3; ++j) {  // side(v_j -> v_{j+1})
         Filt64Vert Vj = filt64_vert(S, d, v[j]);
-        int s = filt64_side(Vj, v[(j + 1) % 3], val[j]);
+        int s = filt64_side(Vj, v[(j + 1) % 3], val[j], bnd[j]);
         zero[j] = 0;
         if (known[j] != 0) {
             s = known[j];
         } else {
             if (count_fp64) atomicAdd(&C->fp64, 1ull);
-            if (s == 0) s = side_exact_or_sos(S, P, v[j], v[(j + 1) % 3], &zero[j], C);
+            if (s == 0) {
+                s = side_exact_or_sos(S, P, v[j], v[(j + 1) % 3], &zero[j], &val[j], C);
+                bnd[j] = 0.0;
+            }
         }
         if (s < 0) return 0;
     }
+    for (int j = 0; j < 3; ++j)
+        if (!zero[j] && fabs(val[j]) < TP_WEIGHT_MARGIN * bnd[j])
+            side_exact_or_sos(S, P, v[j], v[(j + 1) % 3], &zero[j], &val[j], C);
     // weights: w_a = side(b->c) = val[1], w_b = side(c->a) = val[2], w_c = side(a->b) = val[0]
     double wa = zero[1] ? 0.0 : fmax(0.0, val[1]);
     double wb = zero[2] ? 0.0 : fmax(0.0, val[2]);
@@ -379,15 +395,16 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             const float4 *g = reinterpret_cast<const float4 *>(p.m.bfaces + q);
             float4 A = __ldg(g), B = __ldg(g + 1), Cc = __ldg(g + 2);
             f3 a = {A.x, A.y, A.z}, b = {B.x, B.y, B.z}, c = {Cc.x, Cc.y, Cc.z};
-            float sab, sbc, sca;
-            int gab = filt32_side(filt32_vert(fr, a), b, sab);
+            float sab, sbc, sca, bab, bbc, bca;
+            int gab = filt32_side(filt32_vert(fr, a), b, sab, bab);
             if (gab < 0) return false;
-            int gbc = filt32_side(filt32_vert(fr, b), c, sbc);
+            int gbc = filt32_side(filt32_vert(fr, b), c, sbc, bbc);
             if (gbc < 0) return false;
-            int gca = filt32_side(filt32_vert(fr, c), a, sca);
+            int gca = filt32_side(filt32_vert(fr, c), a, sca, bca);
             if (gca < 0) return false;
             int hf = __float_as_int(A.w);
-            if (gab > 0 && gbc > 0 && gca > 0) {
+            if (gab > 0 && gbc > 0 && gca > 0 &&
+                sab + sbc + sca >= (float)TP_WEIGHT_MARGIN * (bab + bbc + bca)) {
                 float iw = 1.f / (sab + sbc + sca);
                 Xin = f3axpy(sca * iw, sub(b, a), f3axpy(sab * iw, sub(c, a), a));
             } else if (!ROBUST) {
@@ -453,19 +470,24 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             else if (f == 2) { n = v2; a = v0; b = v3; c = v1; }
             else { n = v3; a = v0; b = v1; c = v2; }
             Filt32Vert Vn = filt32_vert(fr, n);
-            float sa, sb, sc;
-            int ga = filt32_side(Vn, a, sa);
-            int gb = filt32_side(Vn, b, sb);
-            int gc = filt32_side(Vn, c, sc);
+            float sa, sb, sc, ba, bb, bc;
+            int ga = filt32_side(Vn, a, sa, ba);
+            int gb = filt32_side(Vn, b, sb, bb);
+            int gc = filt32_side(Vn, c, sc, bc);
             int x = -1;
             f3 Xout = Xin;
-            if ((ga != 0) & (gb != 0) & (gc != 0)) {
-                f3 y, z;
-                float wy, wz;
+            bool fast = (ga != 0) & (gb != 0) & (gc != 0);
+            f3 y, z;
+            float wy, wz, bw;
+            if (fast) {
                 x = exit_rule(ga, gb, gc);
-                if (x == 0) { y = b; z = c; wy = -sc; wz = sb; }
-                else if (x == 1) { y = c; z = a; wy = -sa; wz = sc; }
-                else { y = a; z = b; wy = -sb; wz = sa; }
+                if (x == 0) { y = b; z = c; wy = -sc; wz = sb; bw = bc + bb; }
+                else if (x == 1) { y = c; z = a; wy = -sa; wz = sc; bw = ba + bc; }
+                else { y = a; z = b; wy = -sb; wz = sa; bw = bb + ba; }
+                // the ray nearly lies in the exit face: place the crossing exactly
+                fast = x < 0 || wy + wz >= (float)TP_WEIGHT_MARGIN * bw;
+            }
+            if (fast) {
                 float wn = fmaxf(side_val32(fr, y, z), 0.f);
                 float iw = 1.f / (wn + wy + wz);
                 Xout = f3axpy(wz * iw, sub(z, n), f3axpy(wy * iw, sub(y, n), n));
@@ -668,14 +690,14 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
             int ia, ib, ic;
             face_triple(ff, ia, ib, ic);
             d3 v[3] = {rec64_vertex(r, ia), rec64_vertex(r, ib), rec64_vertex(r, ic)};
-            double val[3];
+            double val[3], bnd[3];
             int known[3];
             bool unsure = false;
             for (int j = 0; j < 3; ++j) {
-                int s = filt64_side(filt64_vert(S, d, v[j]), v[(j + 1) % 3], val[j]);
+                int s = filt64_side(filt64_vert(S, d, v[j]), v[(j + 1) % 3], val[j], bnd[j]);
                 if (s < 0) return false;
                 known[j] = s;
-                unsure |= (s == 0);
+                unsure |= (s == 0) || fabs(val[j]) < TP_WEIGHT_MARGIN * bnd[j];
             }
             if (!unsure) {
                 double W = val[0] + val[1] + val[2], iw = 1.0 / W;
@@ -730,22 +752,27 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
             else if (f == 2) { n = v2; a = v0; b = v3; c = v1; }
             else { n = v3; a = v0; b = v1; c = v2; }
             Filt64Vert Vn = filt64_vert(S, d, n);
-            double sa, sb, sc;
-            int ga = filt64_side(Vn, a, sa);
-            int gb = filt64_side(Vn, b, sb);
-            int gc = filt64_side(Vn, c, sc);
-            int x;
+            double sa, sb, sc, ba, bb, bc;
+            int ga = filt64_side(Vn, a, sa, ba);
+            int gb = filt64_side(Vn, b, sb, bb);
+            int gc = filt64_side(Vn, c, sc, bc);
+            int x = -1;
             d3 Xout;
-            if ((ga != 0) & (gb != 0) & (gc != 0)) {
-                d3 y, z;
-                double wy, wz;
+            bool fast = (ga != 0) & (gb != 0) & (gc != 0);
+            d3 y, z;
+            double wy, wz, bw, wn = 0.0;
+            if (fast) {
                 x = exit_rule(ga, gb, gc);
-                if (x == 0) { y = b; z = c; wy = -sc; wz = sb; }
-                else if (x == 1) { y = c; z = a; wy = -sa; wz = sc; }
-                else { y = a; z = b; wy = -sb; wz = sa; }
-                double vn;
-                filt64_side(filt64_vert(S, d, y), z, vn);
-                double wn = fmax(vn, 0.0);
+                if (x == 0) { y = b; z = c; wy = -sc; wz = sb; bw = bc + bb; }
+                else if (x == 1) { y = c; z = a; wy = -sa; wz = sc; bw = ba + bc; }
+                else { y = a; z = b; wy = -sb; wz = sa; bw = bb + ba; }
+                double vn, bn;
+                filt64_side(filt64_vert(S, d, y), z, vn, bn);
+                wn = fmax(vn, 0.0);
+                // weights near their error bounds: the ray nearly lies in the exit face
+                fast = x < 0 || (wy + wz >= TP_WEIGHT_MARGIN * bw && fabs(vn) >= TP_WEIGHT_MARGIN * bn);
+            }
+            if (fast) {
                 double iw = 1.0 / (wn + wy + wz);
                 Xout = d3axpy(wz * iw, sub(z, n), d3axpy(wy * iw, sub(y, n), n));
             } else {

@@ -147,14 +147,19 @@ TP_HD Filt32Vert filt32_vert(const Filt32Ray &r, const f3 &n) {
             fmaf(1.01f, wa.z, 1e-6f * (X.z + Y.z))};
     return v;
 }
-// side(n->k): value, and certain sign (+1/-1) or 0 when the bound is not met
-TP_HD int filt32_side(const Filt32Vert &v, const f3 &k, float &val) {
+// side(n->k): value, its error bound, and the certain sign (+1/-1) or 0 when
+// |value| does not exceed the bound
+TP_HD int filt32_side(const Filt32Vert &v, const f3 &k, float &val, float &B) {
     f3 e = sub(k, v.n);
     val = dotf(v.w, e);
     f3 kabs = fabs3(k);
     f3 kn = {kabs.x + v.nabs.x, kabs.y + v.nabs.y, kabs.z + v.nabs.z};
-    float B = fmaf(TP_FILT32_U, dotf(v.Z1, fabs3(e)) + dotf(v.Z2, kn), TP_FILT32_TINY);
+    B = fmaf(TP_FILT32_U, dotf(v.Z1, fabs3(e)) + dotf(v.Z2, kn), TP_FILT32_TINY);
     return (val > B) - (val < -B);
+}
+TP_HD int filt32_side(const Filt32Vert &v, const f3 &k, float &val) {
+    float B;
+    return filt32_side(v, k, val, B);
 }
 
 // ------------------------------------------------------------------ FP64 stage
@@ -175,12 +180,22 @@ TP_HD Filt64Vert filt64_vert(const d3 &S, const d3 &d, const d3 &n) {
     v.X = abscrossd(dabs(d), dabs(a));
     return v;
 }
-TP_HD int filt64_side(const Filt64Vert &v, const d3 &k, double &val) {
+TP_HD int filt64_side(const Filt64Vert &v, const d3 &k, double &val, double &B) {
     d3 e = sub(k, v.n);
     val = dotd(v.w, e);
-    double B = fma(TP_FILT64_U, dotd(v.X, dabs(e)), TP_FILT64_TINY);
+    B = fma(TP_FILT64_U, dotd(v.X, dabs(e)), TP_FILT64_TINY);
     return (val > B) - (val < -B);
 }
+TP_HD int filt64_side(const Filt64Vert &v, const d3 &k, double &val) {
+    double B;
+    return filt64_side(v, k, val, B);
+}
+
+// A barycentric weight is used as computed only when it exceeds its error
+// bound by this factor; otherwise the crossing point it helps place is
+// ill-conditioned (the ray nearly lies in the face) and the exact value is
+// taken instead.
+#define TP_WEIGHT_MARGIN 128.0
 
 // ------------------------------------------------------- exact arithmetic
 // An expansion is an array of doubles, non-overlapping, increasing magnitude;
@@ -238,6 +253,13 @@ TP_HD int exp_sign(int n, const double *e) {
     double v = e[n - 1];
     return (v > 0.0) - (v < 0.0);
 }
+// The expansion's value rounded to double: summing its non-overlapping
+// components from the smallest up gives it to a few ulps.
+TP_HD double exp_approx(int n, const double *e) {
+    double v = 0.0;
+    for (int k = 0; k < n; ++k) v += e[k];
+    return v;
+}
 // x1*y1 - x2*y2 exactly (<= 4 components); the subtraction negates an input of
 // the error-free product, which is exact.
 TP_EXP int exp_minor(double x1, double y1, double x2, double y2, double *h) {
@@ -250,12 +272,14 @@ TP_EXP int exp_minor(double x1, double y1, double x2, double y2, double *h) {
     return exp_sum(na, al != 0.0 ? aa : aa + 1, nb, bl != 0.0 ? bb : bb + 1, h);
 }
 
-// Exact sign of side(S, P, p, q) = det[P-S, p-S, q-S].
+// Exact sign of side(S, P, p, q) = det[P-S, p-S, q-S]; *approx (if given)
+// receives its value to a few ulps (used as a barycentric weight when the
+// FP64 estimate is below its own error bound).
 // With rows a=S, b=P, c=p, d=q and the 4x4 determinant D4 of rows (x, 1):
 //   side = -D4 = det3(b,c,d) - det3(a,c,d) + det3(a,b,d) - det3(a,b,c),
 //   det3(x,y,z) = x.z m(y,z) - y.z m(x,z) + z.z m(x,y),  m(x,y) = x.x y.y - y.x x.y,
 // so side is a signed sum of 12 products z * m(.,.) of exact 4-term minors.
-TP_HDN int side_exact_sign(const d3 a, const d3 b, const d3 c, const d3 d) {
+TP_HDN int side_exact_sign(const d3 a, const d3 b, const d3 c, const d3 d, double *approx = nullptr) {
     double m_ab[4], m_ac[4], m_ad[4], m_bc[4], m_bd[4], m_cd[4];
     int n_ab = exp_minor(a.x, b.y, b.x, a.y, m_ab);
     int n_ac = exp_minor(a.x, c.y, c.x, a.y, m_ac);
@@ -278,6 +302,7 @@ TP_HDN int side_exact_sign(const d3 a, const d3 b, const d3 c, const d3 d) {
         np = exp_scale(lens[k + 1], mins[k + 1], coef[k + 1], prod);
         nA = exp_sum(nB, B, np, prod, A);
     }
+    if (approx) *approx = exp_approx(nA, A);
     return exp_sign(nA, A);
 }
 
