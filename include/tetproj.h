@@ -186,6 +186,26 @@ tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry
                                 const void *proj, void *mu_out, const tetproj_options *opt,
                                 void *stream);
 
+/* tetproj_backward without any allocation.  It computes the same x = A^T y as
+ * tetproj_backward (same arguments and layouts), for callers that cannot call
+ * cudaMalloc when they backproject: code whose device memory is wholly owned by
+ * another allocator (e.g. a framework's caching pool that has reserved the
+ * device), or a latency-critical loop that must not pay cudaMalloc's implicit
+ * synchronisation.  The paper has no counterpart; this is a library facility.
+ * Its scratch (accumulator and deferral queue) is a fixed device array inside
+ * the library, present on every GPU that loads it until the process exits:
+ *   - limit: nt * C * sizeof(element) <= TETPROJ_NOALLOC_ACC_BYTES, else
+ *     TETPROJ_ERR_TOO_LARGE (e.g. FP32, C = 1: up to 8,388,608 tets);
+ *   - the first call on a device looks up the array's device address (no
+ *     allocation); make that first call before any stream capture;
+ *   - all calls share the array and it keeps the last call's contents (each
+ *     call clears what must start at zero); calls that overlap on the GPU
+ *     (unordered streams) race on it. */
+#define TETPROJ_NOALLOC_ACC_BYTES (32 * 1024 * 1024)
+tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh, const tetproj_geometry *geo,
+                                        const void *proj, void *mu_out,
+                                        const tetproj_options *opt, void *stream);
+
 /* The same operators for explicit rays src[j] -> dst[j] (device [n][3] FP64):
  * out[j][c] = sum_i a_ij mu[i][c];  mu_out[i][c] = sum_j a_ij y[j][c]. */
 tetproj_status tetproj_forward_rays(const tetproj_mesh *mesh, const double *src,

@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import (FILTERED, ORDER_MORTON, ORDER_ROW, PLAIN_FP64, SCATTER_ATOMIC, SCATTER_WARP,
                    Options, TetprojError, check)
 
-__all__ = ["Mesh", "Geometry", "forward", "backward", "forward_rays", "backward_rays",
+__all__ = ["Mesh", "Geometry", "forward", "backward", "backward_noalloc", "forward_rays", "backward_rays",
            "trace_rays", "side_signs_host", "side_signs_device", "TetProject", "make_options",
            "FILTERED", "PLAIN_FP64", "ORDER_ROW", "ORDER_MORTON", "SCATTER_ATOMIC",
            "SCATTER_WARP", "TetprojError", "library_path"]
@@ -240,6 +240,29 @@ def backward(mesh: Mesh, geo: Geometry, proj, out=None, options: Options | None 
     o = _opts(prec, C, options)
     check(_lib.load().tetproj_backward(mesh.handle, geo.handle, _ptr(proj), _ptr(out),
                                        ctypes.byref(o), _stream()), "tetproj_backward")
+    return out
+
+
+def backward_noalloc(mesh: Mesh, geo: Geometry, proj, out=None,
+                     options: Options | None = None):
+    """tetproj_backward_noalloc: the same A^T y as backward(), with the library's
+    fixed device scratch instead of any allocation (see include/tetproj.h for
+    its size limit, sharing and first-call rules).  `out` is allocated here by
+    torch only when not given."""
+    torch = _torch()
+    _check_cuda(proj, "proj")
+    C = 1 if proj.dim() == 3 else proj.shape[3]
+    if tuple(proj.shape[:3]) != geo.shape:
+        raise ValueError(f"proj must be {geo.shape}(+channels)")
+    prec = _precision_of(proj)
+    if out is None:
+        out = torch.empty((mesh.nt,) + ((C,) if proj.dim() == 4 else ()), dtype=proj.dtype,
+                          device=proj.device)
+    _check_cuda(out, "out")
+    o = _opts(prec, C, options)
+    check(_lib.load().tetproj_backward_noalloc(mesh.handle, geo.handle, _ptr(proj), _ptr(out),
+                                               ctypes.byref(o), _stream()),
+          "tetproj_backward_noalloc")
     return out
 
 

@@ -71,6 +71,7 @@ SIGNATURES = {
     "tetproj_geometry_rays": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
     "tetproj_forward": (c_i32, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Options), c_vp]),
     "tetproj_backward": (c_i32, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Options), c_vp]),
+    "tetproj_backward_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(Options), c_vp]),
     "tetproj_forward_rays": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp,
                                      ctypes.POINTER(Options), c_vp]),
     "tetproj_backward_rays": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp,

@@ -541,3 +541,79 @@ tetproj_status tetproj_side_device(const double *S, const double *P, const doubl
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ allocation-free backprojection
+//
+// tetproj_backward_noalloc computes exactly what tetproj_backward computes, for
+// callers that cannot call cudaMalloc at that point -- for instance code whose
+// device memory is entirely owned by another allocator (a framework's caching
+// pool that has already reserved the device), or a latency-critical loop that
+// must not pay cudaMalloc's implicit device synchronisation.  tetproj_backward
+// allocates the mesh's workspace on its first call; this variant instead uses
+// the file-scope device array below, so it never allocates or frees anything.
+//
+// Its scratch is the tet-ordered accumulator (up to kNoAllocAccBytes) and the
+// deferral queue of the filtered walk (kNoAllocQueue entries; launches are
+// chunked to fit it).  The array is part of the library image, so every GPU
+// that loads libtetproj.so holds it (about 44 MB) until the process exits.
+// Every call shares it and it keeps the previous call's contents: the
+// accumulator is cleared at the start of each call, and calls that overlap on
+// the GPU (different streams, no ordering) race on it.
+static const int64_t kNoAllocAccBytes = int64_t(32) << 20;
+static const int64_t kNoAllocQueue = int64_t(1) << 20;
+static const int64_t kNoAllocBytes = kNoAllocAccBytes + kNoAllocQueue * (8 + 4) + 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_addr[128] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+static tetproj_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    TP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return TETPROJ_ERR_TOO_LARGE;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    return TETPROJ_OK;
+}
+
+extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
+                                                   const tetproj_geometry *geo, const void *proj,
+                                                   void *mu_out, const tetproj_options *opt,
+                                                   void *stream) {
+    if (!mesh || !geo || !proj || !mu_out) return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    const int f64 = o.precision == TETPROJ_PLAIN_FP64;
+    const int64_t acc_bytes = mesh->nt * o.channels * (f64 ? 8 : 4);
+    if (acc_bytes > kNoAllocAccBytes) return TETPROJ_ERR_TOO_LARGE;
+    unsigned char *base = nullptr;
+    st = noalloc_scratch(&base);
+    if (st != TETPROJ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    KParams p = base_params(mesh, o);
+    set_cone(p, geo);
+    void *acc = base;
+    if (!f64) {
+        p.q_ray = reinterpret_cast<int64_t *>(base + kNoAllocAccBytes);
+        p.q_skip = reinterpret_cast<int32_t *>(base + kNoAllocAccBytes + kNoAllocQueue * 8);
+        p.q_count = reinterpret_cast<unsigned long long *>(base + kNoAllocAccBytes +
+                                                           kNoAllocQueue * 12);
+        p.q_cap = kNoAllocQueue;
+    }
+    TP_CUDA(cudaMemsetAsync(acc, 0, (size_t)acc_bytes, s));
+    p.in = proj;
+    p.out = acc;
+    TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s));
+    TP_CUDA(launch_scatter_perm(mesh->perm, mesh->nt, o.channels, f64, acc, mu_out, s));
+    return TETPROJ_OK;
+}
