@@ -14,10 +14,9 @@ side(S, P, p, q)
 side_sos(S, P, p, q)
     Sign of ``side`` for the symbolically perturbed line through
     S + (e, e^2, e^4) and P + (e^8, e^16, e^32), e -> 0+.  This is the tie-break
-    used where the paper only says that zero-length intersections need a check
-    (Alg. 2, "if t2 = t1 check if they need to be swapped"): perturbing the
-    *line*, not the vertices, makes every tet see the same perturbed ray, so
-    the walk can neither leak nor loop.
+    used where the paper only asks for an unspecified check on zero-length
+    intersections (Alg. 2): perturbing the *line*, not the vertices, makes every
+    tet see the same perturbed ray, so the walk can neither leak nor loop.
 side_sos_bruteforce(S, P, p, q, eps)
     Sign of the exact determinant for that perturbed line at a concrete tiny
     rational eps; pins ``side_sos``.

@@ -5,9 +5,9 @@ parameters and explicit rays.  It holds none of the projector arithmetic
 (no chord lengths, no traversal, no predicates), so both the CPU oracle and
 the CUDA path can consume the same arrays without sharing method code.
 
-The paper benchmarks on "regular meshes that are then triangulated"
-(Sec. III-D, performance figures) and on a high-aspect-ratio Delaunay mesh
-(Sec. III-C, floating point errors).  Neither mesh ships with the paper, so
+The paper times its kernels on voxel grids split into tetrahedra (Sec. III-D,
+performance figures) and shows precision failures on a Delaunay mesh with
+badly shaped tets (Sec. III-C, floating point errors).  Neither mesh ships with the paper, so
 the stand-ins are Kuhn (Freudenthal) splits of the cube [-1, 1]^3:
 
 * ``kuhn_cube(n)``: n^3 cells, each split into 6 tets along its v000->v111
