@@ -103,6 +103,7 @@ typedef struct tetproj_stats {
     int64_t sos;         /* ... that were exactly zero (symbolic tie-break used)        */
     int64_t bvh_nodes;   /* BVH boxes tested by entry searches                         */
     int64_t bvh_faces;   /* boundary faces tested by entry searches                    */
+    int64_t deferred;    /* rays the fast FP32 walk handed to the robust resume walk   */
     int32_t error;       /* first device-side error code, 0 if none                    */
     int32_t error_count; /* rays that hit a device-side error                          */
 } tetproj_stats;

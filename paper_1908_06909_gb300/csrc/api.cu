@@ -32,15 +32,14 @@ struct tetproj_mesh {
     void *ws[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int64_t ws_bytes[2][2] = {{0, 0}, {0, 0}};
     // deferral queue of the filtered walk (see kernels.cu)
-    int64_t *q_ray = nullptr;
-    int32_t *q_skip = nullptr;
+    QEntry *q = nullptr;
     unsigned long long *q_count = nullptr;
     int64_t q_cap = 0;
     int64_t base_bytes = 0;
 };
 
-// Largest deferral queue (entries); launches over more rays are chunked.
-static const int64_t kQueueMax = int64_t(1) << 24;
+// Largest deferral queue (entries of 64 B); launches over more rays are chunked.
+static const int64_t kQueueMax = int64_t(1) << 23;
 
 struct tetproj_geometry {
     int device = 0;
@@ -113,8 +112,7 @@ static void mesh_free(tetproj_mesh *m) {
     cudaFree(m->counters);
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) cudaFree(m->ws[i][j]);
-    cudaFree(m->q_ray);
-    cudaFree(m->q_skip);
+    cudaFree(m->q);
     cudaFree(m->q_count);
     delete m;
 }
@@ -175,7 +173,7 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *m, tetproj_mesh_info *o
     o->nboundary = m->nb;
     o->nbvh_nodes = m->nnodes;
     o->nflipped = m->nflipped;
-    int64_t b = m->base_bytes + m->q_cap * 12 + (m->q_count ? 8 : 0);
+    int64_t b = m->base_bytes + m->q_cap * (int64_t)sizeof(QEntry) + (m->q_count ? 8 : 0);
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) b += m->ws_bytes[i][j];
     o->device_bytes = b;
@@ -199,13 +197,10 @@ static tetproj_status ensure_queue(tetproj_mesh *m, int64_t nrays) {
     int64_t need = nrays < kQueueMax ? nrays : kQueueMax;
     need = ((need + 4095) / 4096) * 4096;
     if (m->q_cap >= need && m->q_count) return TETPROJ_OK;
-    cudaFree(m->q_ray);
-    cudaFree(m->q_skip);
-    m->q_ray = nullptr;
-    m->q_skip = nullptr;
+    cudaFree(m->q);
+    m->q = nullptr;
     m->q_cap = 0;
-    TP_CUDA(cudaMalloc((void **)&m->q_ray, (size_t)need * sizeof(int64_t)));
-    TP_CUDA(cudaMalloc((void **)&m->q_skip, (size_t)need * sizeof(int32_t)));
+    TP_CUDA(cudaMalloc((void **)&m->q, (size_t)need * sizeof(QEntry)));
     if (!m->q_count) TP_CUDA(cudaMalloc((void **)&m->q_count, sizeof(unsigned long long)));
     m->q_cap = need;
     return TETPROJ_OK;
@@ -250,6 +245,7 @@ tetproj_status tetproj_mesh_stats_read(tetproj_mesh *m, void *stream, tetproj_st
     o->sos = (int64_t)c.sos;
     o->bvh_nodes = (int64_t)c.bvh_nodes;
     o->bvh_faces = (int64_t)c.bvh_faces;
+    o->deferred = (int64_t)c.deferred;
     o->error = c.error;
     o->error_count = c.error_count;
     return TETPROJ_OK;
@@ -389,8 +385,7 @@ static tetproj_status attach_queue(tetproj_mesh *m, KParams &p, const tetproj_op
     if (o.precision != TETPROJ_FILTERED) return TETPROJ_OK;
     tetproj_status st = ensure_queue(m, p.nrays);
     if (st != TETPROJ_OK) return st;
-    p.q_ray = m->q_ray;
-    p.q_skip = m->q_skip;
+    p.q = m->q;
     p.q_count = m->q_count;
     p.q_cap = m->q_cap;
     return TETPROJ_OK;
@@ -555,13 +550,13 @@ tetproj_status tetproj_side_device(const double *S, const double *P, const doubl
 // Its scratch is the tet-ordered accumulator (up to kNoAllocAccBytes) and the
 // deferral queue of the filtered walk (kNoAllocQueue entries; launches are
 // chunked to fit it).  The array is part of the library image, so every GPU
-// that loads libtetproj.so holds it (about 44 MB) until the process exits.
+// that loads libtetproj.so holds it (48 MB) until the process exits.
 // Every call shares it and it keeps the previous call's contents: the
 // accumulator is cleared at the start of each call, and calls that overlap on
 // the GPU (different streams, no ordering) race on it.
 static const int64_t kNoAllocAccBytes = int64_t(32) << 20;
-static const int64_t kNoAllocQueue = int64_t(1) << 20;
-static const int64_t kNoAllocBytes = kNoAllocAccBytes + kNoAllocQueue * (8 + 4) + 256;
+static const int64_t kNoAllocQueue = int64_t(1) << 18;
+static const int64_t kNoAllocBytes = kNoAllocAccBytes + kNoAllocQueue * (int64_t)sizeof(QEntry) + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 static std::mutex g_noalloc_mutex;
@@ -604,10 +599,9 @@ extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
     set_cone(p, geo);
     void *acc = base;
     if (!f64) {
-        p.q_ray = reinterpret_cast<int64_t *>(base + kNoAllocAccBytes);
-        p.q_skip = reinterpret_cast<int32_t *>(base + kNoAllocAccBytes + kNoAllocQueue * 8);
-        p.q_count = reinterpret_cast<unsigned long long *>(base + kNoAllocAccBytes +
-                                                           kNoAllocQueue * 12);
+        p.q = reinterpret_cast<QEntry *>(base + kNoAllocAccBytes);
+        p.q_count = reinterpret_cast<unsigned long long *>(
+            base + kNoAllocAccBytes + kNoAllocQueue * (int64_t)sizeof(QEntry));
         p.q_cap = kNoAllocQueue;
     }
     TP_CUDA(cudaMemsetAsync(acc, 0, (size_t)acc_bytes, s));

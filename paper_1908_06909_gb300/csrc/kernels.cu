@@ -118,9 +118,6 @@ __device__ __forceinline__ f3 f3axpy(float s, const f3 &x, const f3 &y) {
 __device__ __forceinline__ d3 d3axpy(double s, const d3 &x, const d3 &y) {
     return {fma(s, x.x, y.x), fma(s, x.y, y.y), fma(s, x.z, y.z)};
 }
-__device__ __forceinline__ float side_val32(const Filt32Ray &r, const f3 &y, const f3 &z) {
-    return dotf(crossf(r.d, sub(y, r.O)), sub(z, y));
-}
 __device__ __forceinline__ int sel4(const int4 &v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
@@ -347,9 +344,12 @@ __device__ __forceinline__ void bvh_search(const MeshView &m, const BvhNode *sno
 // same order and simply skips the backprojection contributions (or trace
 // entries) that were already written.
 
-// Warp-aggregated append of (ray, skip) to the deferral queue.  All 32 lanes
-// must call it (converged).
-__device__ __forceinline__ void defer_append(const KParams &p, bool want, int64_t ray, int skip) {
+// Warp-aggregated append to the deferral queue.  All 32 lanes must call it
+// (converged); lanes with want = true write their entry.
+template <int C>
+__device__ __forceinline__ void defer_append(const KParams &p, bool want, int64_t ray, int h,
+                                             int fs, const f3 &X, int nvis, const float *acc,
+                                             const float *comp) {
     unsigned m = __ballot_sync(FULL_MASK, want);
     if (!m) return;
     const int lane = threadIdx.x & 31;
@@ -360,17 +360,26 @@ __device__ __forceinline__ void defer_append(const KParams &p, bool want, int64_
     if (want) {
         unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
         if (slot < (unsigned long long)p.q_cap) {
-            p.q_ray[slot] = ray;
-            p.q_skip[slot] = skip;
+            QEntry *e = p.q + slot;
+            e->ray = ray;
+            e->h = h;
+            e->fs = fs;
+            e->x = make_float4(X.x, X.y, X.z, __int_as_float(nvis));
+            e->acc = make_float4(acc[0], acc[1 % C], acc[2 % C], acc[3 % C]);
+            e->comp = make_float4(comp[0], comp[1 % C], comp[2 % C], comp[3 % C]);
         } else {
             report_error(p.m.counters, TETPROJ_ERR_TOO_LARGE);  // host sizes chunks <= capacity
         }
     }
 }
 
+// One filtered walk.  Fast kernel (ROBUST = false): `valid` rays start from
+// scratch.  Resume kernel (ROBUST = true): `qe` is the ray's queue entry; the
+// walk continues from the saved state (or from the entry search when the ray
+// was deferred there).
 template <int C, int MODE, bool ROBUST>
 __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snodes, int nsm,
-                                           int64_t ray, const bool valid, const int skip) {
+                                           int64_t ray, const bool valid, const QEntry *qe) {
     LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     Filt32Ray fr;
     f3 Xin = {0.f, 0.f, 0.f};
@@ -382,50 +391,69 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
     for (int c = 0; c < C; ++c) { acc[c] = 0.f; comp[c] = 0.f; yv[c] = 0.f; }
 
     if (valid) {
-        if (!ROBUST) cnt.rays = 1;
         d3 S, P;
         load_ray(p, ray, S, P);
         fr = filt32_ray(S, P);
         il = rsqrtf(dotf(fr.d, fr.d));
-        f3 inv = safe_inv(fr.d);
-        f3 S32 = tof(S);
-        float smax = fmaxf(fmaxf(fabsf(S32.x), fabsf(S32.y)), fabsf(S32.z));
-        float margin = 16.f * 5.9604645e-8f * (smax + p.m.radius);
-        bvh_search(p.m, snodes, nsm, S32, inv, margin, cnt, [&](int q) -> bool {
-            const float4 *g = reinterpret_cast<const float4 *>(p.m.bfaces + q);
-            float4 A = __ldg(g), B = __ldg(g + 1), Cc = __ldg(g + 2);
-            f3 a = {A.x, A.y, A.z}, b = {B.x, B.y, B.z}, c = {Cc.x, Cc.y, Cc.z};
-            float sab, sbc, sca, bab, bbc, bca;
-            int gab = filt32_side(filt32_vert(fr, a), b, sab, bab);
-            if (gab < 0) return false;
-            int gbc = filt32_side(filt32_vert(fr, b), c, sbc, bbc);
-            if (gbc < 0) return false;
-            int gca = filt32_side(filt32_vert(fr, c), a, sca, bca);
-            if (gca < 0) return false;
-            int hf = __float_as_int(A.w);
-            if (gab > 0 && gbc > 0 && gca > 0 &&
-                sab + sbc + sca >= (float)TP_WEIGHT_MARGIN * (bab + bbc + bca)) {
-                float iw = 1.f / (sab + sbc + sca);
-                Xin = f3axpy(sca * iw, sub(b, a), f3axpy(sab * iw, sub(c, a), a));
-            } else if (!ROBUST) {
-                deferred = true;  // undecided entry face: finish the ray robustly
+        const bool from_entry = !ROBUST || qe->fs < 0;
+        if (!ROBUST) cnt.rays = 1;
+        if (from_entry) {
+            f3 inv = safe_inv(fr.d);
+            f3 S32 = tof(S);
+            float smax = fmaxf(fmaxf(fabsf(S32.x), fabsf(S32.y)), fabsf(S32.z));
+            float margin = 16.f * 5.9604645e-8f * (smax + p.m.radius);
+            bvh_search(p.m, snodes, nsm, S32, inv, margin, cnt, [&](int q) -> bool {
+                const float4 *g = reinterpret_cast<const float4 *>(p.m.bfaces + q);
+                float4 A = __ldg(g), B = __ldg(g + 1), Cc = __ldg(g + 2);
+                f3 a = {A.x, A.y, A.z}, b = {B.x, B.y, B.z}, c = {Cc.x, Cc.y, Cc.z};
+                float sab, sbc, sca, bab, bbc, bca;
+                int gab = filt32_side(filt32_vert(fr, a), b, sab, bab);
+                if (gab < 0) return false;
+                int gbc = filt32_side(filt32_vert(fr, b), c, sbc, bbc);
+                if (gbc < 0) return false;
+                int gca = filt32_side(filt32_vert(fr, c), a, sca, bca);
+                if (gca < 0) return false;
+                int hf = __float_as_int(A.w);
+                if (gab > 0 && gbc > 0 && gca > 0 &&
+                    sab + sbc + sca >= (float)TP_WEIGHT_MARGIN * (bab + bbc + bca)) {
+                    float iw = __frcp_rn(sab + sbc + sca);
+                    Xin = f3axpy(sca * iw, sub(b, a), f3axpy(sab * iw, sub(c, a), a));
+                } else if (!ROBUST) {
+                    deferred = true;  // undecided entry face: finish the ray robustly
+                    return true;
+                } else {
+                    int known[3] = {gab, gbc, gca};
+                    d3 X;
+                    if (!entry_robust(&p, ray, hf >> 2, hf & 3, known, &X, 1)) return false;
+                    Xin = tof(X);
+                }
+                h = hf >> 2;
+                f = hf & 3;
+                alive = true;
                 return true;
-            } else {
-                int known[3] = {gab, gbc, gca};
-                d3 X;
-                if (!entry_robust(&p, ray, hf >> 2, hf & 3, known, &X, 1)) return false;
-                Xin = tof(X);
+            });
+            if (alive) {
+                cnt.hits = 1;
+                // entry behind the source (source inside the mesh, or the mesh behind
+                // it): t_in = 1/2 + (X_in - O).d / |d|^2 < 0, clip segments at t = 0
+                clip0 = dotf(sub(Xin, fr.O), fr.d) < -0.5f * dotf(fr.d, fr.d);
             }
-            h = hf >> 2;
-            f = hf & 3;
+        } else {
+            // continue where the fast kernel stopped
+            h = qe->h;
+            f = qe->fs & 3;
+            clip0 = (qe->fs >> 2) & 1;
+            steps = qe->fs >> 3;
+            float4 x = qe->x;
+            Xin = {x.x, x.y, x.z};
+            nvis = __float_as_int(x.w);
+            float4 a4 = qe->acc, c4 = qe->comp;
+            acc[0] = a4.x; comp[0] = c4.x;
+            if (C == 4) {
+                acc[1 % C] = a4.y; acc[2 % C] = a4.z; acc[3 % C] = a4.w;
+                comp[1 % C] = c4.y; comp[2 % C] = c4.z; comp[3 % C] = c4.w;
+            }
             alive = true;
-            return true;
-        });
-        if (alive) {
-            if (!ROBUST) cnt.hits = 1;
-            // entry behind the source (source inside the mesh, or the mesh behind
-            // it): t_in = 1/2 + (X_in - O).d / |d|^2 < 0, clip segments at t = 0
-            clip0 = dotf(sub(Xin, fr.O), fr.d) < -0.5f * dotf(fr.d, fr.d);
         }
         if (MODE == MODE_BWD && alive) {
             const float *y = reinterpret_cast<const float *>(p.in) + ray * C;
@@ -433,8 +461,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             for (int c = 0; c < C; ++c) yv[c] = __ldg(y + c);
         }
     }
-    if (ROBUST) cnt.hits = (valid && alive && skip < 0) ? 1 : 0;
-    if (!ROBUST) defer_append(p, deferred, ray, -1);
+    if (!ROBUST) defer_append<C>(p, deferred, ray, 0, -1, Xin, 0, acc, comp);
     flush_counters(p.m.counters, cnt);
     cnt = {0, 0, 0, 0, 0, 0, 0, 0};
 
@@ -445,8 +472,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
 
     while (__any_sync(FULL_MASK, alive)) {
         bool did = alive;
-        const int hcur = h;
-        const int seg = steps;
+        const int hcur = h, fcur = f;
         bool defer_now = false;
         float len = 0.f;
         if (alive) {
@@ -462,43 +488,54 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                     muv[0] = __ldg(mu + h);
                 }
             }
-            f3 v0 = {q0.x, q0.y, q0.z}, v1 = {q0.w, q1.x, q1.y};
-            f3 v2 = {q1.z, q1.w, q2.x}, v3 = {q2.y, q2.z, q2.w};
-            f3 n, a, b, c;
-            if (f == 0) { n = v0; a = v1; b = v3; c = v2; }
-            else if (f == 1) { n = v1; a = v0; b = v2; c = v3; }
-            else if (f == 2) { n = v2; a = v0; b = v3; c = v1; }
-            else { n = v3; a = v0; b = v1; c = v2; }
+            // local vertices v0 = q0.xyz, v1 = (q0.w, q1.xy), v2 = (q1.zw, q2.x),
+            // v3 = q2.yzw; n = v_f and the canonical face triple, branch-free
+            const bool f0 = f == 0, f1 = f == 1, f2 = f == 2;
+            f3 n = {f0 ? q0.x : (f1 ? q0.w : (f2 ? q1.z : q2.y)),
+                    f0 ? q0.y : (f1 ? q1.x : (f2 ? q1.w : q2.z)),
+                    f0 ? q0.z : (f1 ? q1.y : (f2 ? q2.x : q2.w))};
+            f3 a = {f0 ? q0.w : q0.x, f0 ? q1.x : q0.y, f0 ? q1.y : q0.z};          // v1 | v0
+            f3 b = {f0 ? q2.y : (f1 ? q1.z : (f2 ? q2.y : q0.w)),                   // v3|v2|v3|v1
+                    f0 ? q2.z : (f1 ? q1.w : (f2 ? q2.z : q1.x)),
+                    f0 ? q2.w : (f1 ? q2.x : (f2 ? q2.w : q1.y))};
+            f3 c = {(f0 || f == 3) ? q1.z : (f1 ? q2.y : q0.w),                     // v2|v3|v1|v2
+                    (f0 || f == 3) ? q1.w : (f1 ? q2.z : q1.x),
+                    (f0 || f == 3) ? q2.x : (f1 ? q2.w : q1.y)};
             Filt32Vert Vn = filt32_vert(fr, n);
+            f3 ea = sub(a, n), eb = sub(b, n), ec = sub(c, n);
             float sa, sb, sc, ba, bb, bc;
-            int ga = filt32_side(Vn, a, sa, ba);
-            int gb = filt32_side(Vn, b, sb, bb);
-            int gc = filt32_side(Vn, c, sc, bc);
+            int ga = filt32_side_e(Vn, a, ea, sa, ba);
+            int gb = filt32_side_e(Vn, b, eb, sb, bb);
+            int gc = filt32_side_e(Vn, c, ec, sc, bc);
             int x = -1;
             f3 Xout = Xin;
             bool fast = (ga != 0) & (gb != 0) & (gc != 0);
-            f3 y, z;
-            float wy, wz, bw;
             if (fast) {
                 x = exit_rule(ga, gb, gc);
-                if (x == 0) { y = b; z = c; wy = -sc; wz = sb; bw = bc + bb; }
-                else if (x == 1) { y = c; z = a; wy = -sa; wz = sc; bw = ba + bc; }
-                else { y = a; z = b; wy = -sb; wz = sa; bw = bb + ba; }
+                // exit face (n, y, z): barycentric weights w_y = -side(n->z),
+                // w_z = side(n->y), and their sum = d . ((y - n) x (z - n))
+                const bool x0 = x == 0, x1 = x == 1;
+                f3 ey = x0 ? eb : (x1 ? ec : ea), ez = x0 ? ec : (x1 ? ea : eb);
+                float wy = x0 ? -sc : (x1 ? -sa : -sb), wz = x0 ? sb : (x1 ? sc : sa);
+                float bw = x0 ? bc + bb : (x1 ? ba + bc : bb + ba);
+                float W = dotf(fr.d, crossf(ey, ez));
                 // the ray nearly lies in the exit face: place the crossing exactly
                 fast = x < 0 || wy + wz >= (float)TP_WEIGHT_MARGIN * bw;
+                if (fast) {
+                    float iw = __frcp_rn(W);
+                    Xout = f3axpy(wz * iw, ez, f3axpy(wy * iw, ey, n));
+                }
             }
-            if (fast) {
-                float wn = fmaxf(side_val32(fr, y, z), 0.f);
-                float iw = 1.f / (wn + wy + wz);
-                Xout = f3axpy(wz * iw, sub(z, n), f3axpy(wy * iw, sub(y, n), n));
-            } else if (!ROBUST) {
-                defer_now = true;  // counted by the resume kernel
-            } else {
-                if (seg >= skip) cnt.fp64 += (ga == 0) + (gb == 0) + (gc == 0);
-                int known[3] = {ga, gb, gc};
-                d3 X;
-                x = step_robust(&p, ray, h, f, known, &X);
-                Xout = tof(X);
+            if (!fast) {
+                if (!ROBUST) {
+                    defer_now = true;
+                } else {
+                    cnt.fp64 += (ga == 0) + (gb == 0) + (gc == 0);
+                    int known[3] = {ga, gb, gc};
+                    d3 X;
+                    x = step_robust(&p, ray, h, f, known, &X);
+                    Xout = tof(X);
+                }
             }
             if (defer_now) {
                 alive = false;
@@ -509,7 +546,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 alive = false;
                 did = false;
             } else {
-                if (!ROBUST || seg >= skip) ++cnt.segs;
+                ++cnt.segs;
                 int ia, ib, ic;
                 face_triple(f, ia, ib, ic);
                 int loc = x == 0 ? ia : (x == 1 ? ib : ic);
@@ -551,7 +588,6 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                     }
                 }
             }
-            if (ROBUST && seg < skip) did = false;  // already scattered by the fast kernel
         }
         if (MODE == MODE_BWD) {
             if (p.scatter == TETPROJ_SCATTER_WARP) {
@@ -591,7 +627,9 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                     atomicAdd(accbuf + hcur, len * yv[0]);
             }
         }
-        if (!ROBUST) defer_append(p, defer_now, ray, seg);
+        if (!ROBUST)
+            defer_append<C>(p, defer_now, ray, hcur, fcur | ((int)clip0 << 2) | (steps << 3), Xin,
+                            nvis, acc, comp);
     }
 
     if (valid && !deferred) {
@@ -607,6 +645,11 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
         }
         if (MODE == MODE_TRACE) p.tr_count[ray] = err ? -1 : nvis;
         if (err) report_error(p.m.counters, err);
+    }
+    if (!ROBUST) {
+        // rays handed to the resume kernel
+        unsigned dm = __ballot_sync(FULL_MASK, valid && deferred);
+        if ((threadIdx.x & 31) == 0 && dm) atomicAdd(&p.m.counters->deferred, (unsigned long long)__popc(dm));
     }
     flush_counters(p.m.counters, cnt);
 }
@@ -624,12 +667,12 @@ __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KPara
     const BvhNode *snodes = stage_bvh_top(p, smem);
     int64_t ray = 0;
     const bool valid = thread_ray(p, ray);
-    walk32_ray<C, MODE, false>(p, snodes, p.smem_nodes, ray, valid, 0);
+    walk32_ray<C, MODE, false>(p, snodes, p.smem_nodes, ray, valid, nullptr);
 }
 
 // Resume kernel: grid-stride over the queued rays (count set by k_walk32).
 template <int C, int MODE>
-__global__ void __launch_bounds__(128) k_resume32(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, 4) k_resume32(const __grid_constant__ KParams p) {
     extern __shared__ float4 smem[];
     const BvhNode *snodes = stage_bvh_top(p, smem);
     const unsigned long long n = *p.q_count;
@@ -638,9 +681,9 @@ __global__ void __launch_bounds__(128) k_resume32(const __grid_constant__ KParam
          base += stride) {
         const unsigned long long k = base + threadIdx.x;
         const bool valid = k < n;
-        int64_t ray = valid ? p.q_ray[k] : 0;
-        int skip = valid ? p.q_skip[k] : 0;  // -1: deferred at the entry search
-        walk32_ray<C, MODE, true>(p, snodes, p.smem_nodes, ray, valid, skip);
+        const QEntry *qe = p.q + (valid ? k : 0);
+        int64_t ray = valid ? qe->ray : 0;
+        walk32_ray<C, MODE, true>(p, snodes, p.smem_nodes, ray, valid, qe);
     }
 }
 

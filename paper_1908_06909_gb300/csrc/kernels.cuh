@@ -10,6 +10,19 @@ namespace tp {
 
 enum { MODE_FWD = 0, MODE_BWD = 1, MODE_TRACE = 2 };
 
+// One deferred ray: where its walk stopped, so the robust kernel continues
+// from there.  fs < 0: deferred during the entry search (no state yet);
+// otherwise fs = f | clip0 << 2 | steps << 3.
+struct __align__(16) QEntry {
+    int64_t ray;
+    int32_t h;
+    int32_t fs;
+    float4 x;     // entry point of tet h (xyz); w = trace visits so far (int bits)
+    float4 acc;   // forward partial sums (channels)
+    float4 comp;  // their Kahan compensations
+};
+static_assert(sizeof(QEntry) == 64, "QEntry must be 64 bytes");
+
 struct KParams {
     MeshView m;
     // ray source: cone-beam tiles (src_kind 0) or explicit rays (1)
@@ -34,9 +47,9 @@ struct KParams {
     // chunked launches: first block (cone tiles) or first block of 128 rays
     int64_t block_offset;
     // deferral queue of the filtered path (rays whose predicates the FP32
-    // filter could not decide); capacity >= rays per launch chunk
-    int64_t *q_ray;
-    int32_t *q_skip;          // segments already produced, or -1 (entry undecided)
+    // filter could not decide, with the walk state to continue from);
+    // capacity >= rays per launch chunk
+    struct QEntry *q;
     unsigned long long *q_count;
     int64_t q_cap;
 };

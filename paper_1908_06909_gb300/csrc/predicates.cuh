@@ -161,6 +161,14 @@ TP_HD int filt32_side(const Filt32Vert &v, const f3 &k, float &val) {
     float B;
     return filt32_side(v, k, val, B);
 }
+// the same with e = k - n already computed (the walk reuses it for the face normal)
+TP_HD int filt32_side_e(const Filt32Vert &v, const f3 &k, const f3 &e, float &val, float &B) {
+    val = dotf(v.w, e);
+    f3 kabs = fabs3(k);
+    f3 kn = {kabs.x + v.nabs.x, kabs.y + v.nabs.y, kabs.z + v.nabs.z};
+    B = fmaf(TP_FILT32_U, dotf(v.Z1, fabs3(e)) + dotf(v.Z2, kn), TP_FILT32_TINY);
+    return (val > B) - (val < -B);
+}
 
 // ------------------------------------------------------------------ FP64 stage
 //

@@ -59,10 +59,9 @@ struct AngleFrame {
 };
 
 struct DevCounters {
-    unsigned long long rays, hits, segments, fp64, exact, sos, bvh_nodes, bvh_faces;
+    unsigned long long rays, hits, segments, fp64, exact, sos, bvh_nodes, bvh_faces, deferred;
     int error;
     int error_count;
-    int pad[2];
 };
 
 struct MeshView {
