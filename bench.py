@@ -1,5 +1,8 @@
 #!/usr/bin/env python
-"""Benchmark: forward + back projection on the jittered Kuhn 96^3 workload.
+"""Benchmark: forward + back projection on the jittered Kuhn 96^3 workload
+(default), or on the batched workload (--workload batch24: 24 problems of
+uneven size, 4 channels, one persistent launch per direction under a CUDA
+graph).
 
 One step = tetproj_forward (b = A mu) followed by tetproj_backward of that
 projection (x = A^T b): 512 x 512 x 360 = 94,371,840 cone-beam rays through
@@ -122,6 +125,18 @@ def build_workload(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
+QUEUE_MAX = 1 << 23  # rays per deferral-queue round (library constant)
+
+
+def walk_launches(geo, tu, tv):
+    """Kernels one filtered forward (or backward) call launches: a
+    permutation kernel plus a fast walk and a resume walk per queue chunk."""
+    tiles = -(-geo.nu // tu) * -(-geo.nv // tv) * geo.nangles
+    q = -(-min(geo.nrays, QUEUE_MAX) // 4096) * 4096
+    per_chunk = max(1, q // (tu * tv))
+    return 1 + 2 * -(-tiles // per_chunk)
+
+
 def cpu_baseline(w, nsample, threads=None):
     """The oracle as it stands, on `nsample` rays spread over the workload:
     forward (b_j for the sampled rays) and backward (A^T y restricted to
@@ -167,6 +182,245 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_workload(name):
+    """The batched workload: 24 problems (config-5 sizes), or a reduced copy."""
+    import workloads as W
+    if name == "batch24":
+        specs = W.config5_specs()
+    elif name == "batch6s":  # small case for quick runs
+        specs = [(3, 16, 5), (8, 48, 9), (5, 24, 3), (12, 40, 7), (4, 32, 12), (6, 20, 4)]
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return [W.config5_problem(k, n, N, na, channels=4) for k, (n, N, na) in enumerate(specs)]
+
+
+def run_batch(args, tp, torch, dist, rank, world, local):
+    """All problems forward + backward, 4 channels, filtered FP32, as one
+    persistent work-queue launch per direction replayed from CUDA graphs;
+    tiles, ordering and scatter from the autotuner.  Beside it: the same
+    problems as sequential single-problem calls (same options), and the plain
+    FP64 path on every 8th angle of each problem, scaled by ray count."""
+    from paper_1908_06909_gb300 import autotune as A
+    C = 4
+    t_build = time.perf_counter()
+    ws = batch_workload(args.workload)
+    meshes = [tp.Mesh(w.verts, w.tets) for w in ws]
+    geos = [tp.Geometry.from_cone(w.geom) for w in ws]
+    t_build = time.perf_counter() - t_build
+    t_tune = time.perf_counter()
+    cache = A.Cache(os.path.join(ROOT, "gpurun_out", "autotune.json") if args.tune_cache is None
+                    else args.tune_cache, device=torch.cuda.get_device_name(), version=tp.version())
+    choices = A.tune_batch(tp, meshes, geos, channels=C, cache=cache, reps=2)
+    t_tune = time.perf_counter() - t_tune
+    tiles = [c.row() for c in choices]
+    b = tp.Batch(meshes, geos, channels=C, tiles=tiles)
+    for k, w in enumerate(ws):
+        b.mu[k].copy_(torch.tensor(w.mu, dtype=torch.float32))
+    stream = torch.cuda.current_stream()
+    nrays = b.nrays
+
+    # work counts per direction (one untimed pass each, outside the graphs)
+    for m in meshes:
+        m.stats_reset()
+    b.forward()
+    sf = _sum_stats([m.stats() for m in meshes])
+    for k in range(b.n):
+        b.y[k].copy_(b.proj[k])
+    for m in meshes:
+        m.stats_reset()
+    b.backward()
+    sb = _sum_stats([m.stats() for m in meshes])
+    assert sf["error"] == 0 and sb["error"] == 0, (sf, sb)
+    torch.cuda.synchronize()
+    gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gf):
+        b.forward()
+    with torch.cuda.graph(gb):
+        b.backward()
+    for _ in range(args.warmup):
+        gf.replay()
+        gb.replay()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            gf.replay()
+            evs[k][1].record(stream)
+            gb.replay()
+            evs[k][2].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t = torch.tensor([start.elapsed_time(end)], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item()) / args.steps
+    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    bwd_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    value = world * nrays / (ms_step / 1e3)
+    segs = sf["segments"] + sb["segments"]
+
+    # the same problems as sequential single-problem calls (same options)
+    opts = [tp.make_options(channels=C, tile=(r[0], r[1]), order=r[2], scatter=r[3])
+            for r in tiles]
+    def singles():
+        for k in range(b.n):
+            tp.forward(meshes[k], geos[k], b.mu[k], out=b.proj[k], options=opts[k])
+            tp.backward(meshes[k], geos[k], b.y[k], out=b.mu_out[k], options=opts[k])
+    singles()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    singles()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1)
+
+    # plain FP64 and filtered single calls on every 8th angle, scaled by rays
+    plain_ms = filt_ms = 0.0
+    rel_num = rel_den = 0.0
+    for k, w in enumerate(ws):
+        sel = w.geom.angles[::8]
+        gs = tp.Geometry(w.geom.dso, w.geom.dsd, w.geom.nu, w.geom.nv, w.geom.du, w.geom.dv, sel)
+        mu64 = b.mu[k].double()
+        o64 = tp.make_options(precision=tp.PLAIN_FP64, channels=C, tile=(tiles[k][0], tiles[k][1]),
+                              order=tiles[k][2], scatter=tiles[k][3])
+        p64 = tp.forward(meshes[k], gs, mu64, options=o64)
+        x64 = tp.backward(meshes[k], gs, p64, options=o64)
+        p32 = tp.forward(meshes[k], gs, b.mu[k], options=opts[k])
+        x32 = tp.backward(meshes[k], gs, p32, options=opts[k])
+        torch.cuda.synchronize()
+        for prec, fn in (("f64", lambda: (tp.forward(meshes[k], gs, mu64, out=p64, options=o64),
+                                          tp.backward(meshes[k], gs, p64, out=x64, options=o64))),
+                         ("f32", lambda: (tp.forward(meshes[k], gs, b.mu[k], out=p32, options=opts[k]),
+                                          tp.backward(meshes[k], gs, p32, out=x32, options=opts[k])))):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            scaled = a0.elapsed_time(a1) * geos[k].nrays / gs.nrays
+            if prec == "f64":
+                plain_ms += scaled
+            else:
+                filt_ms += scaled
+        rel_num += float((p32.double() - p64).abs().sum())
+        rel_den += float(p64.abs().sum())
+        del p64, x64, p32, x32, mu64
+
+    # end to end with host buffers: H2D of every mu, D2H of every projection
+    # and backprojection (the graphs read and write the bound tensors)
+    mu_h = [torch.empty_like(x, device="cpu").pin_memory() for x in b.mu]
+    for k in range(b.n):
+        mu_h[k].copy_(b.mu[k])
+    proj_h = [torch.empty_like(x, device="cpu").pin_memory() for x in b.proj]
+    back_h = [torch.empty_like(x, device="cpu").pin_memory() for x in b.mu_out]
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for k in range(b.n):
+            b.mu[k].copy_(mu_h[k], non_blocking=True)
+        gf.replay()
+        for k in range(b.n):
+            b.y[k].copy_(b.proj[k])
+        gb.replay()
+        for k in range(b.n):
+            proj_h[k].copy_(b.proj[k], non_blocking=True)
+            back_h[k].copy_(b.mu_out[k], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    h2d = sum(x.numel() * 4 for x in mu_h)
+    d2h = sum(x.numel() * 4 for x in proj_h) + sum(x.numel() * 4 for x in back_h)
+    del mu_h, proj_h, back_h
+
+    hbm, peak_kind = peaks()
+    def alg_bytes(s, kind, table=BYTES_STEP):
+        return (s["segments"] * table[(kind, C)] + s["rays"] * BYTES_RAY(C) +
+                s["bvh_nodes"] * BYTES_BOX + s["bvh_faces"] * BYTES_FACE)
+    dom = "bwd" if bwd_ms >= fwd_ms else "fwd"
+    dom_ms = bwd_ms if dom == "bwd" else fwd_ms
+    dom_bytes = alg_bytes(sb if dom == "bwd" else sf, dom)
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": f"k_batch32<4,{'MODE_BWD' if dom == 'bwd' else 'MODE_FWD'}>",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_kind": peak_kind, "bytes_per_launch": dom_bytes,
+            "ms_per_launch": dom_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "layout_gbs": alg_bytes(sb if dom == "bwd" else sf, dom, LAYOUT_STEP) / (dom_ms / 1e3) / 1e9}
+    # warp items of 32 rays; rounds of at most QUEUE_MAX rays
+    nitems = sum(-(-g.nu // r[0]) * -(-g.nv // r[1]) * g.nangles * (r[0] * r[1] // 32)
+                 for g, r in zip(geos, tiles))
+    q_cap = -(-min(nitems * 32, QUEUE_MAX) // 4096) * 4096
+    rounds = -(-nitems // (q_cap // 32))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        per = max(1, args.cpu_sample // len(ws))
+        t0 = time.perf_counter()
+        n_cpu = 0
+        for w in ws:
+            rng = np.random.default_rng(777)
+            idx = np.sort(rng.choice(w.geom.nrays, per, replace=False))
+            S, P = oracle.cone_rays(w.geom, idx)
+            oracle.forward_rays(w.verts, w.tets, w.mu, S, P)
+            oracle.backward_rays(w.verts, w.tets, rng.uniform(size=(per, C)), S, P)
+            n_cpu += per
+        dt = time.perf_counter() - t0
+        cpu = {"value": n_cpu / dt, "unit": "rays/s", "cores": oracle.default_threads(),
+               "kind": "oracle", "sample": f"{per} rays of each of {len(ws)} problems (fwd + back, "
+                                           f"4 channels), brute-force FP64 clipping, {dt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "problems": len(ws),
+                       "nt_total": int(sum(m.nt for m in meshes)), "rays_per_step": nrays,
+                       "channels": C, "precision": "filtered", "launch": "persistent work queue, CUDA graph",
+                       "work_item": "32-ray warp slice of a tile", "tiles": tiles,
+                       "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
+            "gsegments_per_s": world * segs / (ms_step / 1e3) / 1e9,
+            "segments_per_step": segs,
+            "unbatched": {"ms_per_step": single_ms, "value": nrays / (single_ms / 1e3),
+                          "speedup_batched": single_ms / ms_step},
+            "plain_fp64": {"ms_per_step_est": plain_ms, "value": nrays / (plain_ms / 1e3),
+                           "filtered_single_ms_est": filt_ms,
+                           "speedup_batched_vs_plain": plain_ms / ms_step,
+                           "filtered_vs_plain_rel_l1_diff": rel_num / max(rel_den, 1e-300),
+                           "sample": "every 8th angle of each problem, time scaled by ray count"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * nrays / (e2e_ms / 1e3), "unit": "rays/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            # per step: a gather and a scatter kernel per problem, and per
+            # round a persistent walk and a resume walk in each direction
+            "gpu_launches": args.steps * (2 * b.n + 4 * rounds),
+            "clocks": clk.summary(),
+            "host_s": {"build": t_build, "tune": t_tune},
+            "stats": {"fwd": sf, "bwd": sb},
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+
+
+def _sum_stats(rows):
+    out = {}
+    for r in rows:
+        for k, v in r.items():
+            out[k] = out.get(k, 0) + v
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,6 +433,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--scatter", default="atomic", choices=["atomic", "warp"])
     ap.add_argument("--tile", default="8x8")
+    ap.add_argument("--tune-cache", default=None)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -199,6 +454,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if args.workload.startswith("batch"):
+        run_batch(args, tp, torch, dist, rank, world, local)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     w = build_workload(args)
     mesh = tp.Mesh(w.verts, w.tets)
@@ -351,7 +612,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 2 * walk_launches(geo, tu, tv) * args.steps,
             "clocks": clk.summary(),
             "stats": {"fwd": sf, "bwd": sb},
         }

@@ -226,6 +226,40 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
                                   double *out_len, int32_t *out_count,
                                   const tetproj_options *opt, void *stream);
 
+/* --------------------------------------------------------------- batches --
+ * Many independent problems (mesh, geometry) of uneven size projected in one
+ * persistent work-queue launch per round: warps take (problem, angle, tile,
+ * 32-ray slice) items from an atomic counter, so large and small problems
+ * share the GPU without per-problem launch tails (the paper splits projections across GPUs,
+ * Sec. II-F; here many problems share one GPU).  Filtered FP32 path only.
+ *   meshes, geos: HOST arrays of n handles (a mesh may appear several times);
+ *   tiles: HOST [n][4] = (tile_u, tile_v, order, scatter) per problem, or NULL
+ *          for the defaults; each as in the options struct (powers of two,
+ *          32..256 rays per tile); problems may use different tiles;
+ *   channels: C = 1 or 4 for every problem.
+ * The batch owns per-problem workspace and one deferral queue (allocated
+ * here); it keeps pointers into the meshes and geometries, which must outlive
+ * it.  Rays are processed in rounds of at most 2^23 rays.
+ * Errors: TETPROJ_ERR_ARG (null handle, n < 1, bad channels or tiles),
+ * TETPROJ_ERR_TOO_LARGE (2^40 work items or more), CUDA
+ * errors of the allocations; *out is NULL on error. */
+typedef struct tetproj_batch tetproj_batch;
+tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes,
+                                    const tetproj_geometry *const *geos, const int32_t *tiles,
+                                    int32_t n, int32_t channels, tetproj_batch **out);
+/* Binds the operands: HOST arrays of n DEVICE pointers (float, layouts as in
+ * tetproj_forward/backward).  mu/proj are used by tetproj_batch_forward, y/mu_out
+ * by tetproj_batch_backward; the pair not used may be NULL.  Synchronous
+ * (uploads the per-problem tables). */
+tetproj_status tetproj_batch_bind(tetproj_batch *b, const void *const *mu, void *const *proj,
+                                  const void *const *y, void *const *mu_out);
+/* proj[k] = A_k mu[k] and mu_out[k] = A_k^T y[k] for every problem; async on
+ * `stream`, no allocation and no host synchronisation: the sequence can be
+ * captured in a CUDA graph (the graph then replays with the bound buffers). */
+tetproj_status tetproj_batch_forward(tetproj_batch *b, void *stream);
+tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream);
+tetproj_status tetproj_batch_destroy(tetproj_batch *b);
+
 /* ------------------------------------------------------------ predicates --
  * Sign of the side product det[P - S, p - S, q - S] of the line S->P and the
  * edge p->q (the test behind each of the four triangle tests of Sec. II-C),

@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import (FILTERED, ORDER_MORTON, ORDER_ROW, PLAIN_FP64, SCATTER_ATOMIC, SCATTER_WARP,
                    Options, TetprojError, check)
 
-__all__ = ["Mesh", "Geometry", "forward", "backward", "backward_noalloc", "forward_rays", "backward_rays",
+__all__ = ["Mesh", "Geometry", "Batch", "forward", "backward", "backward_noalloc", "forward_rays", "backward_rays",
            "trace_rays", "side_signs_host", "side_signs_device", "TetProject", "make_options",
            "FILTERED", "PLAIN_FP64", "ORDER_ROW", "ORDER_MORTON", "SCATTER_ATOMIC",
            "SCATTER_WARP", "TetprojError", "library_path"]
@@ -29,6 +29,11 @@ __all__ = ["Mesh", "Geometry", "forward", "backward", "backward_noalloc", "forwa
 
 def library_path() -> str:
     return _lib.LIB_PATH
+
+
+def version() -> str:
+    v = int(_lib.load().tetproj_version())
+    return f"{v // 10000}.{v // 100 % 100}.{v % 100}"
 
 
 def _torch():
@@ -138,6 +143,7 @@ class Geometry:
                                         float(dv), a.ctypes.data, a.size, ctypes.byref(h)),
               "tetproj_geometry_create")
         self._h = h
+        self.angles = a.copy()
         self.nu, self.nv, self.nangles = int(nu), int(nv), int(a.size)
         self.dso, self.dsd, self.du, self.dv = float(dso), float(dsd), float(du), float(dv)
 
@@ -336,6 +342,71 @@ def side_signs_device(S, P, p, q):
     check(_lib.load().tetproj_side_device(_ptr(S), _ptr(P), _ptr(p), _ptr(q), n, _ptr(sign),
                                           _ptr(stage), _stream()), "tetproj_side_device")
     return sign, stage
+
+
+class Batch:
+    """Many (mesh, geometry) problems projected by one persistent work-queue
+    launch per direction (``tetproj_batch_*``; filtered FP32 path).
+
+    tiles: per problem (tile_u, tile_v, order, scatter), or None for the
+    defaults; tiles hold 32..256 rays and may differ between problems.  The
+    operand tensors are allocated here (mu/mu_out [nt(,C)], proj/y
+    [na, nv, nu(,C)], float32) and bound once, so ``forward()`` and
+    ``backward()`` issue stream work only and can be captured in a CUDA graph
+    (write new inputs into ``mu[k]`` / ``y[k]`` in place before a replay)."""
+
+    def __init__(self, meshes, geos, channels=1, tiles=None):
+        torch = _torch()
+        L = _lib.load()
+        n = len(meshes)
+        if n != len(geos) or n < 1:
+            raise ValueError("meshes and geos must be non-empty lists of equal length")
+        mh = (ctypes.c_void_p * n)(*[m.handle.value for m in meshes])
+        gh = (ctypes.c_void_p * n)(*[g.handle.value for g in geos])
+        tl = None
+        if tiles is not None:
+            t = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(n, 4))
+            tl = t
+        h = ctypes.c_void_p()
+        check(L.tetproj_batch_create(mh, gh, None if tl is None else tl.ctypes.data, n, channels,
+                                     ctypes.byref(h)), "tetproj_batch_create")
+        self._h = h
+        self.meshes, self.geos, self.channels, self.n = list(meshes), list(geos), channels, n
+        ext = (channels,) if channels > 1 else ()
+        self.mu = [torch.zeros((m.nt,) + ext, dtype=torch.float32, device="cuda") for m in meshes]
+        self.mu_out = [torch.zeros((m.nt,) + ext, dtype=torch.float32, device="cuda")
+                       for m in meshes]
+        self.proj = [torch.zeros(g.shape + ext, dtype=torch.float32, device="cuda") for g in geos]
+        self.y = [torch.zeros(g.shape + ext, dtype=torch.float32, device="cuda") for g in geos]
+        arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+        torch.cuda.synchronize()
+        check(L.tetproj_batch_bind(self._h, arr(self.mu), arr(self.proj), arr(self.y),
+                                   arr(self.mu_out)), "tetproj_batch_bind")
+
+    @property
+    def nrays(self) -> int:
+        return sum(g.nrays for g in self.geos)
+
+    def forward(self):
+        """proj[k] = A_k mu[k] for every problem (async on the current stream)."""
+        check(_lib.load().tetproj_batch_forward(self._h, _stream()), "tetproj_batch_forward")
+        return self.proj
+
+    def backward(self):
+        """mu_out[k] = A_k^T y[k] for every problem (async on the current stream)."""
+        check(_lib.load().tetproj_batch_backward(self._h, _stream()), "tetproj_batch_backward")
+        return self.mu_out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().tetproj_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd_cls():

@@ -78,6 +78,11 @@ SIGNATURES = {
                                       ctypes.POINTER(Options), c_vp]),
     "tetproj_trace_rays": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp,
                                    ctypes.POINTER(Options), c_vp]),
+    "tetproj_batch_create": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_i32, ctypes.POINTER(c_vp)]),
+    "tetproj_batch_bind": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "tetproj_batch_forward": (c_i32, [c_vp, c_vp]),
+    "tetproj_batch_backward": (c_i32, [c_vp, c_vp]),
+    "tetproj_batch_destroy": (c_i32, [c_vp]),
     "tetproj_side_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp]),
     "tetproj_side_device": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
 }

@@ -70,7 +70,7 @@ static cudaError_t upload(T **dst, const std::vector<T> &src) {
 
 extern "C" {
 
-int32_t tetproj_version(void) { return 100; }
+int32_t tetproj_version(void) { return 200; }
 
 void tetproj_default_options(tetproj_options *o) {
     if (!o) return;
@@ -609,5 +609,196 @@ extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
     p.out = acc;
     TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s));
     TP_CUDA(launch_scatter_perm(mesh->perm, mesh->nt, o.channels, f64, acc, mu_out, s));
+    return TETPROJ_OK;
+}
+
+// ------------------------------------------------------------ batched calls
+//
+// A batch holds many (mesh, geometry) problems of uneven size and runs their
+// forward or backward projections in one persistent work-queue launch per
+// round (kernels.cu: k_batch32 / k_batch_resume32).  Operand buffers are bound
+// once (tetproj_batch_bind) so that forward/backward take only a stream and
+// can be captured in a CUDA graph and replayed.
+
+// BVH nodes each warp of the batched kernel stages in shared memory
+static const int kBatchWarpNodes = 0;
+
+struct tetproj_batch {
+    int n = 0, channels = 1;
+    std::vector<KParams> base;        // per-problem parameters (no operands)
+    std::vector<const tetproj_mesh *> meshes;
+    std::vector<void *> ws_in, ws_acc;
+    std::vector<int64_t> ws_bytes;
+    std::vector<int64_t> item_begin;  // host copy, n + 1 entries
+    std::vector<const void *> mu, y;
+    std::vector<void *> proj, mu_out;
+    BatchProblem *d_fwd = nullptr, *d_bwd = nullptr;
+    int64_t *d_item_begin = nullptr;
+    QEntry *q = nullptr;
+    unsigned long long *q_count = nullptr;
+    unsigned *item_counter = nullptr;
+    int64_t q_cap = 0;
+    int smem_nodes = 64;
+    unsigned grid_fwd = 0, grid_bwd = 0, rgrid = 0;
+    bool bound = false;
+};
+
+static void batch_free(tetproj_batch *b) {
+    if (!b) return;
+    for (void *p : b->ws_in) cudaFree(p);
+    for (void *p : b->ws_acc) cudaFree(p);
+    cudaFree(b->d_fwd);
+    cudaFree(b->d_bwd);
+    cudaFree(b->d_item_begin);
+    cudaFree(b->q);
+    cudaFree(b->q_count);
+    cudaFree(b->item_counter);
+    delete b;
+}
+
+extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes,
+                                               const tetproj_geometry *const *geos,
+                                               const int32_t *tiles, int32_t n,
+                                               int32_t channels, tetproj_batch **out) {
+    if (!out) return TETPROJ_ERR_ARG;
+    *out = nullptr;
+    if (!meshes || !geos || n < 1 || n >= (1 << 20) || (channels != 1 && channels != 4))
+        return TETPROJ_ERR_ARG;
+    tetproj_batch *b = new (std::nothrow) tetproj_batch();
+    if (!b) return TETPROJ_ERR_OOM;
+    b->n = n;
+    b->channels = channels;
+    b->item_begin.assign(1, 0);
+    int64_t total_rays = 0;
+    for (int k = 0; k < n; ++k) {
+        if (!meshes[k] || !geos[k]) { batch_free(b); return TETPROJ_ERR_ARG; }
+        tetproj_options o;
+        tetproj_default_options(&o);
+        o.channels = channels;
+        if (tiles) {
+            o.tile_u = tiles[4 * k];
+            o.tile_v = tiles[4 * k + 1];
+            o.order = tiles[4 * k + 2];
+            o.scatter = tiles[4 * k + 3];
+        }
+        tetproj_options oo;
+        tetproj_status st = check_opts(&o, oo);
+        if (st != TETPROJ_OK) { batch_free(b); return st; }
+        KParams p = base_params(meshes[k], oo);
+        set_cone(p, geos[k]);
+        b->base.push_back(p);
+        b->meshes.push_back(meshes[k]);
+        // warp items: 32 in-tile threads of one tile (tiles hold 32..256 threads),
+        // padded to whole chunks so that every problem starts a chunk
+        int64_t items = (int64_t)p.g.na * p.tiles_u * p.tiles_v * ((oo.tile_u * oo.tile_v) / 32);
+        items = (items + kBatchChunk - 1) / kBatchChunk * kBatchChunk;
+        if (items >= (int64_t(1) << 31)) { batch_free(b); return TETPROJ_ERR_TOO_LARGE; }
+        b->item_begin.push_back(b->item_begin.back() + items);
+        total_rays += items * 32;
+        int64_t bytes = meshes[k]->nt * channels * 4;
+        void *a = nullptr, *c = nullptr;
+        cudaError_t e = cudaMalloc(&a, (size_t)bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&c, (size_t)bytes);
+        b->ws_in.push_back(a);
+        b->ws_acc.push_back(c);
+        b->ws_bytes.push_back(bytes);
+        if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
+    }
+    if (b->item_begin.back() >= (int64_t(1) << 40)) { batch_free(b); return TETPROJ_ERR_TOO_LARGE; }
+    int64_t need = total_rays < kQueueMax ? total_rays : kQueueMax;
+    need = ((need + 4095) / 4096) * 4096;
+    cudaError_t e = cudaMalloc((void **)&b->q, (size_t)need * sizeof(QEntry));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->q_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->item_counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_fwd, sizeof(BatchProblem) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bwd, sizeof(BatchProblem) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_item_begin, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_item_begin, b->item_begin.data(), sizeof(int64_t) * (n + 1),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
+    b->q_cap = need;
+    // launch shapes are fixed here so that forward/backward issue stream work only
+    int snodes = 0;
+    for (auto &p : b->base) snodes = p.smem_nodes > snodes ? p.smem_nodes : snodes;
+    b->smem_nodes = snodes < kBatchWarpNodes ? snodes : kBatchWarpNodes;
+    e = batch_grid(channels, MODE_FWD, b->smem_nodes, b->grid_fwd);
+    if (e == cudaSuccess) e = batch_grid(channels, MODE_BWD, b->smem_nodes, b->grid_bwd);
+    if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
+    b->rgrid = (unsigned)(4 * device_sm_count());
+    for (auto &p : b->base) {
+        p.q = b->q;
+        p.q_count = b->q_count;
+        p.q_cap = b->q_cap;
+    }
+    b->mu.assign(n, nullptr);
+    b->y.assign(n, nullptr);
+    b->proj.assign(n, nullptr);
+    b->mu_out.assign(n, nullptr);
+    *out = b;
+    return TETPROJ_OK;
+}
+
+extern "C" tetproj_status tetproj_batch_bind(tetproj_batch *b, const void *const *mu,
+                                             void *const *proj, const void *const *y,
+                                             void *const *mu_out) {
+    if (!b) return TETPROJ_ERR_ARG;
+    std::vector<BatchProblem> f(b->n), g(b->n);
+    for (int k = 0; k < b->n; ++k) {
+        b->mu[k] = mu ? mu[k] : nullptr;
+        b->proj[k] = proj ? proj[k] : nullptr;
+        b->y[k] = y ? y[k] : nullptr;
+        b->mu_out[k] = mu_out ? mu_out[k] : nullptr;
+        std::memset(&f[k], 0, sizeof(BatchProblem));
+        std::memset(&g[k], 0, sizeof(BatchProblem));
+        f[k].p = b->base[k];
+        f[k].p.in = b->ws_in[k];
+        f[k].p.out = b->proj[k];
+        f[k].p.qtag = (int64_t)k << 40;
+        g[k].p = b->base[k];
+        g[k].p.in = b->y[k];
+        g[k].p.out = b->ws_acc[k];
+        g[k].p.qtag = (int64_t)k << 40;
+    }
+    TP_CUDA(cudaMemcpy(b->d_fwd, f.data(), sizeof(BatchProblem) * b->n, cudaMemcpyHostToDevice));
+    TP_CUDA(cudaMemcpy(b->d_bwd, g.data(), sizeof(BatchProblem) * b->n, cudaMemcpyHostToDevice));
+    b->bound = true;
+    return TETPROJ_OK;
+}
+
+extern "C" tetproj_status tetproj_batch_forward(tetproj_batch *b, void *stream) {
+    if (!b || !b->bound) return TETPROJ_ERR_ARG;
+    for (int k = 0; k < b->n; ++k)
+        if (!b->mu[k] || !b->proj[k]) return TETPROJ_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < b->n; ++k)
+        TP_CUDA(launch_gather_perm(b->meshes[k]->perm, b->meshes[k]->nt, b->channels, 0, b->mu[k],
+                                   b->ws_in[k], s));
+    TP_CUDA(launch_batch(b->d_fwd, b->d_item_begin, b->n, b->item_begin.back(),
+                         b->channels, MODE_FWD, b->grid_fwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
+                         b->smem_nodes, s));
+    return TETPROJ_OK;
+}
+
+extern "C" tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream) {
+    if (!b || !b->bound) return TETPROJ_ERR_ARG;
+    for (int k = 0; k < b->n; ++k)
+        if (!b->y[k] || !b->mu_out[k]) return TETPROJ_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < b->n; ++k)
+        TP_CUDA(cudaMemsetAsync(b->ws_acc[k], 0, (size_t)b->ws_bytes[k], s));
+    TP_CUDA(launch_batch(b->d_bwd, b->d_item_begin, b->n, b->item_begin.back(),
+                         b->channels, MODE_BWD, b->grid_bwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
+                         b->smem_nodes, s));
+    for (int k = 0; k < b->n; ++k)
+        TP_CUDA(launch_scatter_perm(b->meshes[k]->perm, b->meshes[k]->nt, b->channels, 0,
+                                    b->ws_acc[k], b->mu_out[k], s));
+    return TETPROJ_OK;
+}
+
+extern "C" tetproj_status tetproj_batch_destroy(tetproj_batch *b) {
+    if (!b) return TETPROJ_ERR_ARG;
+    cudaDeviceSynchronize();
+    batch_free(b);
     return TETPROJ_OK;
 }

@@ -89,13 +89,15 @@ __device__ __forceinline__ void morton_local(int t, int bx, int by, int &x, int 
     }
 }
 
-__device__ __forceinline__ bool thread_ray(const KParams &p, int64_t &ray) {
+// Ray of this thread in tile / ray block `b` (cone tiles are enumerated
+// tile_u fastest, then tile_v, then angle).
+// Ray of in-tile thread t of tile b (cone tiles), or of thread t of block b
+// (explicit rays, blocks of blockDim.x rays).
+__device__ __forceinline__ bool thread_ray_at(const KParams &p, int64_t b, int t, int64_t &ray) {
     if (p.src_kind == 0) {
         int lu, lv;
-        int t = threadIdx.x;
         if (p.morton) morton_local(t, p.log_tu, p.log_tv, lu, lv);
         else { lu = t & (p.tu - 1); lv = t >> p.log_tu; }
-        int64_t b = (int64_t)blockIdx.x + p.block_offset;
         int tid_u = (int)(b % p.tiles_u);
         int64_t rest = b / p.tiles_u;
         int tid_v = (int)(rest % p.tiles_v);
@@ -105,8 +107,16 @@ __device__ __forceinline__ bool thread_ray(const KParams &p, int64_t &ray) {
         ray = ((int64_t)a * p.g.nv + iv) * p.g.nu + iu;
         return true;
     }
-    ray = ((int64_t)blockIdx.x + p.block_offset) * blockDim.x + threadIdx.x;
+    ray = b * blockDim.x + t;
     return ray < p.nrays;
+}
+
+__device__ __forceinline__ bool thread_ray_in(const KParams &p, int64_t b, int64_t &ray) {
+    return thread_ray_at(p, b, threadIdx.x, ray);
+}
+
+__device__ __forceinline__ bool thread_ray(const KParams &p, int64_t &ray) {
+    return thread_ray_in(p, (int64_t)blockIdx.x + p.block_offset, ray);
 }
 
 // ---------------------------------------------------------- vector helpers
@@ -352,6 +362,7 @@ __device__ __forceinline__ void defer_append(const KParams &p, bool want, int64_
                                              const float *comp) {
     unsigned m = __ballot_sync(FULL_MASK, want);
     if (!m) return;
+    ray |= p.qtag;  // read only when some lane defers
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(m) - 1;
     unsigned long long base = 0;
@@ -590,7 +601,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             }
         }
         if (MODE == MODE_BWD) {
-            if (p.scatter == TETPROJ_SCATTER_WARP) {
+            if (!ROBUST && p.scatter == TETPROJ_SCATTER_WARP) {
                 unsigned peers = __match_any_sync(FULL_MASK, did ? hcur : -1 - lane);
                 if (did) {
                     float v[C];
@@ -675,7 +686,8 @@ template <int C, int MODE>
 __global__ void __launch_bounds__(128, 4) k_resume32(const __grid_constant__ KParams p) {
     extern __shared__ float4 smem[];
     const BvhNode *snodes = stage_bvh_top(p, smem);
-    const unsigned long long n = *p.q_count;
+    // entries past the capacity were never written (the append reported an error)
+    const unsigned long long n = min(*p.q_count, (unsigned long long)p.q_cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n;
          base += stride) {
@@ -908,6 +920,236 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
     flush_counters(p.m.counters, cnt);
 }
 
+
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// ============================================================ batched walk
+//
+// Many meshes and geometries in one persistent launch.  The unit of work is a
+// WARP item: 32 consecutive in-tile threads of one detector tile of one angle
+// of one problem (the rays a warp of the single-problem kernel walks).  Work
+// is handed out in two levels:
+//   * a CTA claims CHUNKS of kBatchChunk consecutive warp items (whole tiles,
+//     as every problem's item range starts at a multiple of the chunk) from a
+//     global counter, so the warps walking neighbouring rays of one tile share
+//     the SM's L1 (spreading the warps of a tile over SMs cut the L1 hit rate
+//     from 67% to 49%);
+//   * the CTA's warps take items from a shared-memory ticket counter on their
+//     own and never wait at a CTA barrier for the slowest warp.
+// A ticket t belongs to CTA-local chunk t / kBatchChunk; the warp drawing the
+// chunk's first ticket claims it and publishes its base in a ring slot, which
+// it may reuse only after every ticket of the slot's previous chunk has read
+// it.  Both waits are between warps of one CTA and bounded (TETPROJ_ERR_TIMEOUT,
+// and the warp stops).  Per warp, the problem's parameters sit in a private
+// shared-memory slot, refreshed only when the warp moves to another problem.
+// Deferred rays carry the problem index in bits 40+ of their queue entry and
+// are finished by k_batch_resume32.
+
+#define TP_BATCH_TAG_SHIFT 40
+#define TP_BATCH_THREADS 128
+#define TP_BATCH_RING 4
+#define TP_BATCH_SPIN_LIMIT (1 << 22)
+
+#ifndef TP_BATCH_MIN_BLOCKS
+#define TP_BATCH_MIN_BLOCKS 8
+#endif
+
+constexpr int kBatchParamVec = (int)((sizeof(KParams) + 15) / 16);
+
+// bounded wait for *a == v on a shared-memory word written by another warp
+__device__ __forceinline__ bool batch_wait_eq(volatile int *a, int v) {
+    for (int i = 0; i < TP_BATCH_SPIN_LIMIT; ++i) {
+        if (*a == v) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+template <int C, int MODE>
+__global__ void __launch_bounds__(TP_BATCH_THREADS, TP_BATCH_MIN_BLOCKS)
+    k_batch32(const BatchProblem *__restrict__ probs, const int64_t *__restrict__ item_begin,
+              int nprob, int64_t round_begin, int64_t round_end, unsigned *chunk_counter,
+              int nsm_max) {
+    extern __shared__ float4 smem[];
+    __shared__ unsigned s_ticket;
+    __shared__ long long s_base[TP_BATCH_RING];
+    __shared__ int s_gen[TP_BATCH_RING];
+    __shared__ int s_used[TP_BATCH_RING];
+    if (threadIdx.x == 0) s_ticket = 0;
+    if (threadIdx.x < TP_BATCH_RING) {
+        s_gen[threadIdx.x] = -1;
+        s_used[threadIdx.x] = kBatchChunk;  // slot free
+    }
+    __syncthreads();  // the only CTA barrier
+
+    // per-warp slot: the current problem's parameters (its smem_nodes field
+    // clamped to the nodes staged here), then the staged BVH nodes.  The
+    // walk reads everything it needs from the slot, so little state stays in
+    // registers across it.
+    const int lane = threadIdx.x & 31;
+    KParams *sp = reinterpret_cast<KParams *>(smem + (threadIdx.x >> 5) *
+                                                         (kBatchParamVec + 4 * nsm_max));
+    int cur = -1;
+    while (true) {
+        long long it = 0;
+        if (lane == 0) {
+            const unsigned t = atomicAdd(&s_ticket, 1u);
+            const int c = (int)(t / kBatchChunk), o = (int)(t % kBatchChunk);
+            const int r = c % TP_BATCH_RING;
+            bool ok = true;
+            if (o == 0) {
+                // claim chunk c: wait until slot r's previous chunk is fully read
+                ok = batch_wait_eq(&s_used[r], kBatchChunk);
+                if (ok) {
+                    s_used[r] = 0;
+                    const unsigned g = atomicAdd(chunk_counter, 1u);
+                    s_base[r] = round_begin + (long long)g * kBatchChunk;
+                    __threadfence_block();
+                    *(volatile int *)&s_gen[r] = c;
+                }
+            }
+            if (ok) ok = batch_wait_eq(&s_gen[r], c);
+            if (ok) {
+                __threadfence_block();
+                it = *(volatile long long *)&s_base[r] + o;
+                __threadfence_block();
+                atomicAdd(&s_used[r], 1);
+            } else {
+                report_error(probs[cur < 0 ? 0 : cur].p.m.counters, TETPROJ_ERR_TIMEOUT);
+                it = round_end;
+            }
+        }
+        it = __shfl_sync(FULL_MASK, it, 0);
+        if (it >= round_end) break;
+        // problem k with item_begin[k] <= it < item_begin[k + 1] (warp-uniform)
+        int k = 0, hi = nprob - 1;
+        while (k < hi) {
+            const int mid = (k + hi + 1) >> 1;
+            if (__ldg(item_begin + mid) <= it) k = mid;
+            else hi = mid - 1;
+        }
+        if (k != cur) {
+            __syncwarp();
+            float4 *dst = reinterpret_cast<float4 *>(sp);
+            const float4 *src = reinterpret_cast<const float4 *>(&probs[k].p);
+            for (int i = lane; i < kBatchParamVec; i += 32) dst[i] = __ldg(src + i);
+            const int want = __ldg(&probs[k].p.smem_nodes);
+            const int nsm = want < nsm_max ? want : nsm_max;
+            const float4 *bv = reinterpret_cast<const float4 *>(__ldg(
+                reinterpret_cast<const unsigned long long *>(&probs[k].p.m.bvh)));
+            for (int i = lane; i < nsm * 4; i += 32) dst[kBatchParamVec + i] = __ldg(bv + i);
+            __syncwarp();
+            if (lane == 0) sp->smem_nodes = nsm;
+            __syncwarp();
+            cur = k;
+        }
+        // items of one problem number < 2^31; items past the problem's last
+        // tile (padding to a whole chunk) map to no ray.  Warps per tile:
+        // tu * tv / 32, a power of two.
+        const int wpt_log = sp->log_tu + sp->log_tv - 5;
+        const int local = (int)(it - __ldg(item_begin + k));
+        const int t = ((local & ((1 << wpt_log) - 1)) << 5) + lane;
+        int64_t ray = 0;
+        const bool valid = thread_ray_at(*sp, (int64_t)(local >> wpt_log), t, ray);
+        walk32_ray<C, MODE, false>(*sp,
+                                   reinterpret_cast<const BvhNode *>(
+                                       reinterpret_cast<const float4 *>(sp) + kBatchParamVec),
+                                   sp->smem_nodes, ray, valid, nullptr);
+    }
+}
+
+template <int C, int MODE>
+__global__ void __launch_bounds__(128, 4)
+    k_batch_resume32(const BatchProblem *__restrict__ probs, const QEntry *q,
+                     const unsigned long long *q_count, int64_t q_cap) {
+    const unsigned long long n = min(*q_count, (unsigned long long)q_cap);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n;
+         base += stride) {
+        const unsigned long long kq = base + threadIdx.x;
+        const bool valid = kq < n;
+        const QEntry *qe = q + (valid ? kq : 0);
+        const int64_t tagged = valid ? qe->ray : 0;
+        const int prob = (int)(tagged >> TP_BATCH_TAG_SHIFT);
+        const int64_t ray = tagged & ((int64_t(1) << TP_BATCH_TAG_SHIFT) - 1);
+        walk32_ray<C, MODE, true>(probs[prob].p, nullptr, 0, ray, valid, qe);
+    }
+}
+
+static size_t batch_smem(int smem_nodes) {
+    return (size_t)(TP_BATCH_THREADS / 32) * (kBatchParamVec * 16 + (size_t)smem_nodes * sizeof(BvhNode));
+}
+
+template <int C, int MODE>
+static cudaError_t batch_grid_mode(int smem_nodes, unsigned &grid) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch32<C, MODE>,
+                                                                  TP_BATCH_THREADS,
+                                                                  batch_smem(smem_nodes));
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    grid = (unsigned)(per_sm * sm_count());
+    return cudaSuccess;
+}
+
+cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid) {
+    if (mode == MODE_FWD)
+        return channels == 4 ? batch_grid_mode<4, MODE_FWD>(smem_nodes, grid)
+                             : batch_grid_mode<1, MODE_FWD>(smem_nodes, grid);
+    return channels == 4 ? batch_grid_mode<4, MODE_BWD>(smem_nodes, grid)
+                         : batch_grid_mode<1, MODE_BWD>(smem_nodes, grid);
+}
+
+template <int C, int MODE>
+static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *item_begin,
+                                     int nprob, int64_t nitems, unsigned grid,
+                                     unsigned rgrid, QEntry *q, unsigned long long *q_count,
+                                     int64_t q_cap, unsigned *item_counter,
+                                     int smem_nodes, cudaStream_t stream) {
+    // rounds of whole chunks of warp items (32 rays each), at most q_cap rays
+    const int64_t round_items = (q_cap / (32 * kBatchChunk)) * kBatchChunk;
+    if (round_items < 1) return cudaErrorInvalidValue;
+    for (int64_t r0 = 0; r0 < nitems; r0 += round_items) {
+        const int64_t r1 = nitems - r0 < round_items ? nitems : r0 + round_items;
+        cudaError_t e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(q_count, 0, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return e;
+        k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
+            probs, item_begin, nprob, r0, r1, item_counter, smem_nodes);
+        k_batch_resume32<C, MODE><<<rgrid, 128, 0, stream>>>(probs, q, q_count, q_cap);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, int nprob,
+                         int64_t nitems, int channels, int mode, unsigned grid,
+                         unsigned rgrid, QEntry *q, unsigned long long *q_count, int64_t q_cap,
+                         unsigned *item_counter, int smem_nodes, cudaStream_t stream) {
+    if (nitems <= 0) return cudaSuccess;
+    if (grid < 1 || rgrid < 1) return cudaErrorInvalidValue;
+#define TP_BATCH_ARGS probs, item_begin, nprob, nitems, grid, rgrid, q, q_count, q_cap, \
+                      item_counter, smem_nodes, stream
+    if (mode == MODE_FWD)
+        return channels == 4 ? launch_batch_mode<4, MODE_FWD>(TP_BATCH_ARGS)
+                             : launch_batch_mode<1, MODE_FWD>(TP_BATCH_ARGS);
+    return channels == 4 ? launch_batch_mode<4, MODE_BWD>(TP_BATCH_ARGS)
+                         : launch_batch_mode<1, MODE_BWD>(TP_BATCH_ARGS);
+#undef TP_BATCH_ARGS
+}
+
+int device_sm_count() { return sm_count(); }
+
 // ============================================================ small kernels
 
 template <typename T>
@@ -957,17 +1199,6 @@ __global__ void k_side(const double *S, const double *P, const double *p, const 
 }
 
 // ================================================================ launchers
-
-static int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
 
 template <int C, int MODE>
 static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks, int threads,

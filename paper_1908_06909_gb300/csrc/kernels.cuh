@@ -52,7 +52,35 @@ struct KParams {
     struct QEntry *q;
     unsigned long long *q_count;
     int64_t q_cap;
+    // OR-ed into the ray index of queue entries (batched launches: the problem
+    // index in bits 40+; 0 otherwise)
+    int64_t qtag;
 };
+
+// One problem of a batched launch: its parameters (operands included) and a
+// spare 16 bytes so the 16-byte-vector copy into shared memory stays in bounds.
+struct __align__(16) BatchProblem {
+    KParams p;
+    int64_t spare[2];
+};
+
+// Warp items per work chunk of the batched walk; every problem's item range
+// starts at a multiple of it (a whole number of tiles of up to 256 rays).
+constexpr int kBatchChunk = 8;
+
+// Batched filtered walk over `nitems` warp items (32 rays of one tile) of
+// `nprob` problems (problem k owns items [item_begin[k], item_begin[k+1]),
+// item_begin[k] a multiple of kBatchChunk), in
+// rounds of at most q_cap rays: per round one persistent work-queue launch of
+// `grid` CTAs and one resume launch of `rgrid` CTAs.  `smem_nodes`: BVH nodes
+// staged per warp.  Only stream operations (graph-capturable).
+cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, int nprob,
+                         int64_t nitems, int channels, int mode, unsigned grid, unsigned rgrid,
+                         QEntry *q, unsigned long long *q_count, int64_t q_cap,
+                         unsigned *item_counter, int smem_nodes, cudaStream_t stream);
+// Persistent grid for the batched walk: resident CTAs per SM x SM count.
+cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid);
+int device_sm_count();
 
 // one launch of the walk; returns a cudaError_t
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,

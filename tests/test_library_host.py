@@ -180,3 +180,22 @@ def test_fp32_filter_sound_near_threshold(tp):
     assert fp32.size > 3000 and (stage != 0).sum() > 5000
     for k in fp32:
         assert sign[k] == exact.side_sign_int(S[k], P[k], p[k], q[k]), k
+
+
+def test_batch_argument_errors(tp):
+    """Batch entry points reject bad arguments before touching the device."""
+    import ctypes as C
+    from paper_1908_06909_gb300 import _lib
+    L = tp._lib.load()
+    h = C.c_void_p(7)
+    assert L.tetproj_batch_create(None, None, None, 3, 1, C.byref(h)) == _lib.ERR_ARG
+    assert h.value is None
+    arr = (C.c_void_p * 1)(None)
+    assert L.tetproj_batch_create(arr, arr, None, 0, 1, C.byref(h)) == _lib.ERR_ARG
+    assert L.tetproj_batch_create(arr, arr, None, 1, 2, C.byref(h)) == _lib.ERR_ARG
+    assert L.tetproj_batch_create(arr, arr, None, 1, 1, C.byref(h)) == _lib.ERR_ARG  # null handles
+    assert L.tetproj_batch_create(arr, arr, None, 1, 1, None) == _lib.ERR_ARG
+    assert L.tetproj_batch_bind(None, None, None, None, None) == _lib.ERR_ARG
+    assert L.tetproj_batch_forward(None, None) == _lib.ERR_ARG
+    assert L.tetproj_batch_backward(None, None) == _lib.ERR_ARG
+    assert L.tetproj_batch_destroy(None) == _lib.ERR_ARG
