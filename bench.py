@@ -47,6 +47,38 @@ BYTES_FACE = 48                      # one boundary face record
 LAYOUT_STEP = {("fwd", 1): 68, ("fwd", 4): 80, ("bwd", 1): 72, ("bwd", 4): 96}
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk32_kuhn96_traffic.md")
+WALK_SOURCES = ["kernels.cu", "kernels.cuh", "predicates.cuh", "tetproj_internal.h"]
+
+
+def measured_traffic(workload, tile, order, scatter):
+    """DRAM bytes per call {fwd, bwd} from the committed ncu capture of the bench
+    workload, or None if the walk sources changed since it was taken or the
+    launch configuration differs."""
+    import hashlib
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for f in WALK_SOURCES:
+        with open(os.path.join(ROOT, "paper_1908_06909_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    vals = {}
+    for line in text.splitlines():
+        parts = line.split()
+        if len(parts) == 2 and parts[0] == "source_sha256":
+            vals["sha"] = parts[1]
+        if parts and parts[0] == "workload":
+            vals["cfg"] = parts[1:]
+        if parts and parts[0] == "traffic_bytes_per_call":
+            vals["t"] = {k: int(v) for k, v in (p.split("=") for p in parts[1:])}
+    want = [workload, "tile", tile, "order", order, "scatter", scatter, "channels", "1"]
+    if vals.get("sha") != h.hexdigest() or vals.get("cfg") != want or "t" not in vals:
+        return None
+    return vals["t"]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -135,6 +167,16 @@ def walk_launches(geo, tu, tv):
     q = -(-min(geo.nrays, QUEUE_MAX) // 4096) * 4096
     per_chunk = max(1, q // (tu * tv))
     return 1 + 2 * -(-tiles // per_chunk)
+
+
+L2_BYTES = 129e6
+
+
+def l2_note(nt, nrays, C):
+    rec, proj = nt * 64, nrays * 4 * C
+    kind = "larger" if rec + proj > L2_BYTES else "SMALLER"
+    return (f"inputs {kind} than L2, not flushed (tet records {rec / 1e6:.0f} MB, "
+            f"projections {proj / 1e6:.0f} MB)")
 
 
 def cpu_baseline(w, nsample, threads=None):
@@ -580,9 +622,13 @@ def main():
     dom_ms = bwd_ms if dom == "bwd" else fwd_ms
     dom_bytes = alg_bytes(sb if dom == "bwd" else sf, dom)
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    tr = measured_traffic(w.name, args.tile, "morton", args.scatter)
     roof = {"bound": "hbm", "kernel": f"k_walk32<1,{'MODE_BWD' if dom == 'bwd' else 'MODE_FWD'}>",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "peak_kind": peak_kind,
+            "traffic": None if tr is None else tr[dom], "peak_kind": peak_kind,
+            "traffic_note": ("DRAM read+write bytes per call, ncu capture in "
+                             "profiles/walk32_kuhn96_traffic.md (cold cache per launch)")
+                            if tr is not None else "no capture for this build/configuration",
             "bytes_per_launch": dom_bytes, "ms_per_launch": dom_ms,
             "layout_gbs": alg_bytes(sb if dom == "bwd" else sf, dom, LAYOUT_STEP) / (dom_ms / 1e3) / 1e9,
             "fwd_ms": fwd_ms, "bwd_ms": bwd_ms}
@@ -604,7 +650,7 @@ def main():
             "config": {"workload": w.name, "nt": mesh.nt, "rays_per_step": nrays,
                        "channels": C, "precision": "filtered", "tile": args.tile,
                        "scatter": args.scatter,
-                       "l2": "inputs larger than L2 (tet records 340 MB, projections 377 MB)",
+                       "l2": l2_note(mesh.nt, nrays, C),
                        "parallelism": f"replicas{world}"},
             "gsegments_per_s": world * segs / (ms_step / 1e3) / 1e9,
             "segments_per_step": segs,
