@@ -473,7 +473,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--scatter", default="atomic", choices=["atomic", "warp"])
+    ap.add_argument("--scatter", default="atomic", choices=["atomic", "warp", "sort"])
     ap.add_argument("--tile", default="8x8")
     ap.add_argument("--tune-cache", default=None)
     args = ap.parse_args()
@@ -507,8 +507,9 @@ def main():
     mesh = tp.Mesh(w.verts, w.tets)
     geo = tp.Geometry.from_cone(w.geom)
     tu, tv = (int(x) for x in args.tile.split("x"))
-    opt = tp.make_options(tile=(tu, tv), scatter=tp.SCATTER_WARP if args.scatter == "warp"
-                          else tp.SCATTER_ATOMIC)
+    opt = tp.make_options(tile=(tu, tv), scatter={"atomic": tp.SCATTER_ATOMIC,
+                                                  "warp": tp.SCATTER_WARP,
+                                                  "sort": tp.SCATTER_SORT}[args.scatter])
     C = 1
     mu = torch.tensor(w.mu, dtype=torch.float32, device="cuda")
     proj = torch.empty(geo.shape, dtype=torch.float32, device="cuda")

@@ -79,6 +79,8 @@ typedef int32_t tetproj_status;
 /* backprojection scatter */
 #define TETPROJ_SCATTER_ATOMIC 0  /* one atomic add per segment                     */
 #define TETPROJ_SCATTER_WARP 1    /* lanes of a warp on the same tet merge first     */
+#define TETPROJ_SCATTER_SORT 2    /* segment sort-and-reduce: deterministic (see
+                                     tetproj_backward); filtered path, cone rays   */
 
 typedef struct tetproj_mesh tetproj_mesh;
 typedef struct tetproj_geometry tetproj_geometry;
@@ -87,9 +89,9 @@ typedef struct tetproj_options {
     int32_t precision; /* TETPROJ_FILTERED (default) or TETPROJ_PLAIN_FP64            */
     int32_t channels;  /* C: 1 (default) or 4                                          */
     int32_t tile_u;    /* ray tile width in pixels: 1..32, power of two (default 8)    */
-    int32_t tile_v;    /* ray tile height: tile_u*tile_v in {32,64,128,256,512}        */
+    int32_t tile_v;    /* ray tile height: tile_u*tile_v in {32,64,128,256}            */
     int32_t order;     /* TETPROJ_ORDER_MORTON (default) or TETPROJ_ORDER_ROW          */
-    int32_t scatter;   /* TETPROJ_SCATTER_ATOMIC (default) or TETPROJ_SCATTER_WARP     */
+    int32_t scatter;   /* TETPROJ_SCATTER_ATOMIC (default), _WARP or _SORT             */
     int32_t max_steps; /* walk step limit per ray; 0 = 64 + 16*ceil(nt^(1/3))          */
     int32_t flags;     /* reserved, must be 0                                          */
 } tetproj_options;
@@ -179,7 +181,18 @@ tetproj_status tetproj_geometry_rays(const tetproj_geometry *geo, const int64_t 
  *   mu: device [nt][C]; proj: device [nangles][nv][nu][C] (overwritten).
  * tetproj_backward (Eq. 3): mu_out[i][c] = sum_j a_ij proj[j][c] (overwritten).
  * opt may be NULL (defaults).  Both are exact adjoints of each other up to
- * floating-point rounding. */
+ * floating-point rounding.
+ * Backprojection scatter (Sec. II-F adds with atomics): _ATOMIC and _WARP add
+ * each segment's length x y into its tet atomically, in an order the hardware
+ * picks.  _SORT (filtered path only) writes the segments (tet, length x y) of
+ * a chunk of rays to a buffer at positions fixed by the rays' segment counts,
+ * sorts them stably by tet and sums each tet's run in that order, so the
+ * result is bit-reproducible.  Its first call for a (mesh, geometry, tile
+ * shape, ordering) builds a segment plan (a counting walk; synchronous;
+ * 8 B per ray + 16 B per tile block), reused while the mesh's last plan
+ * matches; sort buffers of 2^27 segments (2 GB at C = 1, 5 GB at C = 4) are
+ * allocated on first use.  Later calls are asynchronous and allocate nothing.
+ * Errors of the counting walk are returned by the call that builds the plan. */
 tetproj_status tetproj_forward(const tetproj_mesh *mesh, const tetproj_geometry *geo,
                                const void *mu, void *proj, const tetproj_options *opt,
                                void *stream);

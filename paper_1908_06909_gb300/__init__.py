@@ -18,13 +18,13 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (FILTERED, ORDER_MORTON, ORDER_ROW, PLAIN_FP64, SCATTER_ATOMIC, SCATTER_WARP,
-                   Options, TetprojError, check)
+from ._lib import (FILTERED, ORDER_MORTON, ORDER_ROW, PLAIN_FP64, SCATTER_ATOMIC, SCATTER_SORT,
+                   SCATTER_WARP, Options, TetprojError, check)
 
 __all__ = ["Mesh", "Geometry", "Batch", "forward", "backward", "backward_noalloc", "forward_rays", "backward_rays",
            "trace_rays", "side_signs_host", "side_signs_device", "TetProject", "make_options",
            "FILTERED", "PLAIN_FP64", "ORDER_ROW", "ORDER_MORTON", "SCATTER_ATOMIC",
-           "SCATTER_WARP", "TetprojError", "library_path"]
+           "SCATTER_WARP", "SCATTER_SORT", "TetprojError", "library_path"]
 
 
 def library_path() -> str:

@@ -27,6 +27,7 @@ ORDER_ROW = 0
 ORDER_MORTON = 1
 SCATTER_ATOMIC = 0
 SCATTER_WARP = 1
+SCATTER_SORT = 2
 
 c_vp = ctypes.c_void_p
 c_i32 = ctypes.c_int32

@@ -5,8 +5,9 @@ fastest (Sec. II-F).  This module does the same per *size class* of problem
 and caches the result on disk:
 
 * space: ray tile (tile_u x tile_v threads per CTA), tile ordering (row-major
-  or Morton inside the tile) and backprojection scatter (plain atomics or
-  warp-aggregated atomics);
+  or Morton inside the tile) and backprojection scatter (plain atomics,
+  warp-aggregated atomics, or the deterministic segment sort-and-reduce; the
+  batched launch adds atomically, so batches choose between the first two);
 * size class: (ceil log2 of the tet count, ceil log2 of the detector pixel
   count, channels, threads per CTA or "any");
 * measurement: forward + backward on a reduced scan of the problem itself (a
@@ -45,8 +46,10 @@ TILES = {
     128: [(16, 8), (8, 16), (32, 4)],
     256: [(16, 16), (32, 8)],
 }
+SCATTER_SORT = 2
 ORDERS = (ORDER_MORTON, ORDER_ROW)
-SCATTERS = (SCATTER_ATOMIC, SCATTER_WARP)
+SCATTERS = (SCATTER_ATOMIC, SCATTER_WARP, SCATTER_SORT)
+BATCH_SCATTERS = (SCATTER_ATOMIC, SCATTER_WARP)  # the batched launch adds atomically
 MAX_TUNE_RAYS = 2_000_000
 BATCH_MIN_THREADS = 32  # the batched kernel walks 32-ray slices of a tile
 
@@ -85,17 +88,17 @@ def candidates(threads: int | None = None, min_threads: int = 32):
     return out
 
 
-def search(measure, threads: int | None = None, min_threads: int = 32):
+def search(measure, threads: int | None = None, min_threads: int = 32, scatters=SCATTERS):
     """Pick (Choice, best_ms) with measure(Choice, what) -> ms, what in
-    {"fwd+bwd", "bwd"}: tile/order on fwd+bwd with atomic scatter, then scatter
-    on bwd with the chosen tile."""
+    {"fwd+bwd", "bwd"}: tile/order on fwd+bwd with atomic scatter, then the
+    scatter among `scatters` on bwd with the chosen tile."""
     best, best_ms = None, math.inf
     for tu, tv, o in candidates(threads, min_threads):
         c = Choice(tu, tv, o, SCATTER_ATOMIC)
         ms = measure(c, "fwd+bwd")
         if ms < best_ms:
             best, best_ms = c, ms
-    bwd = {s: measure(Choice(best.tile_u, best.tile_v, best.order, s), "bwd") for s in SCATTERS}
+    bwd = {s: measure(Choice(best.tile_u, best.tile_v, best.order, s), "bwd") for s in scatters}
     s = min(bwd, key=lambda k: (bwd[k], k))
     if s != best.scatter:
         best_ms += bwd[s] - bwd[best.scatter]
@@ -139,14 +142,14 @@ class Cache:
 
 
 def tune_problem(key: str, make_measure, threads: int | None, cache: Cache | None,
-                 min_threads: int = 32):
+                 min_threads: int = 32, scatters=SCATTERS):
     """(Choice, ms) for a size class: from the cache, else by search() over the
     callback make_measure() returns (built only on a cache miss)."""
     if cache is not None:
         hit = cache.get(key)
         if hit is not None:
             return hit
-    choice, ms = search(make_measure(), threads, min_threads)
+    choice, ms = search(make_measure(), threads, min_threads, scatters)
     if cache is not None:
         cache.put(key, choice, ms)
     return choice, ms
@@ -235,10 +238,12 @@ def tune_batch(tp, meshes, geos, channels: int = 1, cache=None, reps: int = 3):
     memo = {}
     out = []
     for m, g in zip(meshes, geos):
-        key = size_class(m.nt, g.nu * g.nv, channels, None, min_threads=BATCH_MIN_THREADS)
+        key = size_class(m.nt, g.nu * g.nv, channels, None,
+                         min_threads=BATCH_MIN_THREADS) + "_batch"
         if key not in memo:
             memo[key] = tune_problem(key, lambda m=m, g=g: gpu_measure(tp, m, g, channels, reps),
-                                     None, c, min_threads=BATCH_MIN_THREADS)[0]
+                                     None, c, min_threads=BATCH_MIN_THREADS,
+                                     scatters=BATCH_SCATTERS)[0]
         out.append(memo[key])
     if c is not None:
         c.save()

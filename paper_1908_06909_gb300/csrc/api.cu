@@ -5,16 +5,50 @@
 // configuration.  Every step of the projection itself runs in kernels.cu.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "../../include/tetproj.h"
 #include "kernels.cuh"
 #include "mesh_build.h"
 
 using namespace tp;
+
+// Segment plan of the sort-and-reduce backprojection for one (geometry, tile
+// shape, ordering): per-ray segment counts and offsets, and the split of the
+// tile blocks into chunks whose segments fit the sort buffers.  It depends on
+// the mesh and the rays only, so it is built once and reused.
+struct SegPlan {
+    bool valid = false;
+    uint64_t geo_uid = 0;
+    int32_t tu = 0, tv = 0, morton = 0;
+    int64_t nrays = 0, nblocks = 0;
+    int32_t *count = nullptr;    // [nrays] segments per ray
+    int32_t *ray_off = nullptr;  // [nrays] offset inside the ray's tile block
+    int64_t *block_cnt = nullptr, *block_off = nullptr, *scan_tmp = nullptr;
+    DevCounters *counters = nullptr;  // the counting walk's own counters
+    std::vector<int64_t> chunk_b, chunk_s;  // chunk boundaries: blocks, segments
+    int64_t max_chunk = 0;
+    int64_t bytes = 0;
+};
+
+// Sort buffers (double-buffered keys and C-float values) and radix scratch.
+struct SortWs {
+    uint32_t *k[2] = {nullptr, nullptr};
+    float *v[2] = {nullptr, nullptr};
+    uint32_t *hist = nullptr, *tmp = nullptr;
+    int64_t cap = 0;
+    int32_t cap_c = 0;
+    int64_t bytes = 0;
+};
+
+// Segments per sort chunk (pairs of a 4-byte key and 4C bytes of values,
+// double-buffered: 2 GB at C = 1, 5 GB at C = 4).
+static const int64_t kSegChunk = int64_t(1) << 27;
 
 struct tetproj_mesh {
     int device = 0;
@@ -36,13 +70,18 @@ struct tetproj_mesh {
     unsigned long long *q_count = nullptr;
     int64_t q_cap = 0;
     int64_t base_bytes = 0;
+    SegPlan plan;
+    SortWs sort;
 };
 
 // Largest deferral queue (entries of 64 B); launches over more rays are chunked.
 static const int64_t kQueueMax = int64_t(1) << 23;
 
+static std::atomic<uint64_t> g_geometry_uid{1};
+
 struct tetproj_geometry {
     int device = 0;
+    uint64_t uid = 0;  // distinguishes geometries for cached segment plans
     AngleFrame *frames = nullptr;
     int32_t nu = 0, nv = 0, na = 0;
     double du = 0, dv = 0, dso = 0, dsd = 0;
@@ -58,6 +97,13 @@ static tetproj_status cuda_status(cudaError_t e) {
         cudaError_t _e = (x);                              \
         if (_e != cudaSuccess) return cuda_status(_e);     \
     } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T **p, int64_t n, int64_t &bytes) {
+    cudaError_t e = cudaMalloc((void **)p, (size_t)(n > 0 ? n : 1) * sizeof(T));
+    if (e == cudaSuccess) bytes += (n > 0 ? n : 1) * (int64_t)sizeof(T);
+    return e;
+}
 
 template <typename T>
 static cudaError_t upload(T **dst, const std::vector<T> &src) {
@@ -102,8 +148,30 @@ const char *tetproj_status_string(tetproj_status s) {
     }
 }
 
+static void plan_free(SegPlan &pl) {
+    cudaFree(pl.count);
+    cudaFree(pl.ray_off);
+    cudaFree(pl.block_cnt);
+    cudaFree(pl.block_off);
+    cudaFree(pl.scan_tmp);
+    cudaFree(pl.counters);
+    pl = SegPlan();
+}
+
+static void sort_free(SortWs &w) {
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(w.k[i]);
+        cudaFree(w.v[i]);
+    }
+    cudaFree(w.hist);
+    cudaFree(w.tmp);
+    w = SortWs();
+}
+
 static void mesh_free(tetproj_mesh *m) {
     if (!m) return;
+    plan_free(m->plan);
+    sort_free(m->sort);
     cudaFree(m->rec32);
     cudaFree(m->rec64);
     cudaFree(m->bvh);
@@ -173,7 +241,8 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *m, tetproj_mesh_info *o
     o->nboundary = m->nb;
     o->nbvh_nodes = m->nnodes;
     o->nflipped = m->nflipped;
-    int64_t b = m->base_bytes + m->q_cap * (int64_t)sizeof(QEntry) + (m->q_count ? 8 : 0);
+    int64_t b = m->base_bytes + m->q_cap * (int64_t)sizeof(QEntry) + (m->q_count ? 8 : 0) +
+                m->plan.bytes + m->sort.bytes;
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) b += m->ws_bytes[i][j];
     o->device_bytes = b;
@@ -287,6 +356,7 @@ tetproj_status tetproj_geometry_create(double dso, double dsd, int32_t nu, int32
     g->dv = dv;
     g->dso = dso;
     g->dsd = dsd;
+    g->uid = g_geometry_uid.fetch_add(1);
     cudaError_t e = upload(&g->frames, F);
     if (e != cudaSuccess) {
         delete g;
@@ -338,7 +408,8 @@ static tetproj_status check_opts(const tetproj_options *in, tetproj_options &o) 
     int t = o.tile_u * o.tile_v;
     if (t < 32 || t > 256) return TETPROJ_ERR_ARG;
     if (o.order != TETPROJ_ORDER_ROW && o.order != TETPROJ_ORDER_MORTON) return TETPROJ_ERR_ARG;
-    if (o.scatter != TETPROJ_SCATTER_ATOMIC && o.scatter != TETPROJ_SCATTER_WARP)
+    if (o.scatter != TETPROJ_SCATTER_ATOMIC && o.scatter != TETPROJ_SCATTER_WARP &&
+        o.scatter != TETPROJ_SCATTER_SORT)
         return TETPROJ_ERR_ARG;
     if (o.max_steps < 0 || o.flags != 0) return TETPROJ_ERR_ARG;
     return TETPROJ_OK;
@@ -420,6 +491,133 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
     return TETPROJ_OK;
 }
 
+// ------------------------------------------ sort-and-reduce backprojection
+
+// Builds (or reuses) the segment plan of (mesh, geometry, tile options):
+// a counting walk (trace mode, no tets stored) gives each ray's number of
+// segments; per tile block their exclusive prefix (ray_off) and total; a scan
+// of the totals gives each block's first segment.  Chunks of consecutive
+// blocks hold at most kSegChunk segments and q_cap rays.  Synchronous.
+static tetproj_status ensure_plan(tetproj_mesh *m, const tetproj_geometry *geo, const KParams &p,
+                                  cudaStream_t s) {
+    SegPlan &pl = m->plan;
+    if (pl.valid && pl.geo_uid == geo->uid && pl.tu == p.tu && pl.tv == p.tv &&
+        pl.morton == p.morton)
+        return TETPROJ_OK;
+    TP_CUDA(cudaStreamSynchronize(s));
+    plan_free(pl);
+    const int threads = p.tu * p.tv;
+    const int64_t nblocks = (int64_t)p.g.na * p.tiles_u * p.tiles_v;
+    pl.nrays = p.nrays;
+    pl.nblocks = nblocks;
+    cudaError_t e = dalloc(&pl.count, p.nrays, pl.bytes);
+    if (e == cudaSuccess) e = dalloc(&pl.ray_off, p.nrays, pl.bytes);
+    if (e == cudaSuccess) e = dalloc(&pl.block_cnt, nblocks, pl.bytes);
+    if (e == cudaSuccess) e = dalloc(&pl.block_off, nblocks + 1, pl.bytes);
+    if (e == cudaSuccess) e = dalloc(&pl.scan_tmp, scan_temp_elems(nblocks), pl.bytes);
+    if (e == cudaSuccess) e = dalloc(&pl.counters, 1, pl.bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl.counters, 0, sizeof(DevCounters), s);
+    if (e != cudaSuccess) { plan_free(pl); return cuda_status(e); }
+    KParams pc = p;
+    pc.m.counters = pl.counters;  // the user's statistics count only real calls
+    pc.tr_tet = nullptr;
+    pc.tr_len = nullptr;
+    pc.tr_count = pl.count;
+    pc.max_visits = 0;
+    e = launch_walk(pc, TETPROJ_FILTERED, 1, MODE_TRACE, s);
+    if (e == cudaSuccess) e = launch_block_offsets(pc, pl.count, pl.ray_off, pl.block_cnt, nblocks, s);
+    if (e == cudaSuccess) e = launch_scan_i64(pl.block_cnt, pl.block_off, nblocks, pl.scan_tmp, s);
+    std::vector<int64_t> off((size_t)nblocks + 1);
+    DevCounters dc;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(off.data(), pl.block_off, sizeof(int64_t) * (nblocks + 1),
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&dc, pl.counters, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { plan_free(pl); return cuda_status(e); }
+    if (dc.error != 0) { int code = dc.error; plan_free(pl); return code; }
+    // chunks: consecutive blocks, <= kSegChunk segments and <= q_cap rays
+    const int64_t max_blocks = p.q_cap / threads;
+    pl.chunk_b.push_back(0);
+    pl.chunk_s.push_back(0);
+    int64_t b0 = 0;
+    while (b0 < nblocks) {
+        int64_t b1 = b0 + 1;
+        while (b1 < nblocks && b1 - b0 < max_blocks && off[b1 + 1] - off[b0] <= kSegChunk) ++b1;
+        if (off[b1] - off[b0] > kSegChunk) { plan_free(pl); return TETPROJ_ERR_TOO_LARGE; }
+        pl.chunk_b.push_back(b1);
+        pl.chunk_s.push_back(off[b1]);
+        if (off[b1] - off[b0] > pl.max_chunk) pl.max_chunk = off[b1] - off[b0];
+        b0 = b1;
+    }
+    pl.geo_uid = geo->uid;
+    pl.tu = p.tu;
+    pl.tv = p.tv;
+    pl.morton = p.morton;
+    pl.valid = true;
+    return TETPROJ_OK;
+}
+
+static tetproj_status ensure_sort_ws(tetproj_mesh *m, int64_t nseg, int channels) {
+    SortWs &w = m->sort;
+    if (w.k[0] && w.cap >= nseg && w.cap_c >= channels) return TETPROJ_OK;
+    cudaDeviceSynchronize();
+    const int64_t cap = nseg > w.cap ? nseg : w.cap;
+    const int cc = channels > w.cap_c ? channels : w.cap_c;
+    sort_free(w);
+    const int64_t hist = radix_hist_elems(cap);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = dalloc(&w.k[i], cap, w.bytes);
+        if (e == cudaSuccess) e = dalloc(&w.v[i], cap * cc, w.bytes);
+    }
+    if (e == cudaSuccess) e = dalloc(&w.hist, hist, w.bytes);
+    if (e == cudaSuccess) e = dalloc(&w.tmp, scan_temp_elems(hist), w.bytes);
+    if (e != cudaSuccess) { sort_free(w); return cuda_status(e); }
+    w.cap = cap;
+    w.cap_c = cc;
+    return TETPROJ_OK;
+}
+
+// mu_out = A^T y through the segment buffer: per chunk, the walk writes the
+// chunk's segments, a stable radix sort groups them by tet, and one thread per
+// tet sums its run in buffer order.  Deterministic.
+static tetproj_status run_backward_sort(tetproj_mesh *m, const tetproj_geometry *geo, KParams &p,
+                                        const tetproj_options &o, const void *y, void *mu_out,
+                                        cudaStream_t s) {
+    tetproj_status st = ensure_ws(m, o.precision, o.channels);
+    if (st == TETPROJ_OK) st = attach_queue(m, p, o);
+    if (st == TETPROJ_OK) st = ensure_plan(m, geo, p, s);
+    if (st == TETPROJ_OK) st = ensure_sort_ws(m, m->plan.max_chunk, o.channels);
+    if (st != TETPROJ_OK) return st;
+    const SegPlan &pl = m->plan;
+    SortWs &w = m->sort;
+    void *ws = m->ws[0][o.channels == 4];
+    TP_CUDA(cudaMemsetAsync(ws, 0, (size_t)m->ws_bytes[0][o.channels == 4], s));
+    int key_bits = 1;
+    while ((int64_t(1) << key_bits) < m->nt) ++key_bits;
+    p.in = y;
+    p.out = ws;
+    p.block_off = pl.block_off;
+    p.ray_off = pl.ray_off;
+    p.seg_key = w.k[0];
+    p.seg_val = w.v[0];
+    for (size_t c = 0; c + 1 < pl.chunk_b.size(); ++c) {
+        const int64_t n = pl.chunk_s[c + 1] - pl.chunk_s[c];
+        p.seg_base = pl.chunk_s[c];
+        p.seg_cap = n;
+        TP_CUDA(launch_walk_blocks(p, o.channels, MODE_SEG, pl.chunk_b[c], pl.chunk_b[c + 1], s));
+        uint32_t *ko = nullptr;
+        float *vo = nullptr;
+        TP_CUDA(launch_radix_sort(w.k[0], w.v[0], w.k[1], w.v[1], n, o.channels, key_bits, w.hist,
+                                  w.tmp, &ko, &vo, s));
+        TP_CUDA(launch_seg_reduce(ko, vo, n, o.channels, reinterpret_cast<float *>(ws), s));
+    }
+    TP_CUDA(launch_scatter_perm(m->perm, m->nt, o.channels, 0, ws, mu_out, s));
+    return TETPROJ_OK;
+}
+
 tetproj_status tetproj_forward(const tetproj_mesh *mesh, const tetproj_geometry *geo,
                                const void *mu, void *proj, const tetproj_options *opt,
                                void *stream) {
@@ -443,6 +641,10 @@ tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry
     tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
     KParams p = base_params(m, o);
     set_cone(p, geo);
+    if (o.scatter == TETPROJ_SCATTER_SORT) {
+        if (o.precision != TETPROJ_FILTERED) return TETPROJ_ERR_ARG;
+        return run_backward_sort(m, geo, p, o, proj, mu_out, (cudaStream_t)stream);
+    }
     return run_backward(m, p, o, proj, mu_out, (cudaStream_t)stream);
 }
 
@@ -471,6 +673,7 @@ tetproj_status tetproj_backward_rays(const tetproj_mesh *mesh, const double *src
     tetproj_options o;
     tetproj_status st = check_opts(opt, o);
     if (st != TETPROJ_OK) return st;
+    if (o.scatter == TETPROJ_SCATTER_SORT) return TETPROJ_ERR_ARG;  // cone geometries only
     tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
     KParams p = base_params(m, o);
     p.src_kind = 1;
@@ -587,6 +790,7 @@ extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
     if (!mesh || !geo || !proj || !mu_out) return TETPROJ_ERR_ARG;
     tetproj_options o;
     tetproj_status st = check_opts(opt, o);
+    if (st == TETPROJ_OK && o.scatter == TETPROJ_SCATTER_SORT) st = TETPROJ_ERR_ARG;  // allocates
     if (st != TETPROJ_OK) return st;
     const int f64 = o.precision == TETPROJ_PLAIN_FP64;
     const int64_t acc_bytes = mesh->nt * o.channels * (f64 ? 8 : 4);
@@ -683,6 +887,7 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
         }
         tetproj_options oo;
         tetproj_status st = check_opts(&o, oo);
+        if (st == TETPROJ_OK && oo.scatter == TETPROJ_SCATTER_SORT) st = TETPROJ_ERR_ARG;
         if (st != TETPROJ_OK) { batch_free(b); return st; }
         KParams p = base_params(meshes[k], oo);
         set_cone(p, geos[k]);

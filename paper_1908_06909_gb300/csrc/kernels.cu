@@ -384,6 +384,17 @@ __device__ __forceinline__ void defer_append(const KParams &p, bool want, int64_
     }
 }
 
+// First segment-buffer slot of cone ray `ray` (MODE_SEG): its tile block's
+// offset, minus the chunk's base, plus the ray's offset inside the block.
+__device__ __forceinline__ int64_t seg_slot(const KParams &p, int64_t ray) {
+    const int64_t t = ray / p.g.nu;
+    const int iu = (int)(ray - t * p.g.nu);
+    const int64_t a = t / p.g.nv;
+    const int iv = (int)(t - a * p.g.nv);
+    const int64_t b = (a * p.tiles_v + (iv >> p.log_tv)) * p.tiles_u + (iu >> p.log_tu);
+    return __ldg(p.block_off + b) - p.seg_base + __ldg(p.ray_off + ray);
+}
+
 // One filtered walk.  Fast kernel (ROBUST = false): `valid` rays start from
 // scratch.  Resume kernel (ROBUST = true): `qe` is the ray's queue entry; the
 // walk continues from the saved state (or from the entry search when the ray
@@ -466,12 +477,15 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             }
             alive = true;
         }
-        if (MODE == MODE_BWD && alive) {
+        if ((MODE == MODE_BWD || MODE == MODE_SEG) && alive) {
             const float *y = reinterpret_cast<const float *>(p.in) + ray * C;
 #pragma unroll
             for (int c = 0; c < C; ++c) yv[c] = __ldg(y + c);
         }
     }
+    // MODE_SEG: this ray's next slot in the segment buffer
+    int64_t spos = 0;
+    if (MODE == MODE_SEG && valid) spos = seg_slot(p, ray) + steps;
     if (!ROBUST) defer_append<C>(p, deferred, ray, 0, -1, Xin, 0, acc, comp);
     flush_counters(p.m.counters, cnt);
     cnt = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -599,6 +613,20 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                     }
                 }
             }
+        }
+        if (MODE == MODE_SEG && did) {
+            if (spos >= 0 && spos < p.seg_cap) {
+                p.seg_key[spos] = (uint32_t)hcur;
+                if (C == 4)
+                    reinterpret_cast<float4 *>(p.seg_val)[spos] =
+                        make_float4(len * yv[0], len * yv[1 % C], len * yv[2 % C], len * yv[3 % C]);
+                else
+                    p.seg_val[spos] = len * yv[0];
+            } else {
+                err = TETPROJ_ERR_TOO_LARGE;  // the plan's counts disagree with this walk
+                alive = false;
+            }
+            ++spos;
         }
         if (MODE == MODE_BWD) {
             if (!ROBUST && p.scatter == TETPROJ_SCATTER_WARP) {
@@ -1224,6 +1252,74 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+template <int C, int MODE>
+static cudaError_t launch_blocks_mode(const KParams &p0, int64_t b0, int64_t b1,
+                                      cudaStream_t stream) {
+    KParams p = p0;
+    const int threads = p.tu * p.tv;
+    const size_t smem = (size_t)p.smem_nodes * sizeof(BvhNode);
+    if (b1 <= b0) return cudaSuccess;
+    if ((b1 - b0) * threads > p.q_cap || b1 - b0 > 0x7fffffff) return cudaErrorInvalidValue;
+    p.block_offset = b0;
+    cudaError_t e = cudaMemsetAsync(p.q_count, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    k_walk32<C, MODE><<<(unsigned)(b1 - b0), threads, smem, stream>>>(p);
+    k_resume32<C, MODE><<<(unsigned)(4 * sm_count()), 128, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk_blocks(const KParams &p, int channels, int mode, int64_t b0, int64_t b1,
+                               cudaStream_t stream) {
+    if (p.src_kind != 0) return cudaErrorInvalidValue;
+    switch (mode) {
+    case MODE_FWD:
+        return channels == 4 ? launch_blocks_mode<4, MODE_FWD>(p, b0, b1, stream)
+                             : launch_blocks_mode<1, MODE_FWD>(p, b0, b1, stream);
+    case MODE_BWD:
+        return channels == 4 ? launch_blocks_mode<4, MODE_BWD>(p, b0, b1, stream)
+                             : launch_blocks_mode<1, MODE_BWD>(p, b0, b1, stream);
+    case MODE_SEG:
+        return channels == 4 ? launch_blocks_mode<4, MODE_SEG>(p, b0, b1, stream)
+                             : launch_blocks_mode<1, MODE_SEG>(p, b0, b1, stream);
+    default:
+        return launch_blocks_mode<1, MODE_TRACE>(p, b0, b1, stream);
+    }
+}
+
+// one CTA per tile block, threads = tile size (<= 256)
+__global__ void k_block_offsets(const __grid_constant__ KParams p, const int32_t *__restrict__ count,
+                                int32_t *__restrict__ ray_off, int64_t *__restrict__ block_cnt) {
+    __shared__ int64_t wsum[8];
+    int64_t ray = 0;
+    const bool valid = thread_ray_in(p, (int64_t)blockIdx.x, ray);
+    const int c = valid ? max(__ldg(count + ray), 0) : 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = c;  // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int64_t before = 0, total = 0;
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) {
+        if (i < w) before += wsum[i];
+        total += wsum[i];
+    }
+    if (valid) ray_off[ray] = (int32_t)(before + x - c);
+    if (threadIdx.x == 0) block_cnt[blockIdx.x] = total;
+}
+
+cudaError_t launch_block_offsets(const KParams &p, const int32_t *count, int32_t *ray_off,
+                                 int64_t *block_cnt, int64_t nblocks, cudaStream_t stream) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (nblocks > 0x7fffffff || p.src_kind != 0) return cudaErrorInvalidValue;
+    k_block_offsets<<<(unsigned)nblocks, p.tu * p.tv, 0, stream>>>(p, count, ray_off, block_cnt);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,

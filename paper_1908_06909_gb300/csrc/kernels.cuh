@@ -8,7 +8,9 @@
 
 namespace tp {
 
-enum { MODE_FWD = 0, MODE_BWD = 1, MODE_TRACE = 2 };
+// MODE_SEG: the backprojection's sort-and-reduce variant -- the walk writes
+// each segment (tet, length x y) to a segment buffer instead of adding it.
+enum { MODE_FWD = 0, MODE_BWD = 1, MODE_TRACE = 2, MODE_SEG = 3 };
 
 // One deferred ray: where its walk stopped, so the robust kernel continues
 // from there.  fs < 0: deferred during the entry search (no state yet);
@@ -55,6 +57,14 @@ struct KParams {
     // OR-ed into the ray index of queue entries (batched launches: the problem
     // index in bits 40+; 0 otherwise)
     int64_t qtag;
+    // MODE_SEG (cone rays only): segment j of ray r (tile block b) is written
+    // to seg_key / seg_val[(block_off[b] - seg_base + ray_off[r] + j)(*C)],
+    // for positions in [0, seg_cap)
+    uint32_t *seg_key;
+    float *seg_val;
+    const int64_t *block_off;
+    const int32_t *ray_off;
+    int64_t seg_base, seg_cap;
 };
 
 // One problem of a batched launch: its parameters (operands included) and a
@@ -81,6 +91,34 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
 // Persistent grid for the batched walk: resident CTAs per SM x SM count.
 cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid);
 int device_sm_count();
+
+// Filtered walk over the tile blocks [b0, b1) (b1 - b0 <= q_cap / threads):
+// one fast and one resume launch.  Cone rays; modes FWD, BWD, TRACE, SEG.
+cudaError_t launch_walk_blocks(const KParams &p, int channels, int mode, int64_t b0, int64_t b1,
+                               cudaStream_t stream);
+// Per tile block b: ray_off[r] = exclusive prefix of max(count[r], 0) over the
+// block's rays in thread order, block_cnt[b] = their sum (cone rays).
+cudaError_t launch_block_offsets(const KParams &p, const int32_t *count, int32_t *ray_off,
+                                 int64_t *block_cnt, int64_t nblocks, cudaStream_t stream);
+// Exclusive prefix sums out[0..n] of in[0..n-1] (out[n] = total); `tmp` holds
+// scan_temp_elems(n) elements.
+int64_t scan_temp_elems(int64_t n);
+cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp,
+                            cudaStream_t stream);
+cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp,
+                            cudaStream_t stream);
+// Stable LSD radix sort of n (key, C-float value) pairs by the low `key_bits`
+// bits of the key (8 bits per pass).  Sorted data ends in (*k_out, *v_out),
+// which point to either the a or the b buffers.  `hist` holds
+// radix_hist_elems(n) and `tmp` scan_temp_elems(radix_hist_elems(n)) words.
+int64_t radix_hist_elems(int64_t n);
+cudaError_t launch_radix_sort(uint32_t *k_a, float *v_a, uint32_t *k_b, float *v_b, int64_t n,
+                              int channels, int key_bits, uint32_t *hist, uint32_t *tmp,
+                              uint32_t **k_out, float **v_out, cudaStream_t stream);
+// acc[key][c] += sum of the run of equal keys (sorted order, Kahan), one thread
+// per run: deterministic.
+cudaError_t launch_seg_reduce(const uint32_t *keys, const float *vals, int64_t n, int channels,
+                              float *acc, cudaStream_t stream);
 
 // one launch of the walk; returns a cudaError_t
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,

@@ -24,14 +24,14 @@ def synthetic(best, bwd_best_scatter, calls):
 def test_search_finds_minimum(threads):
     cands = A.candidates(threads)
     for k, (tu, tv, o) in enumerate(cands):
-        for sc in (A.SCATTER_ATOMIC, A.SCATTER_WARP):
+        for sc in A.SCATTERS:
             calls = []
             choice, ms = A.search(synthetic((tu, tv, o), sc, calls), threads)
             assert choice == A.Choice(tu, tv, o, sc)
-            # every tile/order candidate measured once, plus the two scatters
-            assert len(calls) == len(cands) + 2
-            # with warp scatter the bwd part drops from 5.5 to 4.0
-            assert ms == pytest.approx(8.5 if sc == A.SCATTER_WARP else 10.0)
+            # every tile/order candidate measured once, plus each scatter
+            assert len(calls) == len(cands) + len(A.SCATTERS)
+            # a faster scatter than atomic drops the bwd part from 5.5 to 4.0
+            assert ms == pytest.approx(10.0 if sc == A.SCATTER_ATOMIC else 8.5)
 
 
 def test_candidates_respect_thread_count():
@@ -82,3 +82,10 @@ def test_candidates_hold_whole_warps():
     assert len(A.candidates(None, min_threads=128)) == 2 * (len(A.TILES[128]) + len(A.TILES[256]))
     assert A.size_class(10, 10, 4, None) == "t4_p4_c4_nany"
     assert A.size_class(10, 10, 4, None, 64) == "t4_p4_c4_nge64"
+
+
+def test_batch_scatter_space():
+    calls = []
+    ch, _ = A.search(synthetic((8, 8, 1), A.SCATTER_SORT, calls), None, scatters=A.BATCH_SCATTERS)
+    assert ch.scatter in A.BATCH_SCATTERS
+    assert sum(1 for _, what in calls if what == "bwd") == len(A.BATCH_SCATTERS)
