@@ -157,18 +157,6 @@ def build_workload(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
-QUEUE_MAX = 1 << 23  # rays per deferral-queue round (library constant)
-
-
-def walk_launches(geo, tu, tv):
-    """Kernels one filtered forward (or backward) call launches: a
-    permutation kernel plus a fast walk and a resume walk per queue chunk."""
-    tiles = -(-geo.nu // tu) * -(-geo.nv // tv) * geo.nangles
-    q = -(-min(geo.nrays, QUEUE_MAX) // 4096) * 4096
-    per_chunk = max(1, q // (tu * tv))
-    return 1 + 2 * -(-tiles // per_chunk)
-
-
 L2_BYTES = 129e6
 
 
@@ -275,10 +263,12 @@ def run_batch(args, tp, torch, dist, rank, world, local):
     assert sf["error"] == 0 and sb["error"] == 0, (sf, sb)
     torch.cuda.synchronize()
     gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    launches0 = tp.launch_count()
     with torch.cuda.graph(gf):
         b.forward()
     with torch.cuda.graph(gb):
         b.backward()
+    launches_per_step = tp.launch_count() - launches0  # kernels in the two graphs
     for _ in range(args.warmup):
         gf.replay()
         gb.replay()
@@ -397,11 +387,6 @@ def run_batch(args, tp, torch, dist, rank, world, local):
             "traffic": None, "peak_kind": peak_kind, "bytes_per_launch": dom_bytes,
             "ms_per_launch": dom_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
             "layout_gbs": alg_bytes(sb if dom == "bwd" else sf, dom, LAYOUT_STEP) / (dom_ms / 1e3) / 1e9}
-    # warp items of 32 rays; rounds of at most QUEUE_MAX rays
-    nitems = sum(-(-g.nu // r[0]) * -(-g.nv // r[1]) * g.nangles * (r[0] * r[1] // 32)
-                 for g, r in zip(geos, tiles))
-    q_cap = -(-min(nitems * 32, QUEUE_MAX) // 4096) * 4096
-    rounds = -(-nitems // (q_cap // 32))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
@@ -444,9 +429,9 @@ def run_batch(args, tp, torch, dist, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": {"value": world * nrays / (e2e_ms / 1e3), "unit": "rays/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            # per step: a gather and a scatter kernel per problem, and per
-            # round a persistent walk and a resume walk in each direction
-            "gpu_launches": args.steps * (2 * b.n + 4 * rounds),
+            # kernels captured in the two graphs (counted by the library at
+            # capture) times the replays of the timed region
+            "gpu_launches": args.steps * launches_per_step,
             "clocks": clk.summary(),
             "host_s": {"build": t_build, "tune": t_tune},
             "stats": {"fwd": sf, "bwd": sb},
@@ -538,6 +523,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = tp.launch_count()
     with ClockSampler(local) as clk:
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
@@ -551,6 +537,7 @@ def main():
             e2.record(stream)
         end.record(stream)
         torch.cuda.synchronize()
+    launches = tp.launch_count() - launches0
     if dist:
         dist.barrier()
     total_ms = start.elapsed_time(end)
@@ -659,7 +646,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * walk_launches(geo, tu, tv) * args.steps,
+            "gpu_launches": launches,
             "clocks": clk.summary(),
             "stats": {"fwd": sf, "bwd": sb},
         }

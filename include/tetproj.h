@@ -188,10 +188,11 @@ tetproj_status tetproj_geometry_rays(const tetproj_geometry *geo, const int64_t 
  * a chunk of rays to a buffer at positions fixed by the rays' segment counts,
  * sorts them stably by tet and sums each tet's run in that order, so the
  * result is bit-reproducible.  Its first call for a (mesh, geometry, tile
- * shape, ordering) builds a segment plan (a counting walk; synchronous;
+ * shape, ordering, C) builds a segment plan (a counting walk; synchronous;
  * 8 B per ray + 16 B per tile block), reused while the mesh's last plan
- * matches; sort buffers of 2^27 segments (2 GB at C = 1, 5 GB at C = 4) are
- * allocated on first use.  Later calls are asynchronous and allocate nothing.
+ * matches; sort buffers for chunks of 2^29 segments at C = 1 (8.6 GB) or 2^27
+ * at C = 4 (6.4 GB) are allocated on first use.  Later calls are
+ * asynchronous and allocate nothing.
  * Errors of the counting walk are returned by the call that builds the plan. */
 tetproj_status tetproj_forward(const tetproj_mesh *mesh, const tetproj_geometry *geo,
                                const void *mu, void *proj, const tetproj_options *opt,
@@ -290,6 +291,11 @@ tetproj_status tetproj_side_device(const double *S, const double *P, const doubl
 
 /* Library version (major*10000 + minor*100 + patch). */
 int32_t tetproj_version(void);
+
+/* Number of CUDA kernels this library has launched in this process, counted
+ * on the host at each launch (for benchmarks; no counterpart in the paper).
+ * Kernels replayed from a captured CUDA graph are counted once, at capture. */
+int64_t tetproj_launch_count(void);
 
 #ifdef __cplusplus
 }

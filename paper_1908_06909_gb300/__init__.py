@@ -31,6 +31,11 @@ def library_path() -> str:
     return _lib.LIB_PATH
 
 
+def launch_count() -> int:
+    """Kernels the library has launched in this process (host-side count)."""
+    return int(_lib.load().tetproj_launch_count())
+
+
 def version() -> str:
     v = int(_lib.load().tetproj_version())
     return f"{v // 10000}.{v // 100 % 100}.{v % 100}"

@@ -57,6 +57,7 @@ class MeshInfo(ctypes.Structure):
 # name -> (restype, argtypes); mirrors include/tetproj.h
 SIGNATURES = {
     "tetproj_version": (c_i32, []),
+    "tetproj_launch_count": (c_i64, []),
     "tetproj_default_options": (None, [ctypes.POINTER(Options)]),
     "tetproj_status_string": (ctypes.c_char_p, [c_i32]),
     "tetproj_mesh_create": (c_i32, [c_vp, c_i64, c_vp, c_i64, ctypes.POINTER(c_vp)]),

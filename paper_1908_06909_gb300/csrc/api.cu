@@ -25,7 +25,7 @@ using namespace tp;
 struct SegPlan {
     bool valid = false;
     uint64_t geo_uid = 0;
-    int32_t tu = 0, tv = 0, morton = 0;
+    int32_t tu = 0, tv = 0, morton = 0, channels = 0;
     int64_t nrays = 0, nblocks = 0;
     int32_t *count = nullptr;    // [nrays] segments per ray
     int32_t *ray_off = nullptr;  // [nrays] offset inside the ray's tile block
@@ -46,9 +46,10 @@ struct SortWs {
     int64_t bytes = 0;
 };
 
-// Segments per sort chunk (pairs of a 4-byte key and 4C bytes of values,
-// double-buffered: 2 GB at C = 1, 5 GB at C = 4).
-static const int64_t kSegChunk = int64_t(1) << 27;
+// Segments per sort chunk: 2^29 at C = 1 (8-byte records, double-buffered:
+// 8.6 GB), 2^27 at C = 4 (24 bytes per record: 6.4 GB).  Fewer chunks mean
+// fewer walk/resume launch tails.
+static int64_t seg_chunk(int channels) { return int64_t(1) << (channels == 4 ? 27 : 29); }
 
 struct tetproj_mesh {
     int device = 0;
@@ -117,6 +118,8 @@ static cudaError_t upload(T **dst, const std::vector<T> &src) {
 extern "C" {
 
 int32_t tetproj_version(void) { return 200; }
+
+int64_t tetproj_launch_count(void) { return (int64_t)launch_count(); }
 
 void tetproj_default_options(tetproj_options *o) {
     if (!o) return;
@@ -499,11 +502,12 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
 // of the totals gives each block's first segment.  Chunks of consecutive
 // blocks hold at most kSegChunk segments and q_cap rays.  Synchronous.
 static tetproj_status ensure_plan(tetproj_mesh *m, const tetproj_geometry *geo, const KParams &p,
-                                  cudaStream_t s) {
+                                  int channels, cudaStream_t s) {
     SegPlan &pl = m->plan;
     if (pl.valid && pl.geo_uid == geo->uid && pl.tu == p.tu && pl.tv == p.tv &&
-        pl.morton == p.morton)
+        pl.morton == p.morton && pl.channels == channels)
         return TETPROJ_OK;
+    const int64_t budget = seg_chunk(channels);
     TP_CUDA(cudaStreamSynchronize(s));
     plan_free(pl);
     const int threads = p.tu * p.tv;
@@ -537,21 +541,22 @@ static tetproj_status ensure_plan(tetproj_mesh *m, const tetproj_geometry *geo, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { plan_free(pl); return cuda_status(e); }
     if (dc.error != 0) { int code = dc.error; plan_free(pl); return code; }
-    // chunks: consecutive blocks, <= kSegChunk segments and <= q_cap rays
+    // chunks: consecutive blocks, <= budget segments and <= q_cap rays
     const int64_t max_blocks = p.q_cap / threads;
     pl.chunk_b.push_back(0);
     pl.chunk_s.push_back(0);
     int64_t b0 = 0;
     while (b0 < nblocks) {
         int64_t b1 = b0 + 1;
-        while (b1 < nblocks && b1 - b0 < max_blocks && off[b1 + 1] - off[b0] <= kSegChunk) ++b1;
-        if (off[b1] - off[b0] > kSegChunk) { plan_free(pl); return TETPROJ_ERR_TOO_LARGE; }
+        while (b1 < nblocks && b1 - b0 < max_blocks && off[b1 + 1] - off[b0] <= budget) ++b1;
+        if (off[b1] - off[b0] > budget) { plan_free(pl); return TETPROJ_ERR_TOO_LARGE; }
         pl.chunk_b.push_back(b1);
         pl.chunk_s.push_back(off[b1]);
         if (off[b1] - off[b0] > pl.max_chunk) pl.max_chunk = off[b1] - off[b0];
         b0 = b1;
     }
     pl.geo_uid = geo->uid;
+    pl.channels = channels;
     pl.tu = p.tu;
     pl.tv = p.tv;
     pl.morton = p.morton;
@@ -559,6 +564,9 @@ static tetproj_status ensure_plan(tetproj_mesh *m, const tetproj_geometry *geo, 
     return TETPROJ_OK;
 }
 
+// Sort buffers for nseg records: k[i] hold 8 bytes per record (C = 1 records,
+// or C = 4 keys) and v[i] 16 bytes (C = 4 values); the buffer a sort does not
+// end in is the run reduce's scratch.
 static tetproj_status ensure_sort_ws(tetproj_mesh *m, int64_t nseg, int channels) {
     SortWs &w = m->sort;
     if (w.k[0] && w.cap >= nseg && w.cap_c >= channels) return TETPROJ_OK;
@@ -567,13 +575,14 @@ static tetproj_status ensure_sort_ws(tetproj_mesh *m, int64_t nseg, int channels
     const int cc = channels > w.cap_c ? channels : w.cap_c;
     sort_free(w);
     const int64_t hist = radix_hist_elems(cap);
+    const int64_t tmp_h = scan_temp_elems(hist), tmp_r = scan_temp_elems(cap + 1);
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = dalloc(&w.k[i], cap, w.bytes);
-        if (e == cudaSuccess) e = dalloc(&w.v[i], cap * cc, w.bytes);
+        e = dalloc(&w.k[i], 2 * (cap + 1), w.bytes);
+        if (e == cudaSuccess) e = dalloc(&w.v[i], cc == 4 ? 4 * (cap + 1) : 1, w.bytes);
     }
     if (e == cudaSuccess) e = dalloc(&w.hist, hist, w.bytes);
-    if (e == cudaSuccess) e = dalloc(&w.tmp, scan_temp_elems(hist), w.bytes);
+    if (e == cudaSuccess) e = dalloc(&w.tmp, tmp_h > tmp_r ? tmp_h : tmp_r, w.bytes);
     if (e != cudaSuccess) { sort_free(w); return cuda_status(e); }
     w.cap = cap;
     w.cap_c = cc;
@@ -588,7 +597,7 @@ static tetproj_status run_backward_sort(tetproj_mesh *m, const tetproj_geometry 
                                         cudaStream_t s) {
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
     if (st == TETPROJ_OK) st = attach_queue(m, p, o);
-    if (st == TETPROJ_OK) st = ensure_plan(m, geo, p, s);
+    if (st == TETPROJ_OK) st = ensure_plan(m, geo, p, o.channels, s);
     if (st == TETPROJ_OK) st = ensure_sort_ws(m, m->plan.max_chunk, o.channels);
     if (st != TETPROJ_OK) return st;
     const SegPlan &pl = m->plan;
@@ -612,7 +621,10 @@ static tetproj_status run_backward_sort(tetproj_mesh *m, const tetproj_geometry 
         float *vo = nullptr;
         TP_CUDA(launch_radix_sort(w.k[0], w.v[0], w.k[1], w.v[1], n, o.channels, key_bits, w.hist,
                                   w.tmp, &ko, &vo, s));
-        TP_CUDA(launch_seg_reduce(ko, vo, n, o.channels, reinterpret_cast<float *>(ws), s));
+        // scratch: the key buffer the sorted records are not in (2 (n + 1) words)
+        uint32_t *scratch = ko == w.k[0] ? w.k[1] : w.k[0];
+        TP_CUDA(launch_seg_reduce(ko, vo, n, o.channels, reinterpret_cast<float *>(ws), scratch,
+                                  w.tmp, s));
     }
     TP_CUDA(launch_scatter_perm(m->perm, m->nt, o.channels, 0, ws, mu_out, s));
     return TETPROJ_OK;

@@ -23,6 +23,8 @@
 // * every warp runs its 32 rays in lock-step (the loop condition is a warp
 //   vote), which makes warp-level aggregation of backprojection atomics legal.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <math.h>
 
 #include "../../include/tetproj.h"
@@ -616,12 +618,14 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
         }
         if (MODE == MODE_SEG && did) {
             if (spos >= 0 && spos < p.seg_cap) {
-                p.seg_key[spos] = (uint32_t)hcur;
-                if (C == 4)
+                if (C == 4) {
+                    p.seg_key[spos] = (uint32_t)hcur;
                     reinterpret_cast<float4 *>(p.seg_val)[spos] =
                         make_float4(len * yv[0], len * yv[1 % C], len * yv[2 % C], len * yv[3 % C]);
-                else
-                    p.seg_val[spos] = len * yv[0];
+                } else {
+                    reinterpret_cast<uint2 *>(p.seg_key)[spos] =
+                        make_uint2((uint32_t)hcur, __float_as_uint(len * yv[0]));
+                }
             } else {
                 err = TETPROJ_ERR_TOO_LARGE;  // the plan's counts disagree with this walk
                 alive = false;
@@ -949,6 +953,10 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
 }
 
 
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 static int sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -1153,7 +1161,9 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
         if (e != cudaSuccess) return e;
         k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
             probs, item_begin, nprob, r0, r1, item_counter, smem_nodes);
+        note_launch();
         k_batch_resume32<C, MODE><<<rgrid, 128, 0, stream>>>(probs, q, q_count, q_cap);
+        note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1235,6 +1245,7 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
     if (precision != TETPROJ_FILTERED) {
         p.block_offset = 0;
         k_walk64<C, MODE><<<(unsigned)nblocks, threads, smem, stream>>>(p);
+        note_launch();
         return cudaGetLastError();
     }
     // chunks of at most q_cap rays, each followed by the resume kernel
@@ -1247,7 +1258,9 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
         cudaError_t e = cudaMemsetAsync(p.q_count, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
         k_walk32<C, MODE><<<(unsigned)nb, threads, smem, stream>>>(p);
+        note_launch();
         k_resume32<C, MODE><<<rgrid, 128, smem, stream>>>(p);
+        note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1266,7 +1279,9 @@ static cudaError_t launch_blocks_mode(const KParams &p0, int64_t b0, int64_t b1,
     cudaError_t e = cudaMemsetAsync(p.q_count, 0, sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
     k_walk32<C, MODE><<<(unsigned)(b1 - b0), threads, smem, stream>>>(p);
+    note_launch();
     k_resume32<C, MODE><<<(unsigned)(4 * sm_count()), 128, smem, stream>>>(p);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1319,6 +1334,7 @@ cudaError_t launch_block_offsets(const KParams &p, const int32_t *count, int32_t
     if (nblocks <= 0) return cudaSuccess;
     if (nblocks > 0x7fffffff || p.src_kind != 0) return cudaErrorInvalidValue;
     k_block_offsets<<<(unsigned)nblocks, p.tu * p.tv, 0, stream>>>(p, count, ray_off, block_cnt);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1357,6 +1373,7 @@ cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, in
     else
         k_gather_perm<float><<<(unsigned)blocks, 256, 0, stream>>>(
             perm, nt, channels, (const float *)src_user, (float *)dst_h);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1370,6 +1387,7 @@ cudaError_t launch_scatter_perm(const int32_t *perm, int64_t nt, int channels, i
     else
         k_scatter_perm<float><<<(unsigned)blocks, 256, 0, stream>>>(
             perm, nt, channels, (const float *)src_h, (float *)dst_user);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1377,6 +1395,7 @@ cudaError_t launch_geometry_rays(const GeoView &g, const int64_t *idx, int64_t n
                                  double *dst, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
     k_geometry_rays<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(g, idx, n, src, dst);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1385,6 +1404,7 @@ cudaError_t launch_side_device(const double *S, const double *P, const double *p
                                cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
     k_side<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(S, P, p, q, n, sign, stage);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -57,9 +57,10 @@ struct KParams {
     // OR-ed into the ray index of queue entries (batched launches: the problem
     // index in bits 40+; 0 otherwise)
     int64_t qtag;
-    // MODE_SEG (cone rays only): segment j of ray r (tile block b) is written
-    // to seg_key / seg_val[(block_off[b] - seg_base + ray_off[r] + j)(*C)],
-    // for positions in [0, seg_cap)
+    // MODE_SEG (cone rays only): segment j of ray r (tile block b) goes to
+    // slot s = block_off[b] - seg_base + ray_off[r] + j, s in [0, seg_cap):
+    // C = 1: uint2 (tet, value bits) at ((uint2 *)seg_key)[s]; C = 4: the tet
+    // at seg_key[s] and a float4 at ((float4 *)seg_val)[s]
     uint32_t *seg_key;
     float *seg_val;
     const int64_t *block_off;
@@ -107,18 +108,26 @@ cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t 
                             cudaStream_t stream);
 cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp,
                             cudaStream_t stream);
-// Stable LSD radix sort of n (key, C-float value) pairs by the low `key_bits`
-// bits of the key (8 bits per pass).  Sorted data ends in (*k_out, *v_out),
-// which point to either the a or the b buffers.  `hist` holds
+// Stable LSD radix sort of n segment records by the low `key_bits` bits of
+// the key (8 bits per pass).  Records: C = 1, uint2 (key, value bits) in the k
+// buffers (v unused); C = 4, keys in k and float4 values in v.  Sorted data
+// ends in (*k_out, *v_out), either the a or the b buffers.  `hist` holds
 // radix_hist_elems(n) and `tmp` scan_temp_elems(radix_hist_elems(n)) words.
 int64_t radix_hist_elems(int64_t n);
 cudaError_t launch_radix_sort(uint32_t *k_a, float *v_a, uint32_t *k_b, float *v_b, int64_t n,
                               int channels, int key_bits, uint32_t *hist, uint32_t *tmp,
                               uint32_t **k_out, float **v_out, cudaStream_t stream);
-// acc[key][c] += sum of the run of equal keys (sorted order, Kahan), one thread
-// per run: deterministic.
+// acc[key][c] += sum of each run of equal keys of the sorted records (Kahan,
+// in order): deterministic.  scratch: seg_reduce_scratch_elems(n) words; tmp:
+// scan_temp_elems(n) words.
+int64_t seg_reduce_scratch_elems(int64_t n);
 cudaError_t launch_seg_reduce(const uint32_t *keys, const float *vals, int64_t n, int channels,
-                              float *acc, cudaStream_t stream);
+                              float *acc, uint32_t *scratch, uint32_t *tmp, cudaStream_t stream);
+
+// Host-side count of the kernels this library has launched (every launcher
+// calls note_launch once per launch; graph replays are not seen).
+void note_launch();
+long long launch_count();
 
 // one launch of the walk; returns a cudaError_t
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
