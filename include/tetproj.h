@@ -274,6 +274,26 @@ tetproj_status tetproj_batch_forward(tetproj_batch *b, void *stream);
 tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream);
 tetproj_status tetproj_batch_destroy(tetproj_batch *b);
 
+/* ------------------------------------------------- the paper's own walk --
+ * Alg. 1 and 2 as printed (Sec. II-C..E): Moller-Trumbore ray-triangle tests
+ * with a safety margin eps = 1e-9 multiplied by 10 until two faces of the
+ * current tet are hit; the walk leaves through the face of the larger hit
+ * parameter.  A COMPARISON mode for the paper's floating-point experiment
+ * (Sec. IV): FP32 (TETPROJ_FILTERED selects single precision here) or FP64
+ * (TETPROJ_PLAIN_FP64) arithmetic throughout, no exact predicates.  Forward
+ * only, C = 1, tiles of at most 128 rays.  status (device int8 [nrays], or
+ * NULL): 0 = walk completed (or missed the mesh), 1 = halted (eps reached
+ * 1e-2 without two intersections: a missed exit), 2 = more than max_steps
+ * tets (looping).  Halted and looping rays return their partial sums.
+ * Readings of what the paper leaves open are listed in kernels.cu. */
+tetproj_status tetproj_forward_mt(const tetproj_mesh *mesh, const tetproj_geometry *geo,
+                                  const void *mu, void *proj, int8_t *status,
+                                  const tetproj_options *opt, void *stream);
+tetproj_status tetproj_forward_rays_mt(const tetproj_mesh *mesh, const double *src,
+                                       const double *dst, int64_t nrays, const void *mu,
+                                       void *out, int8_t *status, const tetproj_options *opt,
+                                       void *stream);
+
 /* ------------------------------------------------------------ predicates --
  * Sign of the side product det[P - S, p - S, q - S] of the line S->P and the
  * edge p->q (the test behind each of the four triangle tests of Sec. II-C),

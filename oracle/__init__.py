@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_MT = os.path.join(_HERE, "mt.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 _c_dp = ctypes.POINTER(ctypes.c_double)
@@ -29,10 +30,11 @@ _c_lp = ctypes.POINTER(ctypes.c_int64)
 
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so (plain C, FP64, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_MT))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+               "-shared", "-pthread", "-o", tmp, _SRC, _SRC_MT, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -50,6 +52,10 @@ def lib():
         L.oracle_cone_rays.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                        ctypes.c_int64, ctypes.c_double, ctypes.c_double, _c_dp,
                                        ctypes.c_int64, _c_lp, ctypes.c_int64, _c_dp, _c_dp]
+        L.oracle_mt_forward_rays.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
+                                             _c_dp, _c_dp, ctypes.c_int64, ctypes.c_int,
+                                             ctypes.c_int64, _c_dp,
+                                             ctypes.POINTER(ctypes.c_int8)]
         L.oracle_tet_chord.argtypes = [_c_dp, _c_dp, _c_dp, _c_dp, _c_dp]
         L.oracle_tet_chord.restype = ctypes.c_double
         L.oracle_forward_rays.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
@@ -272,6 +278,26 @@ def backward_cone_subset(verts, tets, y, geom, tet_idx, threads=None):
                                              threads or default_threads()),
            "oracle_backward_cone_subset")
     return out[:, 0] if C == 1 else out
+
+
+def mt_forward_rays(verts, tets, mu, S, P, precision="f64", max_steps=100000):
+    """The paper's own walk (Alg. 1-2, mt.c) for explicit rays, in single
+    ("f32") or double ("f64") arithmetic: (sums [n], status [n] int8:
+    0 done, 1 halted, 2 step limit).  Single-threaded."""
+    v, vp = _d(verts)
+    t, tp = _i(tets)
+    m, mp = _d(np.asarray(mu, dtype=np.float64).reshape(-1))
+    s, sp = _d(S)
+    p, pp = _d(P)
+    n = s.shape[0]
+    out = np.zeros(n)
+    status = np.zeros(n, np.int8)
+    _check(lib().oracle_mt_forward_rays(vp, v.shape[0], tp, t.shape[0], mp, sp, pp, n,
+                                        4 if precision == "f32" else 8, int(max_steps),
+                                        out.ctypes.data_as(_c_dp),
+                                        status.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))),
+           "oracle_mt_forward_rays")
+    return out, status
 
 
 def trace_rays(verts, tets, S, P, max_visits=1024, threads=None):

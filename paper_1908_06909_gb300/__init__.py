@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import (FILTERED, ORDER_MORTON, ORDER_ROW, PLAIN_FP64, SCATTER_ATOMIC, SCATTER_SORT,
                    SCATTER_WARP, Options, TetprojError, check)
 
-__all__ = ["Mesh", "Geometry", "Batch", "forward", "backward", "backward_noalloc", "forward_rays", "backward_rays",
+__all__ = ["Mesh", "Geometry", "Batch", "forward", "forward_mt", "forward_rays_mt", "backward", "backward_noalloc", "forward_rays", "backward_rays",
            "trace_rays", "side_signs_host", "side_signs_device", "TetProject", "make_options",
            "FILTERED", "PLAIN_FP64", "ORDER_ROW", "ORDER_MORTON", "SCATTER_ATOMIC",
            "SCATTER_WARP", "SCATTER_SORT", "TetprojError", "library_path"]
@@ -307,6 +307,41 @@ def backward_rays(mesh: Mesh, src, dst, y, out=None, options: Options | None = N
                                             _ptr(y), _ptr(out), ctypes.byref(o), _stream()),
           "tetproj_backward_rays")
     return out
+
+
+def forward_mt(mesh: Mesh, geo: Geometry, mu, options: Options | None = None):
+    """The paper's own walk (Alg. 1-2, Moller-Trumbore + growing eps): a
+    comparison mode.  float32 mu: single-precision arithmetic, float64: double.
+    Returns (proj [na, nv, nu], status int8 [na, nv, nu]: 0 done, 1 halted,
+    2 step limit)."""
+    torch = _torch()
+    _check_cuda(mu, "mu")
+    if mu.dim() != 1 or mu.shape[0] != mesh.nt:
+        raise ValueError("mu must be [nt]")
+    prec = _precision_of(mu)
+    out = torch.empty(geo.shape, dtype=mu.dtype, device=mu.device)
+    status = torch.empty(geo.shape, dtype=torch.int8, device=mu.device)
+    o = _opts(prec, 1, options)
+    check(_lib.load().tetproj_forward_mt(mesh.handle, geo.handle, _ptr(mu), _ptr(out),
+                                         _ptr(status), ctypes.byref(o), _stream()),
+          "tetproj_forward_mt")
+    return out, status
+
+
+def forward_rays_mt(mesh: Mesh, src, dst, mu, options: Options | None = None):
+    """forward_mt for explicit rays (device [n, 3] float64 src / dst)."""
+    torch = _torch()
+    for t, nm in ((src, "src"), (dst, "dst"), (mu, "mu")):
+        _check_cuda(t, nm)
+    n = src.shape[0]
+    prec = _precision_of(mu)
+    out = torch.empty((n,), dtype=mu.dtype, device=mu.device)
+    status = torch.empty((n,), dtype=torch.int8, device=mu.device)
+    o = _opts(prec, 1, options)
+    check(_lib.load().tetproj_forward_rays_mt(mesh.handle, _ptr(src), _ptr(dst), n, _ptr(mu),
+                                              _ptr(out), _ptr(status), ctypes.byref(o),
+                                              _stream()), "tetproj_forward_rays_mt")
+    return out, status
 
 
 def trace_rays(mesh: Mesh, src, dst, max_visits=512, precision=FILTERED,

@@ -85,6 +85,8 @@ SIGNATURES = {
     "tetproj_batch_forward": (c_i32, [c_vp, c_vp]),
     "tetproj_batch_backward": (c_i32, [c_vp, c_vp]),
     "tetproj_batch_destroy": (c_i32, [c_vp]),
+    "tetproj_forward_mt": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "tetproj_forward_rays_mt": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tetproj_side_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp]),
     "tetproj_side_device": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
 }

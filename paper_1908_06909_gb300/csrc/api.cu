@@ -58,6 +58,7 @@ struct tetproj_mesh {
     BvhNode *bvh = nullptr;
     BFace32 *bfaces = nullptr;
     int32_t *perm = nullptr;
+    int4 *vid = nullptr;
     DevCounters *counters = nullptr;
     int64_t nt = 0, nv = 0, nb = 0, nnodes = 0, nflipped = 0;
     int32_t root = 0;
@@ -180,6 +181,7 @@ static void mesh_free(tetproj_mesh *m) {
     cudaFree(m->bvh);
     cudaFree(m->bfaces);
     cudaFree(m->perm);
+    cudaFree(m->vid);
     cudaFree(m->counters);
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) cudaFree(m->ws[i][j]);
@@ -217,6 +219,7 @@ tetproj_status tetproj_mesh_create(const double *vertices, int64_t nv, const int
     if (e == cudaSuccess) e = upload(&m->bvh, H.bvh);
     if (e == cudaSuccess) e = upload(&m->bfaces, H.bfaces);
     if (e == cudaSuccess) e = upload(&m->perm, H.perm);
+    if (e == cudaSuccess) e = upload(&m->vid, H.vid);
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->counters, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaMemset(m->counters, 0, sizeof(DevCounters));
     if (e != cudaSuccess) {
@@ -225,7 +228,8 @@ tetproj_status tetproj_mesh_create(const double *vertices, int64_t nv, const int
     }
     m->base_bytes = (int64_t)(H.rec32.size() * sizeof(TetRec32) + H.rec64.size() * sizeof(TetRec64) +
                               H.bvh.size() * sizeof(BvhNode) + H.bfaces.size() * sizeof(BFace32) +
-                              H.perm.size() * sizeof(int32_t) + sizeof(DevCounters));
+                              H.perm.size() * sizeof(int32_t) + H.vid.size() * sizeof(int4) +
+                              sizeof(DevCounters));
     *out = m;
     return TETPROJ_OK;
 }
@@ -423,6 +427,7 @@ static KParams base_params(const tetproj_mesh *m, const tetproj_options &o) {
     std::memset(&p, 0, sizeof(p));
     p.m.rec32 = m->rec32;
     p.m.rec64 = m->rec64;
+    p.m.vid = m->vid;
     p.m.bvh = m->bvh;
     p.m.bfaces = m->bfaces;
     p.m.perm = m->perm;
@@ -1018,4 +1023,53 @@ extern "C" tetproj_status tetproj_batch_destroy(tetproj_batch *b) {
     cudaDeviceSynchronize();
     batch_free(b);
     return TETPROJ_OK;
+}
+
+// ------------------------------------------------- the paper's walk (Alg. 1-2)
+
+static tetproj_status run_forward_mt(tetproj_mesh *m, KParams &p, const tetproj_options &o,
+                                     const void *mu, void *out, int8_t *status, cudaStream_t s) {
+    if (o.channels != 1) return TETPROJ_ERR_ARG;
+    if (p.src_kind == 0 && o.tile_u * o.tile_v > 128) return TETPROJ_ERR_ARG;
+    tetproj_status st = ensure_ws(m, o.precision, 1);
+    if (st != TETPROJ_OK) return st;
+    const int f64 = o.precision == TETPROJ_PLAIN_FP64;
+    void *ws = m->ws[f64][0];
+    TP_CUDA(launch_gather_perm(m->perm, m->nt, 1, f64, mu, ws, s));
+    p.in = ws;
+    p.out = out;
+    TP_CUDA(launch_walk_mt(p, f64, status, s));
+    return TETPROJ_OK;
+}
+
+extern "C" tetproj_status tetproj_forward_mt(const tetproj_mesh *mesh,
+                                             const tetproj_geometry *geo, const void *mu,
+                                             void *proj, int8_t *status,
+                                             const tetproj_options *opt, void *stream) {
+    if (!mesh || !geo || !mu || !proj) return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
+    KParams p = base_params(m, o);
+    set_cone(p, geo);
+    return run_forward_mt(m, p, o, mu, proj, status, (cudaStream_t)stream);
+}
+
+extern "C" tetproj_status tetproj_forward_rays_mt(const tetproj_mesh *mesh, const double *src,
+                                                  const double *dst, int64_t nrays,
+                                                  const void *mu, void *out, int8_t *status,
+                                                  const tetproj_options *opt, void *stream) {
+    if (!mesh || nrays < 0 || (nrays > 0 && (!src || !dst || !mu || !out))) return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    if (nrays == 0) return TETPROJ_OK;
+    tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
+    KParams p = base_params(m, o);
+    p.src_kind = 1;
+    p.rsrc = src;
+    p.rdst = dst;
+    p.nrays = nrays;
+    return run_forward_mt(m, p, o, mu, out, status, (cudaStream_t)stream);
 }

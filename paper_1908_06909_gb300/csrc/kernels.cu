@@ -1188,6 +1188,197 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
 
 int device_sm_count() { return sm_count(); }
 
+// ========================================== the paper's walk (comparison)
+//
+// Alg. 1 and 2 as the paper prints them, kept as a comparison mode for the
+// floating-point experiment of Sec. IV (not the product path, which decides
+// exit faces with exact signs).  Per ray: l = |R2 - R1|; the entry tet is the
+// boundary face with the smallest Moller-Trumbore parameter t >= 0 (the
+// paper's R*-tree search keeps the minimum t; the same boundary-face BVH is
+// traversed here without early exit; ties go to the smaller user tet id, then
+// the face opposite the smaller vertex id);
+// then per tet all four faces are tested with the safety margin eps = 1e-9,
+// multiplied by 10 until two faces are hit; t1 / t2 are the smallest /
+// largest hit parameters, sum += l (t2 - t1) mu, and the walk moves through
+// the face of t2.  Readings of what the paper leaves open: the eps loop stops
+// at 1e-2 (status 1, "halt": a missed intersection); the walk stops after
+// max_steps tets (status 2, "loop"); "if t2 = t1 check if they need to be
+// swapped" is read as: when the two parameters are equal and the face of t2
+// is the face the ray entered through, leave through the face of t1 instead;
+// Alg. 1's v = f (d x r) is read as the dot product f (d . r).  The face's
+// vertices enter Alg. 1 in increasing user vertex id, and a tet's faces are
+// tested in increasing id of their opposite vertex (t1 = the first minimum,
+// t2 = the last maximum in that order), so every description of the same mesh
+// gives the same arithmetic and the same decisions.
+
+template <typename T>
+struct MtV {
+    T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ MtV<T> mt_sub(const MtV<T> &a, const MtV<T> &b) {
+    return {a.x - b.x, a.y - b.y, a.z - b.z};
+}
+template <typename T>
+__device__ __forceinline__ MtV<T> mt_cross(const MtV<T> &a, const MtV<T> &b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ T mt_dot(const MtV<T> &a, const MtV<T> &b) {
+    return (a.x * b.x + a.y * b.y) + a.z * b.z;
+}
+
+// Alg. 1: does the line R1 + t d cross triangle (P1, P2, P3), with the
+// barycentric bounds widened by eps?  t on success.
+template <typename T>
+__device__ __forceinline__ bool mt_hit(const MtV<T> &R1, const MtV<T> &d, const MtV<T> &P1,
+                                       const MtV<T> &P2, const MtV<T> &P3, T eps, T &t) {
+    const MtV<T> E1 = mt_sub(P2, P1), E2 = mt_sub(P3, P1);
+    const MtV<T> q = mt_cross(d, E2);
+    const T a = mt_dot(E1, q);
+    if (a > T(-1e-8) && a < T(1e-8)) return false;
+    const T f = T(1) / a;
+    const MtV<T> s = mt_sub(R1, P1);
+    const T u = f * mt_dot(s, q);
+    if (u < T(0) - eps) return false;
+    const MtV<T> r = mt_cross(s, E1);
+    const T v = f * mt_dot(d, r);
+    if (v < T(0) - eps || u + v > T(1) + eps) return false;
+    t = f * mt_dot(E2, r);
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ MtV<T> mt_vertex(const MeshView &m, int h, int k);
+template <>
+__device__ __forceinline__ MtV<float> mt_vertex<float>(const MeshView &m, int h, int k) {
+    const float *r = reinterpret_cast<const float *>(m.rec32 + h);  // v0..v3 xyz first
+    return {__ldg(r + 3 * k), __ldg(r + 3 * k + 1), __ldg(r + 3 * k + 2)};
+}
+template <>
+__device__ __forceinline__ MtV<double> mt_vertex<double>(const MeshView &m, int h, int k) {
+    const double *r = m.rec64[h].v;
+    return {__ldg(r + 3 * k), __ldg(r + 3 * k + 1), __ldg(r + 3 * k + 2)};
+}
+
+// Alg. 1 on face f of tet h (the face opposite local vertex f)
+template <typename T>
+__device__ __forceinline__ bool mt_face(const MeshView &m, int h, int f, const int4 &vid,
+                                        const MtV<T> &R1, const MtV<T> &d, T eps, T &t) {
+    int a, b, c;
+    face_triple(f, a, b, c);
+    int ia = sel4(vid, a), ib = sel4(vid, b), ic = sel4(vid, c);
+    // increasing user vertex id
+    if (ia > ib) { int x = a; a = b; b = x; x = ia; ia = ib; ib = x; }
+    if (ib > ic) { int x = b; b = c; c = x; x = ib; ib = ic; ic = x; }
+    if (ia > ib) { int x = a; a = b; b = x; x = ia; ia = ib; ib = x; }
+    return mt_hit<T>(R1, d, mt_vertex<T>(m, h, a), mt_vertex<T>(m, h, b), mt_vertex<T>(m, h, c),
+                     eps, t);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_walk_mt(const __grid_constant__ KParams p,
+                                                 int8_t *__restrict__ status) {
+    int64_t ray = 0;
+    if (!thread_ray(p, ray)) return;  // no warp-collective operations below
+    d3 S, P;
+    load_ray(p, ray, S, P);
+    const MtV<T> R1 = {(T)S.x, (T)S.y, (T)S.z}, R2 = {(T)P.x, (T)P.y, (T)P.z};
+    const MtV<T> d = mt_sub(R2, R1);
+    const T l = sqrt(mt_dot(d, d));
+    // entry: the boundary face with the smallest t >= 0
+    const f3 S32 = tof(S);
+    const f3 d32 = {(float)(P.x - S.x), (float)(P.y - S.y), (float)(P.z - S.z)};
+    const float smax = fmaxf(fmaxf(fabsf(S32.x), fabsf(S32.y)), fabsf(S32.z));
+    const float margin = 16.f * 5.9604645e-8f * (smax + p.m.radius);
+    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    T tbest = T(0);
+    int hbest = -1, fbest = -1, ubest = 0, obest = 0;
+    bvh_search(p.m, nullptr, 0, S32, safe_inv(d32), margin, cnt, [&](int q) -> bool {
+        const int code = __float_as_int(__ldg(&p.m.bfaces[q].a.w));
+        const int hq = code >> 2, fq = code & 3;
+        T t;
+        const int4 vq = __ldg(p.m.vid + hq);
+        if (mt_face<T>(p.m, hq, fq, vq, R1, d, T(1e-9), t) && t >= T(0)) {
+            const int uq = __ldg(p.m.perm + hq), oq = sel4(vq, fq);
+            if (hbest < 0 || t < tbest || (t == tbest && (uq < ubest ||
+                                                          (uq == ubest && oq < obest)))) {
+                tbest = t; hbest = hq; fbest = fq; ubest = uq; obest = oq;
+            }
+        }
+        return false;  // visit every candidate: the minimum is wanted
+    });
+    T sum = T(0);
+    int st = 0;
+    const T *mu = reinterpret_cast<const T *>(p.in);
+    int h = hbest, fin = fbest, steps = 0;
+    while (h >= 0) {
+        const int4 vid = __ldg(p.m.vid + h);
+        // faces in increasing id of the opposite vertex
+        int ord[4] = {0, 1, 2, 3};
+#pragma unroll
+        for (int i = 1; i < 4; ++i)
+#pragma unroll
+            for (int j = i; j > 0; --j)
+                if (sel4(vid, ord[j - 1]) > sel4(vid, ord[j])) {
+                    const int x = ord[j]; ord[j] = ord[j - 1]; ord[j - 1] = x;
+                }
+        T th[4];
+        int fh[4];
+        int nh = 0;
+        T eps = T(1e-9);
+        while (true) {
+            nh = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int f = ord[j];
+                T t;
+                if (mt_face<T>(p.m, h, f, vid, R1, d, eps, t)) { th[nh] = t; fh[nh] = f; ++nh; }
+            }
+            if (nh >= 2) break;
+            eps = eps * T(10);
+            if (eps > T(1e-2)) break;
+        }
+        if (nh < 2) { st = 1; break; }
+        int i1 = 0, i2 = 0;
+        for (int k = 1; k < nh; ++k) {
+            if (th[k] < th[i1]) i1 = k;
+            if (th[k] >= th[i2]) i2 = k;
+        }
+        const T t1 = th[i1], t2 = th[i2];
+        int fout = fh[i2];
+        if (t2 == t1 && fout == fin) fout = fh[i1];
+        sum = sum + (l * (t2 - t1)) * __ldg(mu + h);
+        const int nx = sel4(__ldg(reinterpret_cast<const int4 *>(&p.m.rec32[h].adj)), fout);
+        if (nx < 0) break;
+        h = nx >> 2;
+        fin = nx & 3;
+        if (++steps >= p.max_steps) { st = 2; break; }
+    }
+    reinterpret_cast<T *>(p.out)[ray] = sum;
+    if (status) status[ray] = (int8_t)st;
+}
+
+cudaError_t launch_walk_mt(const KParams &p, int f64, int8_t *status, cudaStream_t stream) {
+    int64_t nblocks;
+    int threads;
+    if (p.src_kind == 0) {
+        threads = p.tu * p.tv;
+        nblocks = (int64_t)p.g.na * p.tiles_u * p.tiles_v;
+    } else {
+        threads = 128;
+        nblocks = (p.nrays + threads - 1) / threads;
+    }
+    if (nblocks <= 0) return cudaSuccess;
+    if (nblocks > 0x7fffffff || threads > 128) return cudaErrorInvalidConfiguration;
+    if (f64)
+        k_walk_mt<double><<<(unsigned)nblocks, threads, 0, stream>>>(p, status);
+    else
+        k_walk_mt<float><<<(unsigned)nblocks, threads, 0, stream>>>(p, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ============================================================ small kernels
 
 template <typename T>

@@ -129,6 +129,12 @@ cudaError_t launch_seg_reduce(const uint32_t *keys, const float *vals, int64_t n
 void note_launch();
 long long launch_count();
 
+// The paper's own walk (Alg. 1 and 2, Moller-Trumbore with a growing safety
+// margin) in FP32 (f64 = 0) or FP64: C = 1 forward into p.out, per-ray
+// status 0 done / 1 halted (no two faces found) / 2 step limit; tiles of at
+// most 128 threads.
+cudaError_t launch_walk_mt(const KParams &p, int f64, int8_t *status, cudaStream_t stream);
+
 // one launch of the walk; returns a cudaError_t
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
                         cudaStream_t stream);

@@ -352,8 +352,10 @@ tetproj_status build_host_mesh(const double *V, int64_t nv, const int32_t *T, in
     // records
     M.rec32.resize(nt);
     M.rec64.resize(nt);
+    M.vid.resize(nt);
     for (int64_t h = 0; h < nt; ++h) {
         int64_t t = M.perm[h];
+        M.vid[h] = make_int4(tt[4 * t], tt[4 * t + 1], tt[4 * t + 2], tt[4 * t + 3]);
         TetRec64 &r = M.rec64[h];
         float c[12];
         for (int k = 0; k < 4; ++k)

@@ -16,6 +16,7 @@ struct HostMesh {
     std::vector<BvhNode> bvh;
     std::vector<BFace32> bfaces;
     std::vector<int32_t> perm;  // h -> user tet id
+    std::vector<int4> vid;      // h -> user vertex ids in local (oriented) order
     int32_t root = 0;
     float radius = 0.f;
     double bbox[6] = {0, 0, 0, 0, 0, 0};

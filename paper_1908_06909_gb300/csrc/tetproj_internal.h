@@ -70,6 +70,7 @@ struct MeshView {
     const BvhNode *bvh;
     const BFace32 *bfaces;
     const int32_t *perm;  // h -> user tet id
+    const int4 *vid;      // h -> user vertex ids in local order
     int64_t nt, nb, nnodes;
     int32_t root;         // root code (0, or a leaf code for tiny meshes)
     float radius;         // max |coordinate| over all vertices
