@@ -82,6 +82,13 @@ typedef int32_t tetproj_status;
 #define TETPROJ_SCATTER_SORT 2    /* segment sort-and-reduce: deterministic (see
                                      tetproj_backward); filtered path, cone rays   */
 
+/* options.flags */
+#define TETPROJ_FLAG_RSTAR_ENTRY 1 /* entry search through an R*-tree of the boundary
+                                      faces (the paper's structure, Sec. II-E)
+                                      instead of the binary BVH: filtered forward
+                                      (C = 1) and tetproj_entry only; the tree is
+                                      built on first use (synchronous)          */
+
 typedef struct tetproj_mesh tetproj_mesh;
 typedef struct tetproj_geometry tetproj_geometry;
 
@@ -93,7 +100,7 @@ typedef struct tetproj_options {
     int32_t order;     /* TETPROJ_ORDER_MORTON (default) or TETPROJ_ORDER_ROW          */
     int32_t scatter;   /* TETPROJ_SCATTER_ATOMIC (default), _WARP or _SORT             */
     int32_t max_steps; /* walk step limit per ray; 0 = 64 + 16*ceil(nt^(1/3))          */
-    int32_t flags;     /* reserved, must be 0                                          */
+    int32_t flags;     /* 0 or TETPROJ_FLAG_RSTAR_ENTRY                               */
 } tetproj_options;
 
 typedef struct tetproj_stats {
@@ -293,6 +300,26 @@ tetproj_status tetproj_forward_rays_mt(const tetproj_mesh *mesh, const double *s
                                        const double *dst, int64_t nrays, const void *mu,
                                        void *out, int8_t *status, const tetproj_options *opt,
                                        void *stream);
+
+/* ---------------------------------------------------------- entry search --
+ * entry_tet[ray] = user id of the first tet each cone ray enters (-1: the ray
+ * misses the mesh): the entry search alone (Sec. II-E), filtered precision,
+ * through the BVH or, with TETPROJ_FLAG_RSTAR_ENTRY, the R*-tree.  entry_tet:
+ * device int32 [nangles][nv][nu]. */
+tetproj_status tetproj_entry(const tetproj_mesh *mesh, const tetproj_geometry *geo,
+                             int32_t *entry_tet, const tetproj_options *opt, void *stream);
+
+typedef struct tetproj_rstar_info {
+    int64_t nodes, leaves, entries; /* entries: boundary faces listed in leaves      */
+    int32_t depth;                  /* levels, root to leaves                        */
+    int32_t min_fill, max_fill;     /* entries per non-root node                     */
+    int32_t ok;                     /* 1: fills within [4, 10], leaves at one depth,
+                                       boxes nested, every face in exactly one leaf */
+} tetproj_rstar_info;
+/* Builds the mesh's boundary-face R*-tree on the host (no device needed) and
+ * checks its invariants; HOST inputs as tetproj_mesh_create. */
+tetproj_status tetproj_rstar_build_host(const double *vertices, int64_t nv, const int32_t *tets,
+                                        int64_t nt, tetproj_rstar_info *out);
 
 /* ------------------------------------------------------------ predicates --
  * Sign of the side product det[P - S, p - S, q - S] of the line S->P and the

@@ -18,13 +18,14 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (FILTERED, ORDER_MORTON, ORDER_ROW, PLAIN_FP64, SCATTER_ATOMIC, SCATTER_SORT,
-                   SCATTER_WARP, Options, TetprojError, check)
+from ._lib import (FILTERED, FLAG_RSTAR_ENTRY, ORDER_MORTON, ORDER_ROW, PLAIN_FP64,
+                   SCATTER_ATOMIC, SCATTER_SORT, SCATTER_WARP, Options, TetprojError, check)
 
 __all__ = ["Mesh", "Geometry", "Batch", "forward", "forward_mt", "forward_rays_mt", "backward", "backward_noalloc", "forward_rays", "backward_rays",
            "trace_rays", "side_signs_host", "side_signs_device", "TetProject", "make_options",
            "FILTERED", "PLAIN_FP64", "ORDER_ROW", "ORDER_MORTON", "SCATTER_ATOMIC",
-           "SCATTER_WARP", "SCATTER_SORT", "TetprojError", "library_path"]
+           "SCATTER_WARP", "SCATTER_SORT", "FLAG_RSTAR_ENTRY", "entry", "rstar_build_host",
+           "TetprojError", "library_path"]
 
 
 def library_path() -> str:
@@ -56,7 +57,7 @@ def _ptr(t):
 
 
 def make_options(precision=FILTERED, channels=1, tile=(8, 8), order=ORDER_MORTON,
-                 scatter=SCATTER_ATOMIC, max_steps=0) -> Options:
+                 scatter=SCATTER_ATOMIC, max_steps=0, flags=0) -> Options:
     o = Options()
     _lib.load().tetproj_default_options(ctypes.byref(o))
     o.precision = precision
@@ -65,6 +66,7 @@ def make_options(precision=FILTERED, channels=1, tile=(8, 8), order=ORDER_MORTON
     o.order = order
     o.scatter = scatter
     o.max_steps = max_steps
+    o.flags = flags
     return o
 
 
@@ -307,6 +309,29 @@ def backward_rays(mesh: Mesh, src, dst, y, out=None, options: Options | None = N
                                             _ptr(y), _ptr(out), ctypes.byref(o), _stream()),
           "tetproj_backward_rays")
     return out
+
+
+def entry(mesh: Mesh, geo: Geometry, options: Options | None = None):
+    """User id of the first tet each cone ray enters (-1: miss), int32
+    [na, nv, nu]: the entry search alone (BVH, or the R*-tree with
+    FLAG_RSTAR_ENTRY in the options)."""
+    torch = _torch()
+    out = torch.empty(geo.shape, dtype=torch.int32, device="cuda")
+    o = _opts(FILTERED, 1, options)
+    check(_lib.load().tetproj_entry(mesh.handle, geo.handle, _ptr(out), ctypes.byref(o),
+                                    _stream()), "tetproj_entry")
+    return out
+
+
+def rstar_build_host(vertices, tets) -> dict:
+    """Builds the boundary-face R*-tree on the host and checks its invariants."""
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    t = np.ascontiguousarray(tets, dtype=np.int32)
+    info = _lib.RStarInfo()
+    check(_lib.load().tetproj_rstar_build_host(v.ctypes.data, v.shape[0], t.ctypes.data,
+                                               t.shape[0], ctypes.byref(info)),
+          "tetproj_rstar_build_host")
+    return {k: getattr(info, k) for k, _ in info._fields_}
 
 
 def forward_mt(mesh: Mesh, geo: Geometry, mu, options: Options | None = None):

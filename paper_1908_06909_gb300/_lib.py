@@ -28,6 +28,7 @@ ORDER_MORTON = 1
 SCATTER_ATOMIC = 0
 SCATTER_WARP = 1
 SCATTER_SORT = 2
+FLAG_RSTAR_ENTRY = 1
 
 c_vp = ctypes.c_void_p
 c_i32 = ctypes.c_int32
@@ -47,6 +48,11 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RStarInfo(ctypes.Structure):
+    _fields_ = [("nodes", c_i64), ("leaves", c_i64), ("entries", c_i64), ("depth", c_i32),
+                ("min_fill", c_i32), ("max_fill", c_i32), ("ok", c_i32)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -87,6 +93,8 @@ SIGNATURES = {
     "tetproj_batch_destroy": (c_i32, [c_vp]),
     "tetproj_forward_mt": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tetproj_forward_rays_mt": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "tetproj_entry": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "tetproj_rstar_build_host": (c_i32, [c_vp, c_i64, c_vp, c_i64, c_vp]),
     "tetproj_side_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp]),
     "tetproj_side_device": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
 }

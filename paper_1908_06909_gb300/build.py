@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libtetproj.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["api.cu", "kernels.cu", "segsort.cu"]
-CPP_SOURCES = ["mesh_build.cpp"]
+CPP_SOURCES = ["mesh_build.cpp", "rstar.cpp"]
 
 
 def _nvcc() -> str:

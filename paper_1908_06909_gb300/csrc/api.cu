@@ -15,6 +15,7 @@
 #include "../../include/tetproj.h"
 #include "kernels.cuh"
 #include "mesh_build.h"
+#include "rstar.h"
 
 using namespace tp;
 
@@ -59,6 +60,8 @@ struct tetproj_mesh {
     BFace32 *bfaces = nullptr;
     int32_t *perm = nullptr;
     int4 *vid = nullptr;
+    RStarNode *rstar = nullptr;  // built on first use of TETPROJ_FLAG_RSTAR_ENTRY
+    int64_t rstar_bytes = 0;
     DevCounters *counters = nullptr;
     int64_t nt = 0, nv = 0, nb = 0, nnodes = 0, nflipped = 0;
     int32_t root = 0;
@@ -182,6 +185,7 @@ static void mesh_free(tetproj_mesh *m) {
     cudaFree(m->bfaces);
     cudaFree(m->perm);
     cudaFree(m->vid);
+    cudaFree(m->rstar);
     cudaFree(m->counters);
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) cudaFree(m->ws[i][j]);
@@ -249,7 +253,7 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *m, tetproj_mesh_info *o
     o->nbvh_nodes = m->nnodes;
     o->nflipped = m->nflipped;
     int64_t b = m->base_bytes + m->q_cap * (int64_t)sizeof(QEntry) + (m->q_count ? 8 : 0) +
-                m->plan.bytes + m->sort.bytes;
+                m->plan.bytes + m->sort.bytes + m->rstar_bytes;
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) b += m->ws_bytes[i][j];
     o->device_bytes = b;
@@ -418,7 +422,7 @@ static tetproj_status check_opts(const tetproj_options *in, tetproj_options &o) 
     if (o.scatter != TETPROJ_SCATTER_ATOMIC && o.scatter != TETPROJ_SCATTER_WARP &&
         o.scatter != TETPROJ_SCATTER_SORT)
         return TETPROJ_ERR_ARG;
-    if (o.max_steps < 0 || o.flags != 0) return TETPROJ_ERR_ARG;
+    if (o.max_steps < 0 || (o.flags & ~TETPROJ_FLAG_RSTAR_ENTRY) != 0) return TETPROJ_ERR_ARG;
     return TETPROJ_OK;
 }
 
@@ -449,7 +453,32 @@ static KParams base_params(const tetproj_mesh *m, const tetproj_options &o) {
     if (ms > m->nt + 1) ms = m->nt + 1;
     p.max_steps = (int32_t)ms;
     p.smem_nodes = (int32_t)(m->nnodes < 64 ? m->nnodes : 64);
+    p.entry = (o.flags & TETPROJ_FLAG_RSTAR_ENTRY) ? ENTRY_RSTAR : ENTRY_BVH;
+    p.m.rstar = m->rstar;
     return p;
+}
+
+// The R*-tree of the boundary faces, built on the host from the device copy of
+// the faces on first use (synchronous).
+static tetproj_status ensure_rstar(tetproj_mesh *m, KParams &p) {
+    if (!m->rstar) {
+        std::vector<BFace32> faces((size_t)m->nb);
+        TP_CUDA(cudaMemcpy(faces.data(), m->bfaces, sizeof(BFace32) * m->nb,
+                           cudaMemcpyDeviceToHost));
+        std::vector<RStarNode> nodes;
+        rstar_build(faces, nodes);
+        if (rstar_check(faces, nodes).depth > RSTAR_MAX_DEPTH) return TETPROJ_ERR_TOO_LARGE;
+        cudaError_t e = upload(&m->rstar, nodes);
+        if (e != cudaSuccess) return cuda_status(e);
+        m->rstar_bytes = (int64_t)(nodes.size() * sizeof(RStarNode));
+    }
+    p.m.rstar = m->rstar;
+    return TETPROJ_OK;
+}
+
+// Calls without an R*-tree variant reject the flag.
+static bool rstar_unsupported(const tetproj_options &o) {
+    return (o.flags & TETPROJ_FLAG_RSTAR_ENTRY) != 0;
 }
 
 static void set_cone(KParams &p, const tetproj_geometry *g) {
@@ -472,6 +501,11 @@ static tetproj_status attach_queue(tetproj_mesh *m, KParams &p, const tetproj_op
 
 static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
                                   const void *mu, void *out, cudaStream_t s) {
+    if (p.entry == ENTRY_RSTAR) {  // the paper's entry structure: filtered path, C = 1
+        if (o.precision != TETPROJ_FILTERED || o.channels != 1) return TETPROJ_ERR_ARG;
+        tetproj_status st = ensure_rstar(m, p);
+        if (st != TETPROJ_OK) return st;
+    }
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
     if (st == TETPROJ_OK) st = attach_queue(m, p, o);
     if (st != TETPROJ_OK) return st;
@@ -486,6 +520,7 @@ static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_opt
 
 static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
                                    const void *y, void *mu_out, cudaStream_t s) {
+    if (rstar_unsupported(o)) return TETPROJ_ERR_ARG;
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
     if (st == TETPROJ_OK) st = attach_queue(m, p, o);
     if (st != TETPROJ_OK) return st;
@@ -659,7 +694,7 @@ tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry
     KParams p = base_params(m, o);
     set_cone(p, geo);
     if (o.scatter == TETPROJ_SCATTER_SORT) {
-        if (o.precision != TETPROJ_FILTERED) return TETPROJ_ERR_ARG;
+        if (o.precision != TETPROJ_FILTERED || rstar_unsupported(o)) return TETPROJ_ERR_ARG;
         return run_backward_sort(m, geo, p, o, proj, mu_out, (cudaStream_t)stream);
     }
     return run_backward(m, p, o, proj, mu_out, (cudaStream_t)stream);
@@ -728,6 +763,7 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
     p.tr_len = out_len;
     p.tr_count = out_count;
     p.max_visits = max_visits;
+    if (rstar_unsupported(o)) return TETPROJ_ERR_ARG;
     st = attach_queue(m, p, o);
     if (st != TETPROJ_OK) return st;
     TP_CUDA(launch_walk(p, o.precision, 1, MODE_TRACE, (cudaStream_t)stream));
@@ -807,7 +843,8 @@ extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
     if (!mesh || !geo || !proj || !mu_out) return TETPROJ_ERR_ARG;
     tetproj_options o;
     tetproj_status st = check_opts(opt, o);
-    if (st == TETPROJ_OK && o.scatter == TETPROJ_SCATTER_SORT) st = TETPROJ_ERR_ARG;  // allocates
+    if (st == TETPROJ_OK && (o.scatter == TETPROJ_SCATTER_SORT || rstar_unsupported(o)))
+        st = TETPROJ_ERR_ARG;  // both allocate
     if (st != TETPROJ_OK) return st;
     const int f64 = o.precision == TETPROJ_PLAIN_FP64;
     const int64_t acc_bytes = mesh->nt * o.channels * (f64 ? 8 : 4);
@@ -904,7 +941,8 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
         }
         tetproj_options oo;
         tetproj_status st = check_opts(&o, oo);
-        if (st == TETPROJ_OK && oo.scatter == TETPROJ_SCATTER_SORT) st = TETPROJ_ERR_ARG;
+        if (st == TETPROJ_OK && (oo.scatter == TETPROJ_SCATTER_SORT || rstar_unsupported(oo)))
+            st = TETPROJ_ERR_ARG;
         if (st != TETPROJ_OK) { batch_free(b); return st; }
         KParams p = base_params(meshes[k], oo);
         set_cone(p, geos[k]);
@@ -1029,7 +1067,7 @@ extern "C" tetproj_status tetproj_batch_destroy(tetproj_batch *b) {
 
 static tetproj_status run_forward_mt(tetproj_mesh *m, KParams &p, const tetproj_options &o,
                                      const void *mu, void *out, int8_t *status, cudaStream_t s) {
-    if (o.channels != 1) return TETPROJ_ERR_ARG;
+    if (o.channels != 1 || rstar_unsupported(o)) return TETPROJ_ERR_ARG;
     if (p.src_kind == 0 && o.tile_u * o.tile_v > 128) return TETPROJ_ERR_ARG;
     tetproj_status st = ensure_ws(m, o.precision, 1);
     if (st != TETPROJ_OK) return st;
@@ -1072,4 +1110,47 @@ extern "C" tetproj_status tetproj_forward_rays_mt(const tetproj_mesh *mesh, cons
     p.rdst = dst;
     p.nrays = nrays;
     return run_forward_mt(m, p, o, mu, out, status, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------ entry search
+
+extern "C" tetproj_status tetproj_entry(const tetproj_mesh *mesh, const tetproj_geometry *geo,
+                                        int32_t *entry_tet, const tetproj_options *opt,
+                                        void *stream) {
+    if (!mesh || !geo || !entry_tet) return TETPROJ_ERR_ARG;
+    tetproj_options o;
+    tetproj_status st = check_opts(opt, o);
+    if (st != TETPROJ_OK) return st;
+    if (o.precision != TETPROJ_FILTERED) return TETPROJ_ERR_ARG;
+    o.channels = 1;
+    tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
+    KParams p = base_params(m, o);
+    set_cone(p, geo);
+    if (p.entry == ENTRY_RSTAR) st = ensure_rstar(m, p);
+    if (st == TETPROJ_OK) st = attach_queue(m, p, o);
+    if (st != TETPROJ_OK) return st;
+    p.tr_count = entry_tet;
+    TP_CUDA(launch_walk(p, TETPROJ_FILTERED, 1, MODE_ENTRY, (cudaStream_t)stream));
+    return TETPROJ_OK;
+}
+
+extern "C" tetproj_status tetproj_rstar_build_host(const double *vertices, int64_t nv,
+                                                   const int32_t *tets, int64_t nt,
+                                                   tetproj_rstar_info *out) {
+    if (!out) return TETPROJ_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    HostMesh H;
+    tetproj_status st = build_host_mesh(vertices, nv, tets, nt, H);
+    if (st != TETPROJ_OK) return st;
+    std::vector<RStarNode> nodes;
+    rstar_build(H.bfaces, nodes);
+    RStarStats rs = rstar_check(H.bfaces, nodes);
+    out->nodes = rs.nodes;
+    out->leaves = rs.leaves;
+    out->entries = rs.entries;
+    out->depth = rs.depth;
+    out->min_fill = rs.min_fill;
+    out->max_fill = rs.max_fill;
+    out->ok = rs.ok;
+    return TETPROJ_OK;
 }

@@ -343,6 +343,37 @@ __device__ __forceinline__ void bvh_search(const MeshView &m, const BvhNode *sno
     }
 }
 
+// R*-tree depth-first search (the paper's entry search, Sec. II-E): children
+// whose boxes the ray meets are pushed; FaceTest(q) tests boundary face q and
+// returns true to stop.  The stack holds 9 * depth + 1 <= 109 entries.
+template <class FaceTest>
+__device__ __forceinline__ void rstar_search(const MeshView &m, const f3 &S, const f3 &inv,
+                                             float margin, LocalCnt &cnt, FaceTest &&test) {
+    int stack[9 * RSTAR_MAX_DEPTH + 1];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const RStarNode *n = m.rstar + stack[--sp];
+        const int count = __ldg(&n->count), leaf = __ldg(&n->leaf);
+        for (int k = 0; k < count; ++k) {
+            const float4 lo = make_float4(__ldg(&n->lo[0][k]), __ldg(&n->lo[1][k]),
+                                          __ldg(&n->lo[2][k]), 0.f);
+            const float4 hi = make_float4(__ldg(&n->hi[0][k]), __ldg(&n->hi[1][k]),
+                                          __ldg(&n->hi[2][k]), 0.f);
+            ++cnt.nodes;
+            float tn;
+            if (!slab(lo, hi, S, inv, margin, tn)) continue;
+            const int c = __ldg(&n->child[k]);
+            if (leaf) {
+                ++cnt.faces;
+                if (test(c)) return;
+            } else if (sp < 9 * RSTAR_MAX_DEPTH + 1) {
+                stack[sp++] = c;
+            }
+        }
+    }
+}
+
 // ======================================================= filtered FP32 walk
 //
 // Two kernels share one body.  The FAST kernel (ROBUST = false) takes only
@@ -401,7 +432,7 @@ __device__ __forceinline__ int64_t seg_slot(const KParams &p, int64_t ray) {
 // scratch.  Resume kernel (ROBUST = true): `qe` is the ray's queue entry; the
 // walk continues from the saved state (or from the entry search when the ray
 // was deferred there).
-template <int C, int MODE, bool ROBUST>
+template <int C, int MODE, bool ROBUST, int ENTRY = ENTRY_BVH>
 __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snodes, int nsm,
                                            int64_t ray, const bool valid, const QEntry *qe) {
     LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -426,7 +457,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             f3 S32 = tof(S);
             float smax = fmaxf(fmaxf(fabsf(S32.x), fabsf(S32.y)), fabsf(S32.z));
             float margin = 16.f * 5.9604645e-8f * (smax + p.m.radius);
-            bvh_search(p.m, snodes, nsm, S32, inv, margin, cnt, [&](int q) -> bool {
+            auto entry_test = [&](int q) -> bool {
                 const float4 *g = reinterpret_cast<const float4 *>(p.m.bfaces + q);
                 float4 A = __ldg(g), B = __ldg(g + 1), Cc = __ldg(g + 2);
                 f3 a = {A.x, A.y, A.z}, b = {B.x, B.y, B.z}, c = {Cc.x, Cc.y, Cc.z};
@@ -455,7 +486,11 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 f = hf & 3;
                 alive = true;
                 return true;
-            });
+            };
+            if (ENTRY == ENTRY_RSTAR)
+                rstar_search(p.m, S32, inv, margin, cnt, entry_test);
+            else
+                bvh_search(p.m, snodes, nsm, S32, inv, margin, cnt, entry_test);
             if (alive) {
                 cnt.hits = 1;
                 // entry behind the source (source inside the mesh, or the mesh behind
@@ -484,6 +519,10 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
 #pragma unroll
             for (int c = 0; c < C; ++c) yv[c] = __ldg(y + c);
         }
+    }
+    if (MODE == MODE_ENTRY) {  // entry search only
+        if (valid && !deferred) p.tr_count[ray] = alive ? __ldg(p.m.perm + h) : -1;
+        alive = false;
     }
     // MODE_SEG: this ray's next slot in the segment buffer
     int64_t spos = 0;
@@ -704,13 +743,13 @@ __device__ __forceinline__ const BvhNode *stage_bvh_top(const KParams &p, float4
     return reinterpret_cast<const BvhNode *>(smem);
 }
 
-template <int C, int MODE>
+template <int C, int MODE, int ENTRY = ENTRY_BVH>
 __global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KParams p) {
     extern __shared__ float4 smem[];
     const BvhNode *snodes = stage_bvh_top(p, smem);
     int64_t ray = 0;
     const bool valid = thread_ray(p, ray);
-    walk32_ray<C, MODE, false>(p, snodes, p.smem_nodes, ray, valid, nullptr);
+    walk32_ray<C, MODE, false, ENTRY>(p, snodes, p.smem_nodes, ray, valid, nullptr);
 }
 
 // Resume kernel: grid-stride over the queued rays (count set by k_walk32).
@@ -1429,11 +1468,11 @@ __global__ void k_side(const double *S, const double *P, const double *p, const 
 
 // ================================================================ launchers
 
-template <int C, int MODE>
+template <int C, int MODE, int ENTRY = ENTRY_BVH>
 static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks, int threads,
                                size_t smem, cudaStream_t stream) {
     KParams p = p0;
-    if (precision != TETPROJ_FILTERED) {
+    if (ENTRY == ENTRY_BVH && precision != TETPROJ_FILTERED) {
         p.block_offset = 0;
         k_walk64<C, MODE><<<(unsigned)nblocks, threads, smem, stream>>>(p);
         note_launch();
@@ -1448,7 +1487,7 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
         p.block_offset = b0;
         cudaError_t e = cudaMemsetAsync(p.q_count, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
-        k_walk32<C, MODE><<<(unsigned)nb, threads, smem, stream>>>(p);
+        k_walk32<C, MODE, ENTRY><<<(unsigned)nb, threads, smem, stream>>>(p);
         note_launch();
         k_resume32<C, MODE><<<rgrid, 128, smem, stream>>>(p);
         note_launch();
@@ -1544,12 +1583,22 @@ cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
     if (nblocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
     size_t smem = (size_t)p.smem_nodes * sizeof(BvhNode);
     if (mode == MODE_FWD) {
+        if (p.entry == ENTRY_RSTAR) {  // the paper's entry structure: FP32, C = 1
+            if (precision != TETPROJ_FILTERED || channels != 1) return cudaErrorInvalidValue;
+            return launch_mode<1, MODE_FWD, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream);
+        }
         return channels == 4 ? launch_mode<4, MODE_FWD>(p, precision, nblocks, threads, smem, stream)
                              : launch_mode<1, MODE_FWD>(p, precision, nblocks, threads, smem, stream);
     }
     if (mode == MODE_BWD) {
         return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, nblocks, threads, smem, stream)
                              : launch_mode<1, MODE_BWD>(p, precision, nblocks, threads, smem, stream);
+    }
+    if (mode == MODE_ENTRY) {
+        if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;
+        return p.entry == ENTRY_RSTAR
+                   ? launch_mode<1, MODE_ENTRY, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream)
+                   : launch_mode<1, MODE_ENTRY>(p, precision, nblocks, threads, smem, stream);
     }
     return launch_mode<1, MODE_TRACE>(p, precision, nblocks, threads, smem, stream);
 }

@@ -10,7 +10,11 @@ namespace tp {
 
 // MODE_SEG: the backprojection's sort-and-reduce variant -- the walk writes
 // each segment (tet, length x y) to a segment buffer instead of adding it.
-enum { MODE_FWD = 0, MODE_BWD = 1, MODE_TRACE = 2, MODE_SEG = 3 };
+// MODE_ENTRY: only the entry search; the entry tet's user id (or -1) goes to
+// tr_count[ray].
+enum { MODE_FWD = 0, MODE_BWD = 1, MODE_TRACE = 2, MODE_SEG = 3, MODE_ENTRY = 4 };
+// entry-search structure of the fast walk
+enum { ENTRY_BVH = 0, ENTRY_RSTAR = 1 };
 
 // One deferred ray: where its walk stopped, so the robust kernel continues
 // from there.  fs < 0: deferred during the entry search (no state yet);
@@ -66,6 +70,7 @@ struct KParams {
     const int64_t *block_off;
     const int32_t *ray_off;
     int64_t seg_base, seg_cap;
+    int32_t entry;  // ENTRY_BVH or ENTRY_RSTAR (fast walk, FWD C = 1 and ENTRY modes)
 };
 
 // One problem of a batched launch: its parameters (operands included) and a

@@ -54,6 +54,22 @@ struct __align__(16) BvhNode {
     float4 rmax;
 };
 
+// R*-tree node over boundary faces (the paper's entry structure, Sec. II-E):
+// at least RSTAR_MIN and at most RSTAR_MAX entries per node (the paper's 4 and
+// 10); child boxes structure-of-arrays; leaves list boundary-face indices.
+constexpr int RSTAR_MIN = 4;
+constexpr int RSTAR_MAX = 10;
+constexpr int RSTAR_MAX_DEPTH = 12;  // device DFS stack: 9 * depth + 1 entries
+
+struct __align__(16) RStarNode {
+    float lo[3][RSTAR_MAX];
+    float hi[3][RSTAR_MAX];
+    int32_t child[RSTAR_MAX];  // internal: node index; leaf: boundary-face index
+    int32_t count;
+    int32_t leaf;  // 1: children are boundary faces
+    int32_t pad[2];
+};
+
 struct AngleFrame {
     double S[3], C[3], U[3], V[3];
 };
@@ -71,6 +87,7 @@ struct MeshView {
     const BFace32 *bfaces;
     const int32_t *perm;  // h -> user tet id
     const int4 *vid;      // h -> user vertex ids in local order
+    const RStarNode *rstar;  // R*-tree of the boundary faces (built on request)
     int64_t nt, nb, nnodes;
     int32_t root;         // root code (0, or a leaf code for tiny meshes)
     float radius;         // max |coordinate| over all vertices

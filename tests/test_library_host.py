@@ -199,3 +199,23 @@ def test_batch_argument_errors(tp):
     assert L.tetproj_batch_forward(None, None) == _lib.ERR_ARG
     assert L.tetproj_batch_backward(None, None) == _lib.ERR_ARG
     assert L.tetproj_batch_destroy(None) == _lib.ERR_ARG
+
+
+def test_rstar_tree_invariants(tp):
+    """The boundary-face R*-tree (the paper's entry structure): node fills
+    within [4, 10], all leaves at one depth, nested boxes, every boundary face
+    in exactly one leaf -- on regular, cubic-mapped and jittered meshes."""
+    cases = []
+    for n in (1, 3, 8):
+        cases.append(W.kuhn_cube(n))
+    v, t = W.kuhn_cube(6)
+    cases.append((W.cubic_map(v), t))
+    v, t = W.kuhn_cube(7)
+    cases.append((W.jitter_interior(v, t, 7, W.rng_for(7, 1)), t))
+    for v, t in cases:
+        info = tp.rstar_build_host(v, t)
+        nb = tp.topology_host(v, t)[1]
+        assert info["ok"] == 1, info
+        assert info["entries"] == nb
+        if info["depth"] > 1:
+            assert 4 <= info["min_fill"] <= info["max_fill"] <= 10
