@@ -219,6 +219,8 @@ def batch_workload(name):
         specs = W.config5_specs()
     elif name == "batch6s":  # small case for quick runs
         specs = [(3, 16, 5), (8, 48, 9), (5, 24, 3), (12, 40, 7), (4, 32, 12), (6, 20, 4)]
+    elif name == "batch1k64":  # one problem, profiler-sized (jittered Kuhn 64^3, 256^2 x 30)
+        specs = [(64, 256, 30)]
     else:
         raise SystemExit(f"unknown workload {name}")
     return [W.config5_problem(k, n, N, na, channels=4) for k, (n, N, na) in enumerate(specs)]
@@ -240,9 +242,14 @@ def run_batch(args, tp, torch, dist, rank, world, local):
     t_tune = time.perf_counter()
     cache = A.Cache(os.path.join(ROOT, "gpurun_out", "autotune.json") if args.tune_cache is None
                     else args.tune_cache, device=torch.cuda.get_device_name(), version=tp.version())
-    choices = A.tune_batch(tp, meshes, geos, channels=C, cache=cache, reps=2)
+    if args.no_tune:  # fixed tiles from --tile / --scatter, Morton order
+        tu, tv = (int(x) for x in args.tile.split("x"))
+        sc = tp.SCATTER_WARP if args.scatter == "warp" else tp.SCATTER_ATOMIC
+        tiles = [(tu, tv, tp.ORDER_MORTON, sc)] * len(ws)
+    else:
+        choices = A.tune_batch(tp, meshes, geos, channels=C, cache=cache, reps=2)
+        tiles = [c.row() for c in choices]
     t_tune = time.perf_counter() - t_tune
-    tiles = [c.row() for c in choices]
     b = tp.Batch(meshes, geos, channels=C, tiles=tiles)
     for k, w in enumerate(ws):
         b.mu[k].copy_(torch.tensor(w.mu, dtype=torch.float32))
@@ -461,6 +468,8 @@ def main():
     ap.add_argument("--scatter", default="atomic", choices=["atomic", "warp", "sort"])
     ap.add_argument("--tile", default="8x8")
     ap.add_argument("--tune-cache", default=None)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched workloads: fixed --tile/--scatter instead of the autotuner")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
