@@ -240,8 +240,7 @@ def run_batch(args, tp, torch, dist, rank, world, local):
     geos = [tp.Geometry.from_cone(w.geom) for w in ws]
     t_build = time.perf_counter() - t_build
     t_tune = time.perf_counter()
-    cache = A.Cache(os.path.join(ROOT, "gpurun_out", "autotune.json") if args.tune_cache is None
-                    else args.tune_cache, device=torch.cuda.get_device_name(), version=tp.version())
+    cache = A.Cache(args.tune_cache, device=torch.cuda.get_device_name(), version=tp.version())
     if args.no_tune:  # fixed tiles from --tile / --scatter, Morton order
         tu, tv = (int(x) for x in args.tile.split("x"))
         sc = tp.SCATTER_WARP if args.scatter == "warp" else tp.SCATTER_ATOMIC

@@ -5,7 +5,7 @@ Tolerances.  Per ray: |b_gpu - b_ref| <= tau * sum_i a_ij |mu_i| +
 unit roundoff of the path (2^-53 or 2^-24) and R the largest |coordinate| of
 the mesh.  The second term is the coordinate quantum: a crossing point cannot
 be placed closer than ~u R, so rays that only clip a corner (chords ~1e-5)
-are judged on it.  Per tet: tau * sum_j a_ij |y_j|.
+are held to it.  Per tet: tau * sum_j a_ij |y_j|.
 
 References.  b_ref is the oracle's brute-force clip, except for rays the
 oracle flags as (nearly) inside a face plane, where FP64 clipping cannot tell
