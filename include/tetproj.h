@@ -286,7 +286,7 @@ tetproj_status tetproj_batch_destroy(tetproj_batch *b);
  * with a safety margin eps = 1e-9 multiplied by 10 until two faces of the
  * current tet are hit; the walk leaves through the face of the larger hit
  * parameter.  A COMPARISON mode for the paper's floating-point experiment
- * (Sec. IV): FP32 (TETPROJ_FILTERED selects single precision here) or FP64
+ * (Sec. III-C): FP32 (TETPROJ_FILTERED selects single precision here) or FP64
  * (TETPROJ_PLAIN_FP64) arithmetic throughout, no exact predicates.  Forward
  * only, C = 1, tiles of at most 128 rays.  status (device int8 [nrays], or
  * NULL): 0 = walk completed (or missed the mesh), 1 = halted (eps reached

@@ -7,7 +7,7 @@
  * Unlike oracle.c, which evaluates the plain definition a_ij = |ray cap tet|,
  * this file follows the paper's heuristic walk step by step, because the
  * quantity of interest is what that algorithm does in a given precision
- * (Sec. II-C.1, Sec. IV "Floating point errors"):
+ * (Sec. II-C.1, Sec. III-C "Floating point errors"):
  *
  *   Alg. 1 (Moller-Trumbore with safety parameter eps), for ray R1 + t d and
  *   triangle P1 P2 P3:  E1 = P2 - P1, E2 = P3 - P1, q = d x E2, a = E1 . q;

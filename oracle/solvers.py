@@ -2,7 +2,7 @@
 infrastructure only; nothing in the product imports this module).
 
 The paper poses reconstruction as the linear system A x = b (Eq. 1-3) and
-solves it with OS-SART, 50 iterations over blocks of 20 projections (Sec. IV,
+solves it with OS-SART, 50 iterations over blocks of 20 projections (Sec. III-A,
 image reconstruction); it also names CGLS among the usable algorithms
 (Sec. II-A).  Both are written here from their textbook definitions, in FP64
 numpy, over callables so that the same code runs on explicit dense matrices

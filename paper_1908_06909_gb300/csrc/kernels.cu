@@ -1230,7 +1230,7 @@ int device_sm_count() { return sm_count(); }
 // ========================================== the paper's walk (comparison)
 //
 // Alg. 1 and 2 as the paper prints them, kept as a comparison mode for the
-// floating-point experiment of Sec. IV (not the product path, which decides
+// floating-point experiment of Sec. III-C (not the product path, which decides
 // exit faces with exact signs).  Per ray: l = |R2 - R1|; the entry tet is the
 // boundary face with the smallest Moller-Trumbore parameter t >= 0 (the
 // paper's R*-tree search keeps the minimum t; the same boundary-face BVH is

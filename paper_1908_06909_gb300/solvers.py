@@ -1,7 +1,7 @@
 """Iterative reconstruction on the GPU projectors.
 
 The paper reconstructs with OS-SART, 50 iterations over blocks of 20
-projections (Sec. IV), and names CGLS among the algorithms the projectors
+projections (Sec. III-A), and names CGLS among the algorithms the projectors
 serve (Sec. II-A): every such algorithm needs only A x and A^T y (Eq. 2, 3).
 Here both run on ``tetproj_forward`` / ``tetproj_backward`` (float32 tensors:
 the filtered path; float64: the plain FP64 path); the O(n) vector updates

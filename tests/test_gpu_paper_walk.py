@@ -7,7 +7,7 @@ comparison mode, GPU.
   mesh with detector rays and on a cubic-mapped (high aspect ratio) mesh with
   rays aimed exactly at vertices, edge midpoints and face points.
 * On generic rays the FP64 walk agrees with the plain definition (oracle.c).
-* The floating-point experiment of Sec. IV on the robustness workload
+* The floating-point experiment of Sec. III-C on the robustness workload
   (cubic-mapped Kuhn 64^3, 256^2 x 180 rays + 1M adversarial rays): rays
   that halt or loop in FP32 and FP64 Alg. 1-2, against the exact-predicate
   filtered walk (no failures).  Counts are printed and recorded in the design
@@ -99,7 +99,7 @@ def test_paper_walk_matches_reference_adversarial(tp, prec):
 
 
 def test_floating_point_experiment_robustness_workload(tp):
-    """Sec. IV: single-precision Alg. 1-2 loses rays (halts / loops) on a mesh
+    """Sec. III-C: single-precision Alg. 1-2 loses rays (halts / loops) on a mesh
     with large aspect ratios; the exact-predicate walk loses none."""
     import torch
     w = W.config3()
