@@ -79,6 +79,22 @@ def measured_traffic(workload, tile, order, scatter):
     return vals["t"]
 
 
+def max_over_ranks(ms, dist, device="cuda"):
+    """The slowest rank's time (every rank gets it); the value itself without
+    a process group."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, ms):
+    """Whole-job rate: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -297,13 +313,10 @@ def run_batch(args, tp, torch, dist, rank, world, local):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t = torch.tensor([start.elapsed_time(end)], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step = float(t.item()) / args.steps
+    ms_step = max_over_ranks(start.elapsed_time(end), dist) / args.steps
     fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     bwd_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
-    value = world * nrays / (ms_step / 1e3)
+    value = job_throughput(world, nrays, ms_step)
     segs = sf["segments"] + sb["segments"]
 
     # the same problems as sequential single-problem calls (same options)
@@ -375,7 +388,7 @@ def run_batch(args, tp, torch, dist, rank, world, local):
             back_h[k].copy_(b.mu_out[k], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
     h2d = sum(x.numel() * 4 for x in mu_h)
     d2h = sum(x.numel() * 4 for x in proj_h) + sum(x.numel() * 4 for x in back_h)
     del mu_h, proj_h, back_h
@@ -422,7 +435,7 @@ def run_batch(args, tp, torch, dist, rank, world, local):
                        "channels": C, "precision": "filtered", "launch": "persistent work queue, CUDA graph",
                        "work_item": "32-ray warp slice of a tile", "tiles": tiles,
                        "l2": "inputs larger than L2", "parallelism": f"replicas{world}"},
-            "gsegments_per_s": world * segs / (ms_step / 1e3) / 1e9,
+            "gsegments_per_s": job_throughput(world, segs, ms_step) / 1e9,
             "segments_per_step": segs,
             "unbatched": {"ms_per_step": single_ms, "value": nrays / (single_ms / 1e3),
                           "speedup_batched": single_ms / ms_step},
@@ -433,7 +446,7 @@ def run_batch(args, tp, torch, dist, rank, world, local):
                            "sample": "every 8th angle of each problem, time scaled by ray count"},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * nrays / (e2e_ms / 1e3), "unit": "rays/s",
+            "e2e": {"value": job_throughput(world, nrays, e2e_ms), "unit": "rays/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # kernels captured in the two graphs (counted by the library at
             # capture) times the replays of the timed region
@@ -551,12 +564,9 @@ def main():
     total_ms = start.elapsed_time(end)
     fwd_ms = float(np.mean([a.elapsed_time(b) for a, b, _ in evs]))
     bwd_ms = float(np.mean([b.elapsed_time(c) for _, b, c in evs]))
-    t = torch.tensor([total_ms], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step = float(t.item()) / args.steps
+    ms_step = max_over_ranks(total_ms, dist) / args.steps
     nrays = geo.nrays
-    value = world * nrays / (ms_step / 1e3)
+    value = job_throughput(world, nrays, ms_step)
     segs = sf["segments"] + sb["segments"]
 
     # plain FP64 path (the ratio's denominator), same step
@@ -601,10 +611,7 @@ def main():
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / args.steps
-    te = torch.tensor([e2e_ms], device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * nrays / (float(te.item()) / 1e3), "unit": "rays/s",
+    e2e = {"value": job_throughput(world, nrays, max_over_ranks(e2e_ms, dist)), "unit": "rays/s",
            "h2d_bytes_per_step": mu_h.numel() * 4,
            "d2h_bytes_per_step": proj_h.numel() * 4 + back_h.numel() * 4}
 
@@ -648,7 +655,7 @@ def main():
                        "scatter": args.scatter,
                        "l2": l2_note(mesh.nt, nrays, C),
                        "parallelism": f"replicas{world}"},
-            "gsegments_per_s": world * segs / (ms_step / 1e3) / 1e9,
+            "gsegments_per_s": job_throughput(world, segs, ms_step) / 1e9,
             "segments_per_step": segs,
             "plain_fp64": plain,
             "roofline": roof,

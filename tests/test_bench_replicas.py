@@ -1,0 +1,55 @@
+"""The multi-process replica path of bench.py on the CPU (gloo, world size 2):
+every rank gets the slowest rank's time, and the whole-job rate counts every
+rank's units over that time.  (On GPUs the same functions run over NCCL with
+one process per GPU; each rank projects its own replica, no data exchange.)"""
+import os
+import socket
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, times, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = bench.max_over_ranks(times[rank], dist, device="cpu")
+    out.put((rank, ms, bench.job_throughput(world, 1000, ms)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_throughput_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    times = [120.0, 80.0]
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, times, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, rate in res:
+        assert ms == 120.0
+        assert rate == pytest.approx(2 * 1000 / 0.12)
+
+
+def test_single_process_paths():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(42.0, None) == 42.0
+    assert bench.job_throughput(1, 500, 250.0) == pytest.approx(2000.0)
