@@ -480,6 +480,8 @@ def main():
     ap.add_argument("--scatter", default="atomic", choices=["atomic", "warp", "sort"])
     ap.add_argument("--tile", default="8x8")
     ap.add_argument("--tune-cache", default=None)
+    ap.add_argument("--acc", default="auto", choices=["auto", "f32", "f64"],
+                    help="accumulator of the filtered backprojection (auto: FP64 at C = 1)")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workloads: fixed --tile/--scatter instead of the autotuner")
     args = ap.parse_args()
@@ -515,7 +517,8 @@ def main():
     tu, tv = (int(x) for x in args.tile.split("x"))
     opt = tp.make_options(tile=(tu, tv), scatter={"atomic": tp.SCATTER_ATOMIC,
                                                   "warp": tp.SCATTER_WARP,
-                                                  "sort": tp.SCATTER_SORT}[args.scatter])
+                                                  "sort": tp.SCATTER_SORT}[args.scatter],
+                          flags={"auto": 0, "f64": tp.FLAG_ACC64, "f32": tp.FLAG_ACC32}[args.acc])
     C = 1
     mu = torch.tensor(w.mu, dtype=torch.float32, device="cuda")
     proj = torch.empty(geo.shape, dtype=torch.float32, device="cuda")
@@ -652,7 +655,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": w.name, "nt": mesh.nt, "rays_per_step": nrays,
                        "channels": C, "precision": "filtered", "tile": args.tile,
-                       "scatter": args.scatter,
+                       "scatter": args.scatter, "accumulator": ("f64" if args.scatter == "atomic" else "f32") if args.acc == "auto" else args.acc,
                        "l2": l2_note(mesh.nt, nrays, C),
                        "parallelism": f"replicas{world}"},
             "gsegments_per_s": job_throughput(world, segs, ms_step) / 1e9,

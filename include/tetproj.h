@@ -88,6 +88,16 @@ typedef int32_t tetproj_status;
                                       instead of the binary BVH: filtered forward
                                       (C = 1) and tetproj_entry only; the tree is
                                       built on first use (synchronous)          */
+#define TETPROJ_FLAG_ACC64 2       /* filtered backprojection with atomic scatter:
+                                      add the FP32 segment contributions into an
+                                      FP64 accumulator (red.global.add.f64) and
+                                      round once: ~1e-7 for any number of
+                                      segments per tet.  Default for C = 1.    */
+#define TETPROJ_FLAG_ACC32 4       /* the same into an FP32 accumulator (faster for
+                                      C = 4: one 16-byte red per segment instead
+                                      of four 8-byte ones; FP32 sums drift like
+                                      sqrt(segments per tet) * 2^-24).  Default
+                                      for C = 4.  At most one ACC flag.        */
 
 typedef struct tetproj_mesh tetproj_mesh;
 typedef struct tetproj_geometry tetproj_geometry;
@@ -100,7 +110,7 @@ typedef struct tetproj_options {
     int32_t order;     /* TETPROJ_ORDER_MORTON (default) or TETPROJ_ORDER_ROW          */
     int32_t scatter;   /* TETPROJ_SCATTER_ATOMIC (default), _WARP or _SORT             */
     int32_t max_steps; /* walk step limit per ray; 0 = 64 + 16*ceil(nt^(1/3))          */
-    int32_t flags;     /* 0 or TETPROJ_FLAG_RSTAR_ENTRY                               */
+    int32_t flags;     /* 0 or an or of TETPROJ_FLAG_* (RSTAR_ENTRY, ACC64 | ACC32)   */
 } tetproj_options;
 
 typedef struct tetproj_stats {
@@ -260,7 +270,8 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
  *   channels: C = 1 or 4 for every problem.
  * The batch owns per-problem workspace and one deferral queue (allocated
  * here); it keeps pointers into the meshes and geometries, which must outlive
- * it.  Rays are processed in rounds of at most 2^23 rays.
+ * it.  Backprojections add into FP64 accumulators at C = 1 (each problem's
+ * scatter choice then does not apply) and into FP32 ones at C = 4.  Rays are processed in rounds of at most 2^23 rays.
  * Errors: TETPROJ_ERR_ARG (null handle, n < 1, bad channels or tiles),
  * TETPROJ_ERR_TOO_LARGE (2^40 work items or more), CUDA
  * errors of the allocations; *out is NULL on error. */

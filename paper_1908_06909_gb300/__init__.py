@@ -18,13 +18,13 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (FILTERED, FLAG_RSTAR_ENTRY, ORDER_MORTON, ORDER_ROW, PLAIN_FP64,
+from ._lib import (FILTERED, FLAG_ACC32, FLAG_ACC64, FLAG_RSTAR_ENTRY, ORDER_MORTON, ORDER_ROW, PLAIN_FP64,
                    SCATTER_ATOMIC, SCATTER_SORT, SCATTER_WARP, Options, TetprojError, check)
 
 __all__ = ["Mesh", "Geometry", "Batch", "forward", "forward_mt", "forward_rays_mt", "backward", "backward_noalloc", "forward_rays", "backward_rays",
            "trace_rays", "side_signs_host", "side_signs_device", "TetProject", "make_options",
            "FILTERED", "PLAIN_FP64", "ORDER_ROW", "ORDER_MORTON", "SCATTER_ATOMIC",
-           "SCATTER_WARP", "SCATTER_SORT", "FLAG_RSTAR_ENTRY", "entry", "rstar_build_host",
+           "SCATTER_WARP", "SCATTER_SORT", "FLAG_RSTAR_ENTRY", "FLAG_ACC64", "FLAG_ACC32", "entry", "rstar_build_host",
            "TetprojError", "library_path"]
 
 

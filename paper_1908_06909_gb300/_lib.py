@@ -29,6 +29,8 @@ SCATTER_ATOMIC = 0
 SCATTER_WARP = 1
 SCATTER_SORT = 2
 FLAG_RSTAR_ENTRY = 1
+FLAG_ACC64 = 2
+FLAG_ACC32 = 4
 
 c_vp = ctypes.c_void_p
 c_i32 = ctypes.c_int32

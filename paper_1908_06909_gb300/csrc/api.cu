@@ -422,7 +422,10 @@ static tetproj_status check_opts(const tetproj_options *in, tetproj_options &o) 
     if (o.scatter != TETPROJ_SCATTER_ATOMIC && o.scatter != TETPROJ_SCATTER_WARP &&
         o.scatter != TETPROJ_SCATTER_SORT)
         return TETPROJ_ERR_ARG;
-    if (o.max_steps < 0 || (o.flags & ~TETPROJ_FLAG_RSTAR_ENTRY) != 0) return TETPROJ_ERR_ARG;
+    if (o.max_steps < 0 ||
+        (o.flags & ~(TETPROJ_FLAG_RSTAR_ENTRY | TETPROJ_FLAG_ACC64 | TETPROJ_FLAG_ACC32)) != 0 ||
+        ((o.flags & TETPROJ_FLAG_ACC64) && (o.flags & TETPROJ_FLAG_ACC32)))
+        return TETPROJ_ERR_ARG;
     return TETPROJ_OK;
 }
 
@@ -518,9 +521,38 @@ static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_opt
     return TETPROJ_OK;
 }
 
+// Accumulator of the filtered backprojection with atomic scatter: FP64 unless
+// TETPROJ_FLAG_ACC32, or C = 4 without TETPROJ_FLAG_ACC64 (measured on GB300:
+// at C = 1 the FP64 reduction is also the faster one; at C = 4 it needs four
+// 8-byte reductions per segment against one 16-byte FP32 one).
+static bool use_acc64(const tetproj_options &o) {
+    if (o.precision != TETPROJ_FILTERED || o.scatter != TETPROJ_SCATTER_ATOMIC) return false;
+    if (o.flags & TETPROJ_FLAG_ACC64) return true;
+    if (o.flags & TETPROJ_FLAG_ACC32) return false;
+    return o.channels == 1;
+}
+
 static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
                                    const void *y, void *mu_out, cudaStream_t s) {
     if (rstar_unsupported(o)) return TETPROJ_ERR_ARG;
+    if ((o.flags & TETPROJ_FLAG_ACC64) && o.precision == TETPROJ_FILTERED &&
+        o.scatter != TETPROJ_SCATTER_ATOMIC)
+        return TETPROJ_ERR_ARG;  // FP64 accumulation is an atomic-scatter variant
+    if (use_acc64(o)) {
+        // FP32 walk, FP64 accumulator (the plain path's workspace), one rounding at the end
+        tetproj_status st = ensure_ws(m, TETPROJ_PLAIN_FP64, o.channels);
+        if (st == TETPROJ_OK) st = attach_queue(m, p, o);
+        if (st != TETPROJ_OK) return st;
+        void *ws = m->ws[1][o.channels == 4];
+        TP_CUDA(cudaMemsetAsync(ws, 0, (size_t)m->ws_bytes[1][o.channels == 4], s));
+        p.in = y;
+        p.out = ws;
+        TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD64, s));
+        TP_CUDA(launch_scatter_perm_d2f(m->perm, m->nt, o.channels,
+                                        reinterpret_cast<const double *>(ws),
+                                        reinterpret_cast<float *>(mu_out), s));
+        return TETPROJ_OK;
+    }
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
     if (st == TETPROJ_OK) st = attach_queue(m, p, o);
     if (st != TETPROJ_OK) return st;
@@ -694,7 +726,9 @@ tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry
     KParams p = base_params(m, o);
     set_cone(p, geo);
     if (o.scatter == TETPROJ_SCATTER_SORT) {
-        if (o.precision != TETPROJ_FILTERED || rstar_unsupported(o)) return TETPROJ_ERR_ARG;
+        if (o.precision != TETPROJ_FILTERED || rstar_unsupported(o) ||
+            (o.flags & (TETPROJ_FLAG_ACC64 | TETPROJ_FLAG_ACC32)))
+            return TETPROJ_ERR_ARG;
         return run_backward_sort(m, geo, p, o, proj, mu_out, (cudaStream_t)stream);
     }
     return run_backward(m, p, o, proj, mu_out, (cudaStream_t)stream);
@@ -843,8 +877,8 @@ extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
     if (!mesh || !geo || !proj || !mu_out) return TETPROJ_ERR_ARG;
     tetproj_options o;
     tetproj_status st = check_opts(opt, o);
-    if (st == TETPROJ_OK && (o.scatter == TETPROJ_SCATTER_SORT || rstar_unsupported(o)))
-        st = TETPROJ_ERR_ARG;  // both allocate
+    if (st == TETPROJ_OK && (o.scatter == TETPROJ_SCATTER_SORT || o.flags != 0))
+        st = TETPROJ_ERR_ARG;  // FP32 atomics into the fixed scratch only
     if (st != TETPROJ_OK) return st;
     const int f64 = o.precision == TETPROJ_PLAIN_FP64;
     const int64_t acc_bytes = mesh->nt * o.channels * (f64 ? 8 : 4);
@@ -898,6 +932,7 @@ struct tetproj_batch {
     int64_t q_cap = 0;
     int smem_nodes = 64;
     unsigned grid_fwd = 0, grid_bwd = 0, rgrid = 0;
+    bool acc64 = false;  // C = 1: FP64 accumulators (the per-problem scatter choice is for C = 4)
     bool bound = false;
 };
 
@@ -926,6 +961,7 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
     if (!b) return TETPROJ_ERR_OOM;
     b->n = n;
     b->channels = channels;
+    b->acc64 = channels == 1;
     b->item_begin.assign(1, 0);
     int64_t total_rays = 0;
     for (int k = 0; k < n; ++k) {
@@ -958,7 +994,8 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
         int64_t bytes = meshes[k]->nt * channels * 4;
         void *a = nullptr, *c = nullptr;
         cudaError_t e = cudaMalloc(&a, (size_t)bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&c, (size_t)bytes);
+        // accumulator: sized for FP64 (the FP32 case uses the first half)
+        if (e == cudaSuccess) e = cudaMalloc(&c, (size_t)(2 * bytes));
         b->ws_in.push_back(a);
         b->ws_acc.push_back(c);
         b->ws_bytes.push_back(bytes);
@@ -983,7 +1020,8 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
     for (auto &p : b->base) snodes = p.smem_nodes > snodes ? p.smem_nodes : snodes;
     b->smem_nodes = snodes < kBatchWarpNodes ? snodes : kBatchWarpNodes;
     e = batch_grid(channels, MODE_FWD, b->smem_nodes, b->grid_fwd);
-    if (e == cudaSuccess) e = batch_grid(channels, MODE_BWD, b->smem_nodes, b->grid_bwd);
+    if (e == cudaSuccess)
+        e = batch_grid(channels, b->acc64 ? MODE_BWD64 : MODE_BWD, b->smem_nodes, b->grid_bwd);
     if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
     b->rgrid = (unsigned)(4 * device_sm_count());
     for (auto &p : b->base) {
@@ -1046,13 +1084,19 @@ extern "C" tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream)
         if (!b->y[k] || !b->mu_out[k]) return TETPROJ_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < b->n; ++k)
-        TP_CUDA(cudaMemsetAsync(b->ws_acc[k], 0, (size_t)b->ws_bytes[k], s));
+        TP_CUDA(cudaMemsetAsync(b->ws_acc[k], 0, (size_t)(b->acc64 ? 2 : 1) * b->ws_bytes[k], s));
     TP_CUDA(launch_batch(b->d_bwd, b->d_item_begin, b->n, b->item_begin.back(),
-                         b->channels, MODE_BWD, b->grid_bwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
+                         b->channels, b->acc64 ? MODE_BWD64 : MODE_BWD, b->grid_bwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
                          b->smem_nodes, s));
-    for (int k = 0; k < b->n; ++k)
-        TP_CUDA(launch_scatter_perm(b->meshes[k]->perm, b->meshes[k]->nt, b->channels, 0,
-                                    b->ws_acc[k], b->mu_out[k], s));
+    for (int k = 0; k < b->n; ++k) {
+        if (b->acc64)
+            TP_CUDA(launch_scatter_perm_d2f(b->meshes[k]->perm, b->meshes[k]->nt, b->channels,
+                                            reinterpret_cast<const double *>(b->ws_acc[k]),
+                                            reinterpret_cast<float *>(b->mu_out[k]), s));
+        else
+            TP_CUDA(launch_scatter_perm(b->meshes[k]->perm, b->meshes[k]->nt, b->channels, 0,
+                                        b->ws_acc[k], b->mu_out[k], s));
+    }
     return TETPROJ_OK;
 }
 

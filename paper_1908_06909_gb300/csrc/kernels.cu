@@ -514,7 +514,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             }
             alive = true;
         }
-        if ((MODE == MODE_BWD || MODE == MODE_SEG) && alive) {
+        if ((MODE == MODE_BWD || MODE == MODE_SEG || MODE == MODE_BWD64) && alive) {
             const float *y = reinterpret_cast<const float *>(p.in) + ray * C;
 #pragma unroll
             for (int c = 0; c < C; ++c) yv[c] = __ldg(y + c);
@@ -670,6 +670,11 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 alive = false;
             }
             ++spos;
+        }
+        if (MODE == MODE_BWD64 && did) {  // FP64 accumulation: no drift with many segments
+            double *acc64 = reinterpret_cast<double *>(p.out) + (int64_t)hcur * C;
+#pragma unroll
+            for (int cc = 0; cc < C; ++cc) atomicAdd(acc64 + cc, (double)(len * yv[cc]));
         }
         if (MODE == MODE_BWD) {
             if (!ROBUST && p.scatter == TETPROJ_SCATTER_WARP) {
@@ -1180,6 +1185,9 @@ cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid) {
     if (mode == MODE_FWD)
         return channels == 4 ? batch_grid_mode<4, MODE_FWD>(smem_nodes, grid)
                              : batch_grid_mode<1, MODE_FWD>(smem_nodes, grid);
+    if (mode == MODE_BWD64)
+        return channels == 4 ? batch_grid_mode<4, MODE_BWD64>(smem_nodes, grid)
+                             : batch_grid_mode<1, MODE_BWD64>(smem_nodes, grid);
     return channels == 4 ? batch_grid_mode<4, MODE_BWD>(smem_nodes, grid)
                          : batch_grid_mode<1, MODE_BWD>(smem_nodes, grid);
 }
@@ -1220,6 +1228,9 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
     if (mode == MODE_FWD)
         return channels == 4 ? launch_batch_mode<4, MODE_FWD>(TP_BATCH_ARGS)
                              : launch_batch_mode<1, MODE_FWD>(TP_BATCH_ARGS);
+    if (mode == MODE_BWD64)
+        return channels == 4 ? launch_batch_mode<4, MODE_BWD64>(TP_BATCH_ARGS)
+                             : launch_batch_mode<1, MODE_BWD64>(TP_BATCH_ARGS);
     return channels == 4 ? launch_batch_mode<4, MODE_BWD>(TP_BATCH_ARGS)
                          : launch_batch_mode<1, MODE_BWD>(TP_BATCH_ARGS);
 #undef TP_BATCH_ARGS
@@ -1439,6 +1450,24 @@ __global__ void k_scatter_perm(const int32_t *__restrict__ perm, int64_t nt, int
     dst[(int64_t)__ldg(perm + h) * C + c] = src[i];
 }
 
+__global__ void k_scatter_perm_d2f(const int32_t *__restrict__ perm, int64_t nt, int C,
+                                   const double *__restrict__ src, float *__restrict__ dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt * C) return;
+    int64_t h = i / C;
+    int c = (int)(i - h * C);
+    dst[(int64_t)__ldg(perm + h) * C + c] = (float)src[i];
+}
+
+cudaError_t launch_scatter_perm_d2f(const int32_t *perm, int64_t nt, int channels,
+                                    const double *src_h, float *dst_user, cudaStream_t stream) {
+    int64_t blocks = (nt * channels + 255) / 256;
+    if (blocks <= 0) return cudaSuccess;
+    k_scatter_perm_d2f<<<(unsigned)blocks, 256, 0, stream>>>(perm, nt, channels, src_h, dst_user);
+    note_launch();
+    return cudaGetLastError();
+}
+
 __global__ void k_geometry_rays(GeoView g, const int64_t *idx, int64_t n, double *src,
                                 double *dst) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1472,11 +1501,15 @@ template <int C, int MODE, int ENTRY = ENTRY_BVH>
 static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks, int threads,
                                size_t smem, cudaStream_t stream) {
     KParams p = p0;
-    if (ENTRY == ENTRY_BVH && precision != TETPROJ_FILTERED) {
-        p.block_offset = 0;
-        k_walk64<C, MODE><<<(unsigned)nblocks, threads, smem, stream>>>(p);
-        note_launch();
-        return cudaGetLastError();
+    if constexpr (ENTRY == ENTRY_BVH && MODE != MODE_BWD64 && MODE != MODE_ENTRY) {
+        if (precision != TETPROJ_FILTERED) {
+            p.block_offset = 0;
+            k_walk64<C, MODE><<<(unsigned)nblocks, threads, smem, stream>>>(p);
+            note_launch();
+            return cudaGetLastError();
+        }
+    } else {
+        if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;
     }
     // chunks of at most q_cap rays, each followed by the resume kernel
     int64_t chunk = p.q_cap / threads;
@@ -1593,6 +1626,11 @@ cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
     if (mode == MODE_BWD) {
         return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, nblocks, threads, smem, stream)
                              : launch_mode<1, MODE_BWD>(p, precision, nblocks, threads, smem, stream);
+    }
+    if (mode == MODE_BWD64) {
+        if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;
+        return channels == 4 ? launch_mode<4, MODE_BWD64>(p, precision, nblocks, threads, smem, stream)
+                             : launch_mode<1, MODE_BWD64>(p, precision, nblocks, threads, smem, stream);
     }
     if (mode == MODE_ENTRY) {
         if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;

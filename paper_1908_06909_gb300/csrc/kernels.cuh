@@ -11,8 +11,9 @@ namespace tp {
 // MODE_SEG: the backprojection's sort-and-reduce variant -- the walk writes
 // each segment (tet, length x y) to a segment buffer instead of adding it.
 // MODE_ENTRY: only the entry search; the entry tet's user id (or -1) goes to
-// tr_count[ray].
-enum { MODE_FWD = 0, MODE_BWD = 1, MODE_TRACE = 2, MODE_SEG = 3, MODE_ENTRY = 4 };
+// tr_count[ray].  MODE_BWD64: the filtered backprojection with FP64
+// accumulation (p.out is a double [nt][C] buffer; red.global.add.f64).
+enum { MODE_FWD = 0, MODE_BWD = 1, MODE_TRACE = 2, MODE_SEG = 3, MODE_ENTRY = 4, MODE_BWD64 = 5 };
 // entry-search structure of the fast walk
 enum { ENTRY_BVH = 0, ENTRY_RSTAR = 1 };
 
@@ -147,6 +148,9 @@ cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, in
                                const void *src_user, void *dst_h, cudaStream_t stream);
 cudaError_t launch_scatter_perm(const int32_t *perm, int64_t nt, int channels, int f64,
                                 const void *src_h, void *dst_user, cudaStream_t stream);
+// the same from a double accumulator into float output (rounded once)
+cudaError_t launch_scatter_perm_d2f(const int32_t *perm, int64_t nt, int channels,
+                                    const double *src_h, float *dst_user, cudaStream_t stream);
 cudaError_t launch_geometry_rays(const GeoView &g, const int64_t *idx, int64_t n, double *src,
                                  double *dst, cudaStream_t stream);
 cudaError_t launch_side_device(const double *S, const double *P, const double *p,

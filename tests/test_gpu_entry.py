@@ -73,7 +73,7 @@ def test_rstar_flag_rejected_where_unsupported(tp):
         tp.forward(mesh, geo, torch.ones((mesh.nt, 4), device="cuda"),
                    options=tp.make_options(channels=4, flags=tp.FLAG_RSTAR_ENTRY))
     with pytest.raises(tp.TetprojError):  # unknown flag
-        tp.forward(mesh, geo, torch.ones(mesh.nt, device="cuda"), options=tp.make_options(flags=2))
+        tp.forward(mesh, geo, torch.ones(mesh.nt, device="cuda"), options=tp.make_options(flags=8))
 
 
 def _time(fn, reps=3):

@@ -119,3 +119,70 @@ def test_robustness_workload(tp, c3, prec):
     ok[ref["skipped"]] = False
     _rel_report(f"C3 adversarial {prec}", got[ok], ref["want"][ok], want[ok])
     assert np.all(np.abs(got - ref["want"])[ok] <= TOL[prec] * want[ok] + fl)
+
+
+@pytest.mark.parametrize("k", [8, 18, 12])
+def test_batched_workload_problem_sampled(tp, k):
+    """Full-size problems of the batched workload (config 5) through the batched
+    launch: #8 (34^3 cells, 1022^2 x 310 rays) and #18 (27^3, 811^2 x 451) put
+    ~10^5 segments into each tet, #12 is the largest mesh (118^3, 9.9M tets).
+    4 channels; sampled rays against the oracle's clipping, sampled central
+    tets' backprojections of the projection against the oracle's sums."""
+    import torch
+    n, N, na = W.config5_specs()[k]
+    w = W.config5_problem(k, n, N, na, channels=4)
+    mesh = tp.Mesh(w.verts, w.tets)
+    geo = tp.Geometry.from_cone(w.geom)
+    b = tp.Batch([mesh], [geo], channels=4, tiles=[(16, 8, tp.ORDER_MORTON, tp.SCATTER_ATOMIC)])
+    b.mu[0].copy_(torch.tensor(w.mu, dtype=torch.float32))
+    b.forward()
+    b.y[0].copy_(b.proj[0])
+    b.backward()
+    torch.cuda.synchronize()
+    assert mesh.stats()["error"] == 0
+    rng = np.random.default_rng(300 + k)
+    idx = np.sort(rng.choice(geo.nrays, 48, replace=False))
+    want = oracle.forward_cone(w.verts, w.tets, w.mu, w.geom, idx)
+    scale = oracle.forward_cone(w.verts, w.tets, np.abs(w.mu), w.geom, idx)
+    S, P = oracle.cone_rays(w.geom, idx)
+    planar = oracle.trace_rays(w.verts, w.tets, S, P, max_visits=2)[5]
+    got = b.proj[0].reshape(-1, 4)[torch.tensor(idx, device="cuda")].double().cpu().numpy()
+    ok = ~planar
+    _rel_report(f"C5#{k} forward f32", got[ok], want[ok], scale[ok])
+    assert np.all((np.abs(got - want) <= TOL["f32"] * scale + floor_abs("f32", w.verts, w.mu))[ok])
+    cen = W.tet_centroids(w.verts, w.tets)
+    near = np.nonzero(np.linalg.norm(cen, axis=1) < 0.3)[0]
+    tets = rng.choice(near, 3, replace=False)
+    y = b.y[0].double().cpu().numpy().reshape(-1, 4)
+    wantb = oracle.backward_cone_subset(w.verts, w.tets, y, w.geom, tets)
+    gotb = b.mu_out[0][torch.tensor(tets, device="cuda")].double().cpu().numpy()
+    _rel_report(f"C5#{k} backward f32", gotb, wantb, wantb)
+    assert np.all(np.abs(gotb - wantb) <= TOL["f32"] * wantb)
+    b.close()
+
+
+def test_fp64_accumulator_many_segments_per_tet(tp):
+    """Problem #18 of the batched workload (27^3 cells, 811^2 x 451 rays, ~10^5
+    segments per tet): FP32 atomic sums (TETPROJ_FLAG_ACC32) come within 1e-5 of
+    the oracle only just; the FP64 accumulator (the default at C = 1) keeps ~1e-7."""
+    import torch
+    k = 18
+    n, N, na = W.config5_specs()[k]
+    w = W.config5_problem(k, n, N, na, channels=1)
+    mesh = tp.Mesh(w.verts, w.tets)
+    geo = tp.Geometry.from_cone(w.geom)
+    mu = torch.tensor(w.mu[:, 0], dtype=torch.float32, device="cuda")
+    y = tp.forward(mesh, geo, mu)
+    b32 = tp.backward(mesh, geo, y, options=tp.make_options(flags=tp.FLAG_ACC32))
+    b64 = tp.backward(mesh, geo, y)  # the default for C = 1
+    rng = np.random.default_rng(318)
+    cen = W.tet_centroids(w.verts, w.tets)
+    tets = rng.choice(np.nonzero(np.linalg.norm(cen, axis=1) < 0.3)[0], 4, replace=False)
+    wantb = oracle.backward_cone_subset(w.verts, w.tets, y.double().cpu().numpy().reshape(-1),
+                                        w.geom, tets)
+    idx = torch.tensor(tets, device="cuda")
+    g32 = b32[idx].double().cpu().numpy()
+    g64 = b64[idx].double().cpu().numpy()
+    _rel_report("C5#18 backward f32 accumulator", g32, wantb, wantb)
+    _rel_report("C5#18 backward f64 accumulator", g64, wantb, wantb)
+    assert np.all(np.abs(g64 - wantb) <= 1e-6 * wantb)

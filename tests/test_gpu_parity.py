@@ -337,3 +337,33 @@ def test_empty_and_single_tet(tp):
     for dt, tol in ((torch.float64, 1e-14), (torch.float32, 1e-6)):
         got = tp.forward_rays(mesh, src, dst, mu.to(dt)).double().cpu().numpy()
         assert np.allclose(got, 2.0 * rows[:, 6], rtol=tol, atol=tol)
+
+
+@pytest.mark.parametrize("C", [1, 4])
+def test_backward_fp64_accumulator_c1(tp, c1, C):
+    """Backprojection accumulators: FP64 (TETPROJ_FLAG_ACC64, default at C = 1)
+    and FP32 (TETPROJ_FLAG_ACC32, default at C = 4) meet the same oracle bound;
+    invalid combinations are rejected."""
+    import torch
+    w = c1.w
+    rng = np.random.default_rng(31 + C)
+    y = rng.uniform(-1, 1, size=(c1.geo.nrays, C))
+    y[c1.planar] = 0.0
+    y = y.astype(np.float32).astype(np.float64)
+    yt = torch.tensor(y.reshape(c1.geo.shape + ((C,) if C > 1 else ())), dtype=torch.float32,
+                      device="cuda")
+    o = tp.make_options(channels=C, flags=tp.FLAG_ACC64)
+    got = tp.backward(c1.mesh, c1.geo, yt, options=o).double().cpu().numpy()
+    want = oracle.backward_cone(w.verts, w.tets, y if C > 1 else y[:, 0], w.geom)
+    scale = oracle.backward_cone(w.verts, w.tets, np.abs(y) if C > 1 else np.abs(y[:, 0]), w.geom)
+    assert np.all(np.abs(got - want) <= TOL["f32"] * scale + 1e-30)
+    o32 = tp.make_options(channels=C, flags=tp.FLAG_ACC32)
+    got32 = tp.backward(c1.mesh, c1.geo, yt, options=o32).double().cpu().numpy()
+    assert np.all(np.abs(got32 - want) <= TOL["f32"] * scale + 1e-30)
+    bad = [dict(flags=tp.FLAG_ACC64, scatter=tp.SCATTER_SORT),   # sort sums runs itself
+           dict(flags=tp.FLAG_ACC32, scatter=tp.SCATTER_SORT),
+           dict(flags=tp.FLAG_ACC64, scatter=tp.SCATTER_WARP),   # atomic-scatter variant
+           dict(flags=tp.FLAG_ACC64 | tp.FLAG_ACC32)]
+    for kw in bad:
+        with pytest.raises(tp.TetprojError):
+            tp.backward(c1.mesh, c1.geo, yt, options=tp.make_options(channels=C, **kw))
