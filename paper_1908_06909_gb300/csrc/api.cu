@@ -70,10 +70,13 @@ struct tetproj_mesh {
     // workspace per [precision][channels==4]: tet-ordered operand / accumulator
     void *ws[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int64_t ws_bytes[2][2] = {{0, 0}, {0, 0}};
-    // deferral queue of the filtered walk (see kernels.cu)
+    // deferral queue of the filtered walk (see kernels.cu), and a second one
+    // with an auxiliary stream so that resume kernels overlap the next chunk
     QEntry *q = nullptr;
     unsigned long long *q_count = nullptr;
     int64_t q_cap = 0;
+    ResumeOverlap ov = {};
+    bool ov_ready = false;
     int64_t base_bytes = 0;
     SegPlan plan;
     SortWs sort;
@@ -175,8 +178,23 @@ static void sort_free(SortWs &w) {
     w = SortWs();
 }
 
+static void overlap_free(tetproj_mesh *m) {
+    if (!m->ov_ready) return;
+    cudaFree(m->ov.q2);
+    cudaFree(m->ov.q2_count);
+    cudaStreamDestroy(m->ov.aux);
+    for (int j = 0; j < 2; ++j) {
+        cudaEventDestroy(m->ov.ev_fast[j]);
+        cudaEventDestroy(m->ov.ev_res[j]);
+    }
+    cudaEventDestroy(m->ov.ev_start);
+    m->ov = ResumeOverlap{};
+    m->ov_ready = false;
+}
+
 static void mesh_free(tetproj_mesh *m) {
     if (!m) return;
+    overlap_free(m);
     plan_free(m->plan);
     sort_free(m->sort);
     cudaFree(m->rec32);
@@ -252,7 +270,8 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *m, tetproj_mesh_info *o
     o->nboundary = m->nb;
     o->nbvh_nodes = m->nnodes;
     o->nflipped = m->nflipped;
-    int64_t b = m->base_bytes + m->q_cap * (int64_t)sizeof(QEntry) + (m->q_count ? 8 : 0) +
+    int64_t b = m->base_bytes + m->q_cap * (int64_t)sizeof(QEntry) * (m->ov_ready ? 2 : 1) +
+                (m->q_count ? 8 : 0) +
                 m->plan.bytes + m->sort.bytes + m->rstar_bytes;
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) b += m->ws_bytes[i][j];
@@ -276,14 +295,39 @@ static tetproj_status ensure_ws(tetproj_mesh *m, int precision, int channels) {
 static tetproj_status ensure_queue(tetproj_mesh *m, int64_t nrays) {
     int64_t need = nrays < kQueueMax ? nrays : kQueueMax;
     need = ((need + 4095) / 4096) * 4096;
-    if (m->q_cap >= need && m->q_count) return TETPROJ_OK;
-    cudaFree(m->q);
-    m->q = nullptr;
-    m->q_cap = 0;
-    TP_CUDA(cudaMalloc((void **)&m->q, (size_t)need * sizeof(QEntry)));
-    if (!m->q_count) TP_CUDA(cudaMalloc((void **)&m->q_count, sizeof(unsigned long long)));
-    m->q_cap = need;
+    // the second queue and the auxiliary stream only pay off with several chunks
+    const bool want_ov = nrays > kQueueMax;
+    if (m->q_cap >= need && m->q_count && (!want_ov || m->ov_ready)) return TETPROJ_OK;
+    if (m->q_cap < need || !m->q_count) {
+        cudaDeviceSynchronize();  // the queues may be in use by earlier calls
+        overlap_free(m);
+        cudaFree(m->q);
+        m->q = nullptr;
+        m->q_cap = 0;
+        TP_CUDA(cudaMalloc((void **)&m->q, (size_t)need * sizeof(QEntry)));
+        if (!m->q_count) TP_CUDA(cudaMalloc((void **)&m->q_count, sizeof(unsigned long long)));
+        m->q_cap = need;
+    }
+    if (want_ov && !m->ov_ready) {
+        ResumeOverlap &o = m->ov;
+        int lo = 0, hi = 0;
+        TP_CUDA(cudaMalloc((void **)&o.q2, (size_t)m->q_cap * sizeof(QEntry)));
+        TP_CUDA(cudaMalloc((void **)&o.q2_count, sizeof(unsigned long long)));
+        TP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        TP_CUDA(cudaStreamCreateWithPriority(&o.aux, cudaStreamNonBlocking, hi));
+        for (int j = 0; j < 2; ++j) {
+            TP_CUDA(cudaEventCreateWithFlags(&o.ev_fast[j], cudaEventDisableTiming));
+            TP_CUDA(cudaEventCreateWithFlags(&o.ev_res[j], cudaEventDisableTiming));
+        }
+        TP_CUDA(cudaEventCreateWithFlags(&o.ev_start, cudaEventDisableTiming));
+        m->ov_ready = true;
+    }
     return TETPROJ_OK;
+}
+
+// the overlap resources when this mesh has them (calls of several chunks)
+static const ResumeOverlap *overlap_of(const tetproj_mesh *m) {
+    return m->ov_ready ? &m->ov : nullptr;
 }
 
 tetproj_status tetproj_mesh_reserve(tetproj_mesh *m, int32_t precision, int32_t channels) {
@@ -517,7 +561,7 @@ static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_opt
     TP_CUDA(launch_gather_perm(m->perm, m->nt, o.channels, f64, mu, ws, s));
     p.in = ws;
     p.out = out;
-    TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_FWD, s));
+    TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_FWD, s, overlap_of(m)));
     return TETPROJ_OK;
 }
 
@@ -547,7 +591,7 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
         TP_CUDA(cudaMemsetAsync(ws, 0, (size_t)m->ws_bytes[1][o.channels == 4], s));
         p.in = y;
         p.out = ws;
-        TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD64, s));
+        TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD64, s, overlap_of(m)));
         TP_CUDA(launch_scatter_perm_d2f(m->perm, m->nt, o.channels,
                                         reinterpret_cast<const double *>(ws),
                                         reinterpret_cast<float *>(mu_out), s));
@@ -561,7 +605,7 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
     TP_CUDA(cudaMemsetAsync(ws, 0, (size_t)m->ws_bytes[f64][o.channels == 4], s));
     p.in = y;
     p.out = ws;
-    TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s));
+    TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s, overlap_of(m)));
     TP_CUDA(launch_scatter_perm(m->perm, m->nt, o.channels, f64, ws, mu_out, s));
     return TETPROJ_OK;
 }

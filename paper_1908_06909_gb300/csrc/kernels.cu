@@ -1499,7 +1499,7 @@ __global__ void k_side(const double *S, const double *P, const double *p, const 
 
 template <int C, int MODE, int ENTRY = ENTRY_BVH>
 static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks, int threads,
-                               size_t smem, cudaStream_t stream) {
+                               size_t smem, cudaStream_t stream, const ResumeOverlap *ov) {
     KParams p = p0;
     if constexpr (ENTRY == ENTRY_BVH && MODE != MODE_BWD64 && MODE != MODE_ENTRY) {
         if (precision != TETPROJ_FILTERED) {
@@ -1515,6 +1515,38 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
     int64_t chunk = p.q_cap / threads;
     if (chunk < 1) return cudaErrorInvalidValue;
     const unsigned rgrid = (unsigned)(4 * sm_count());
+    if (ov && nblocks > chunk) {
+        // resume of chunk i on ov->aux, overlapping the fast walk of chunk i + 1;
+        // queue i % 2; chunk i + 2 reuses a queue after its resume has read it
+        cudaError_t e = cudaEventRecord(ov->ev_start, stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->ev_start, 0);
+        int used = 0;
+        for (int64_t b0 = 0, i = 0; b0 < nblocks && e == cudaSuccess; b0 += chunk, ++i) {
+            const int j = (int)(i & 1);
+            KParams pc = p;
+            pc.block_offset = b0;
+            pc.q = j ? ov->q2 : p.q;
+            pc.q_count = j ? ov->q2_count : p.q_count;
+            const int64_t nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
+            if (i >= 2) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
+            if (e == cudaSuccess) e = cudaMemsetAsync(pc.q_count, 0, sizeof(unsigned long long), stream);
+            if (e != cudaSuccess) break;
+            k_walk32<C, MODE, ENTRY><<<(unsigned)nb, threads, smem, stream>>>(pc);
+            note_launch();
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ov->ev_fast[j], stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->ev_fast[j], 0);
+            if (e != cudaSuccess) break;
+            k_resume32<C, MODE><<<rgrid, 128, smem, ov->aux>>>(pc);
+            note_launch();
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ov->ev_res[j], ov->aux);
+            used |= 1 << j;
+        }
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j)  // join the auxiliary stream
+            if (used & (1 << j)) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
+        return e;
+    }
     for (int64_t b0 = 0; b0 < nblocks; b0 += chunk) {
         int64_t nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
         p.block_offset = b0;
@@ -1602,7 +1634,7 @@ cudaError_t launch_block_offsets(const KParams &p, const int32_t *count, int32_t
 }
 
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, const ResumeOverlap *ov) {
     int64_t nblocks;
     int threads;
     if (p.src_kind == 0) {
@@ -1618,27 +1650,27 @@ cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
     if (mode == MODE_FWD) {
         if (p.entry == ENTRY_RSTAR) {  // the paper's entry structure: FP32, C = 1
             if (precision != TETPROJ_FILTERED || channels != 1) return cudaErrorInvalidValue;
-            return launch_mode<1, MODE_FWD, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream);
+            return launch_mode<1, MODE_FWD, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream, ov);
         }
-        return channels == 4 ? launch_mode<4, MODE_FWD>(p, precision, nblocks, threads, smem, stream)
-                             : launch_mode<1, MODE_FWD>(p, precision, nblocks, threads, smem, stream);
+        return channels == 4 ? launch_mode<4, MODE_FWD>(p, precision, nblocks, threads, smem, stream, ov)
+                             : launch_mode<1, MODE_FWD>(p, precision, nblocks, threads, smem, stream, ov);
     }
     if (mode == MODE_BWD) {
-        return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, nblocks, threads, smem, stream)
-                             : launch_mode<1, MODE_BWD>(p, precision, nblocks, threads, smem, stream);
+        return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, nblocks, threads, smem, stream, ov)
+                             : launch_mode<1, MODE_BWD>(p, precision, nblocks, threads, smem, stream, ov);
     }
     if (mode == MODE_BWD64) {
         if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;
-        return channels == 4 ? launch_mode<4, MODE_BWD64>(p, precision, nblocks, threads, smem, stream)
-                             : launch_mode<1, MODE_BWD64>(p, precision, nblocks, threads, smem, stream);
+        return channels == 4 ? launch_mode<4, MODE_BWD64>(p, precision, nblocks, threads, smem, stream, ov)
+                             : launch_mode<1, MODE_BWD64>(p, precision, nblocks, threads, smem, stream, ov);
     }
     if (mode == MODE_ENTRY) {
         if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;
         return p.entry == ENTRY_RSTAR
-                   ? launch_mode<1, MODE_ENTRY, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream)
-                   : launch_mode<1, MODE_ENTRY>(p, precision, nblocks, threads, smem, stream);
+                   ? launch_mode<1, MODE_ENTRY, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream, ov)
+                   : launch_mode<1, MODE_ENTRY>(p, precision, nblocks, threads, smem, stream, ov);
     }
-    return launch_mode<1, MODE_TRACE>(p, precision, nblocks, threads, smem, stream);
+    return launch_mode<1, MODE_TRACE>(p, precision, nblocks, threads, smem, stream, ov);
 }
 
 cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, int f64,

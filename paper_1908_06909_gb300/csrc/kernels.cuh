@@ -141,9 +141,20 @@ long long launch_count();
 // most 128 threads.
 cudaError_t launch_walk_mt(const KParams &p, int f64, int8_t *status, cudaStream_t stream);
 
+// Second deferral queue and an auxiliary stream: with them a filtered walk of
+// several chunks runs each chunk's resume kernel on `aux` while the next
+// chunk's fast kernel runs on the caller's stream (queues alternate; events
+// order each queue's reuse and join `aux` back before the call returns).
+struct ResumeOverlap {
+    QEntry *q2;
+    unsigned long long *q2_count;
+    cudaStream_t aux;
+    cudaEvent_t ev_fast[2], ev_res[2], ev_start;
+};
+
 // one launch of the walk; returns a cudaError_t
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
-                        cudaStream_t stream);
+                        cudaStream_t stream, const ResumeOverlap *ov = nullptr);
 cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, int f64,
                                const void *src_user, void *dst_h, cudaStream_t stream);
 cudaError_t launch_scatter_perm(const int32_t *perm, int64_t nt, int channels, int f64,
