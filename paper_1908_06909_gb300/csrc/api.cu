@@ -178,17 +178,40 @@ static void sort_free(SortWs &w) {
     w = SortWs();
 }
 
+// releases whatever part of `o` exists (also after a failed overlap_create)
+static void overlap_release(ResumeOverlap &o) {
+    cudaFree(o.q2);
+    cudaFree(o.q2_count);
+    if (o.aux) cudaStreamDestroy(o.aux);
+    for (int j = 0; j < 2; ++j) {
+        if (o.ev_fast[j]) cudaEventDestroy(o.ev_fast[j]);
+        if (o.ev_res[j]) cudaEventDestroy(o.ev_res[j]);
+    }
+    if (o.ev_start) cudaEventDestroy(o.ev_start);
+    o = ResumeOverlap{};
+}
+
+// second queue of `cap` entries, the auxiliary stream (highest priority, so
+// that a chunk's resume is not starved by the next chunk's walk) and events
+static cudaError_t overlap_create(ResumeOverlap &o, int64_t cap) {
+    o = ResumeOverlap{};
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaMalloc((void **)&o.q2, (size_t)cap * sizeof(QEntry));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&o.q2_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&o.aux, cudaStreamNonBlocking, hi);
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+        e = cudaEventCreateWithFlags(&o.ev_fast[j], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&o.ev_res[j], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&o.ev_start, cudaEventDisableTiming);
+    if (e != cudaSuccess) overlap_release(o);
+    return e;
+}
+
 static void overlap_free(tetproj_mesh *m) {
     if (!m->ov_ready) return;
-    cudaFree(m->ov.q2);
-    cudaFree(m->ov.q2_count);
-    cudaStreamDestroy(m->ov.aux);
-    for (int j = 0; j < 2; ++j) {
-        cudaEventDestroy(m->ov.ev_fast[j]);
-        cudaEventDestroy(m->ov.ev_res[j]);
-    }
-    cudaEventDestroy(m->ov.ev_start);
-    m->ov = ResumeOverlap{};
+    overlap_release(m->ov);
     m->ov_ready = false;
 }
 
@@ -309,17 +332,7 @@ static tetproj_status ensure_queue(tetproj_mesh *m, int64_t nrays) {
         m->q_cap = need;
     }
     if (want_ov && !m->ov_ready) {
-        ResumeOverlap &o = m->ov;
-        int lo = 0, hi = 0;
-        TP_CUDA(cudaMalloc((void **)&o.q2, (size_t)m->q_cap * sizeof(QEntry)));
-        TP_CUDA(cudaMalloc((void **)&o.q2_count, sizeof(unsigned long long)));
-        TP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        TP_CUDA(cudaStreamCreateWithPriority(&o.aux, cudaStreamNonBlocking, hi));
-        for (int j = 0; j < 2; ++j) {
-            TP_CUDA(cudaEventCreateWithFlags(&o.ev_fast[j], cudaEventDisableTiming));
-            TP_CUDA(cudaEventCreateWithFlags(&o.ev_res[j], cudaEventDisableTiming));
-        }
-        TP_CUDA(cudaEventCreateWithFlags(&o.ev_start, cudaEventDisableTiming));
+        TP_CUDA(overlap_create(m->ov, m->q_cap));
         m->ov_ready = true;
     }
     return TETPROJ_OK;
@@ -978,6 +991,8 @@ struct tetproj_batch {
     unsigned grid_fwd = 0, grid_bwd = 0, rgrid = 0;
     bool acc64 = false;  // C = 1: FP64 accumulators (the per-problem scatter choice is for C = 4)
     bool bound = false;
+    ResumeOverlap ov{};  // second queue + auxiliary stream when there are several rounds
+    bool ov_ready = false;
 };
 
 static void batch_free(tetproj_batch *b) {
@@ -990,6 +1005,7 @@ static void batch_free(tetproj_batch *b) {
     cudaFree(b->q);
     cudaFree(b->q_count);
     cudaFree(b->item_counter);
+    if (b->ov_ready) overlap_release(b->ov);
     delete b;
 }
 
@@ -1057,6 +1073,11 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_item_begin, b->item_begin.data(), sizeof(int64_t) * (n + 1),
                        cudaMemcpyHostToDevice);
+    // several rounds: round r's resume overlaps round r + 1's walk
+    if (e == cudaSuccess && total_rays > kQueueMax) {
+        e = overlap_create(b->ov, need);
+        b->ov_ready = e == cudaSuccess;
+    }
     if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
     b->q_cap = need;
     // launch shapes are fixed here so that forward/backward issue stream work only
@@ -1118,7 +1139,7 @@ extern "C" tetproj_status tetproj_batch_forward(tetproj_batch *b, void *stream) 
                                    b->ws_in[k], s));
     TP_CUDA(launch_batch(b->d_fwd, b->d_item_begin, b->n, b->item_begin.back(),
                          b->channels, MODE_FWD, b->grid_fwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
-                         b->smem_nodes, s));
+                         b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr));
     return TETPROJ_OK;
 }
 
@@ -1131,7 +1152,7 @@ extern "C" tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream)
         TP_CUDA(cudaMemsetAsync(b->ws_acc[k], 0, (size_t)(b->acc64 ? 2 : 1) * b->ws_bytes[k], s));
     TP_CUDA(launch_batch(b->d_bwd, b->d_item_begin, b->n, b->item_begin.back(),
                          b->channels, b->acc64 ? MODE_BWD64 : MODE_BWD, b->grid_bwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
-                         b->smem_nodes, s));
+                         b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr));
     for (int k = 0; k < b->n; ++k) {
         if (b->acc64)
             TP_CUDA(launch_scatter_perm_d2f(b->meshes[k]->perm, b->meshes[k]->nt, b->channels,

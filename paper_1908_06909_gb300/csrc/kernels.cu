@@ -1058,7 +1058,7 @@ template <int C, int MODE>
 __global__ void __launch_bounds__(TP_BATCH_THREADS, TP_BATCH_MIN_BLOCKS)
     k_batch32(const BatchProblem *__restrict__ probs, const int64_t *__restrict__ item_begin,
               int nprob, int64_t round_begin, int64_t round_end, unsigned *chunk_counter,
-              int nsm_max) {
+              int nsm_max, QEntry *q, unsigned long long *q_count) {
     extern __shared__ float4 smem[];
     __shared__ unsigned s_ticket;
     __shared__ long long s_base[TP_BATCH_RING];
@@ -1128,7 +1128,11 @@ __global__ void __launch_bounds__(TP_BATCH_THREADS, TP_BATCH_MIN_BLOCKS)
                 reinterpret_cast<const unsigned long long *>(&probs[k].p.m.bvh)));
             for (int i = lane; i < nsm * 4; i += 32) dst[kBatchParamVec + i] = __ldg(bv + i);
             __syncwarp();
-            if (lane == 0) sp->smem_nodes = nsm;
+            if (lane == 0) {
+                sp->smem_nodes = nsm;
+                sp->q = q;  // this round's deferral queue (rounds may alternate queues)
+                sp->q_count = q_count;
+            }
             __syncwarp();
             cur = k;
         }
@@ -1197,17 +1201,49 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
                                      int nprob, int64_t nitems, unsigned grid,
                                      unsigned rgrid, QEntry *q, unsigned long long *q_count,
                                      int64_t q_cap, unsigned *item_counter,
-                                     int smem_nodes, cudaStream_t stream) {
+                                     int smem_nodes, cudaStream_t stream,
+                                     const ResumeOverlap *ov) {
     // rounds of whole chunks of warp items (32 rays each), at most q_cap rays
     const int64_t round_items = (q_cap / (32 * kBatchChunk)) * kBatchChunk;
     if (round_items < 1) return cudaErrorInvalidValue;
+    if (ov && nitems > round_items) {
+        // resume of round r on ov->aux while round r + 1 runs (queues alternate)
+        cudaError_t e = cudaEventRecord(ov->ev_start, stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->ev_start, 0);
+        int used = 0;
+        for (int64_t r0 = 0, i = 0; r0 < nitems && e == cudaSuccess; r0 += round_items, ++i) {
+            const int j = (int)(i & 1);
+            QEntry *qj = j ? ov->q2 : q;
+            unsigned long long *cj = j ? ov->q2_count : q_count;
+            const int64_t r1 = nitems - r0 < round_items ? nitems : r0 + round_items;
+            if (i >= 2) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
+            if (e == cudaSuccess) e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(cj, 0, sizeof(unsigned long long), stream);
+            if (e != cudaSuccess) break;
+            k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
+                probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, qj, cj);
+            note_launch();
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ov->ev_fast[j], stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->ev_fast[j], 0);
+            if (e != cudaSuccess) break;
+            k_batch_resume32<C, MODE><<<rgrid, 128, 0, ov->aux>>>(probs, qj, cj, q_cap);
+            note_launch();
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ov->ev_res[j], ov->aux);
+            used |= 1 << j;
+        }
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+            if (used & (1 << j)) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
+        return e;
+    }
     for (int64_t r0 = 0; r0 < nitems; r0 += round_items) {
         const int64_t r1 = nitems - r0 < round_items ? nitems : r0 + round_items;
         cudaError_t e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(q_count, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
         k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
-            probs, item_begin, nprob, r0, r1, item_counter, smem_nodes);
+            probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, q, q_count);
         note_launch();
         k_batch_resume32<C, MODE><<<rgrid, 128, 0, stream>>>(probs, q, q_count, q_cap);
         note_launch();
@@ -1220,11 +1256,12 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
 cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, int nprob,
                          int64_t nitems, int channels, int mode, unsigned grid,
                          unsigned rgrid, QEntry *q, unsigned long long *q_count, int64_t q_cap,
-                         unsigned *item_counter, int smem_nodes, cudaStream_t stream) {
+                         unsigned *item_counter, int smem_nodes, cudaStream_t stream,
+                         const ResumeOverlap *ov) {
     if (nitems <= 0) return cudaSuccess;
     if (grid < 1 || rgrid < 1) return cudaErrorInvalidValue;
 #define TP_BATCH_ARGS probs, item_begin, nprob, nitems, grid, rgrid, q, q_count, q_cap, \
-                      item_counter, smem_nodes, stream
+                      item_counter, smem_nodes, stream, ov
     if (mode == MODE_FWD)
         return channels == 4 ? launch_batch_mode<4, MODE_FWD>(TP_BATCH_ARGS)
                              : launch_batch_mode<1, MODE_FWD>(TP_BATCH_ARGS);

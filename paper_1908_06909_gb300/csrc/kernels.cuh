@@ -90,11 +90,15 @@ constexpr int kBatchChunk = 8;
 // item_begin[k] a multiple of kBatchChunk), in
 // rounds of at most q_cap rays: per round one persistent work-queue launch of
 // `grid` CTAs and one resume launch of `rgrid` CTAs.  `smem_nodes`: BVH nodes
-// staged per warp.  Only stream operations (graph-capturable).
+// staged per warp.  With `ov` (its q2 holding q_cap entries) and more than one
+// round, round r's resume runs on ov->aux beside round r + 1's walk.  Only
+// stream and event operations (graph-capturable).
+struct ResumeOverlap;
 cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, int nprob,
                          int64_t nitems, int channels, int mode, unsigned grid, unsigned rgrid,
                          QEntry *q, unsigned long long *q_count, int64_t q_cap,
-                         unsigned *item_counter, int smem_nodes, cudaStream_t stream);
+                         unsigned *item_counter, int smem_nodes, cudaStream_t stream,
+                         const ResumeOverlap *ov = nullptr);
 // Persistent grid for the batched walk: resident CTAs per SM x SM count.
 cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid);
 int device_sm_count();
