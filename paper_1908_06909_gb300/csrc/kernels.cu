@@ -542,9 +542,12 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
         bool defer_now = false;
         float len = 0.f;
         if (alive) {
-            const float4 *g = reinterpret_cast<const float4 *>(rec + h);
-            float4 q0 = __ldg(g), q1 = __ldg(g + 1), q2 = __ldg(g + 2);
-            int4 adj = __ldg(reinterpret_cast<const int4 *>(g + 3));
+            // n = v_f and face f's canonical triple (a, b, c), loaded by index;
+            // the .w of a, b, c are the neighbours across the faces opposite them
+            const float4 *g = rec[h].v;
+            const int tri = (FACE_TRIPLES >> (6 * f)) & 63;
+            const float4 vn = __ldg(g + f), va = __ldg(g + (tri & 3)),
+                         vb = __ldg(g + ((tri >> 2) & 3)), vc = __ldg(g + (tri >> 4));
             float muv[C];
             if (MODE == MODE_FWD) {
                 if (C == 4) {
@@ -554,25 +557,14 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                     muv[0] = __ldg(mu + h);
                 }
             }
-            // local vertices v0 = q0.xyz, v1 = (q0.w, q1.xy), v2 = (q1.zw, q2.x),
-            // v3 = q2.yzw; n = v_f and the canonical face triple, branch-free
-            const bool f0 = f == 0, f1 = f == 1, f2 = f == 2;
-            f3 n = {f0 ? q0.x : (f1 ? q0.w : (f2 ? q1.z : q2.y)),
-                    f0 ? q0.y : (f1 ? q1.x : (f2 ? q1.w : q2.z)),
-                    f0 ? q0.z : (f1 ? q1.y : (f2 ? q2.x : q2.w))};
-            f3 a = {f0 ? q0.w : q0.x, f0 ? q1.x : q0.y, f0 ? q1.y : q0.z};          // v1 | v0
-            f3 b = {f0 ? q2.y : (f1 ? q1.z : (f2 ? q2.y : q0.w)),                   // v3|v2|v3|v1
-                    f0 ? q2.z : (f1 ? q1.w : (f2 ? q2.z : q1.x)),
-                    f0 ? q2.w : (f1 ? q2.x : (f2 ? q2.w : q1.y))};
-            f3 c = {(f0 || f == 3) ? q1.z : (f1 ? q2.y : q0.w),                     // v2|v3|v1|v2
-                    (f0 || f == 3) ? q1.w : (f1 ? q2.z : q1.x),
-                    (f0 || f == 3) ? q2.x : (f1 ? q2.w : q1.y)};
+            const f3 n = {vn.x, vn.y, vn.z}, a = {va.x, va.y, va.z}, b = {vb.x, vb.y, vb.z},
+                     c = {vc.x, vc.y, vc.z};
             Filt32Vert Vn = filt32_vert(fr, n);
             f3 ea = sub(a, n), eb = sub(b, n), ec = sub(c, n);
             float sa, sb, sc, ba, bb, bc;
-            int ga = filt32_side_e(Vn, a, ea, sa, ba);
-            int gb = filt32_side_e(Vn, b, eb, sb, bb);
-            int gc = filt32_side_e(Vn, c, ec, sc, bc);
+            int ga = filt32_side_e(Vn, ea, sa, ba);
+            int gb = filt32_side_e(Vn, eb, sb, bb);
+            int gc = filt32_side_e(Vn, ec, sc, bc);
             int x = -1;
             f3 Xout = Xin;
             bool fast = (ga != 0) & (gb != 0) & (gc != 0);
@@ -613,10 +605,8 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 did = false;
             } else {
                 ++cnt.segs;
-                int ia, ib, ic;
-                face_triple(f, ia, ib, ic);
-                int loc = x == 0 ? ia : (x == 1 ? ib : ic);
-                int nxt = sel4(adj, loc);
+                // the exit face is opposite a (x = 0), b (1) or c (2)
+                const int nxt = __float_as_int(x == 0 ? va.w : (x == 1 ? vb.w : vc.w));
                 len = dotf(sub(Xout, Xin), fr.d) * il;
                 if (clip0) {  // only the part with t >= 0 counts
                     float dd = dotf(fr.d, fr.d);
@@ -1436,7 +1426,7 @@ __global__ void __launch_bounds__(128) k_walk_mt(const __grid_constant__ KParams
         int fout = fh[i2];
         if (t2 == t1 && fout == fin) fout = fh[i1];
         sum = sum + (l * (t2 - t1)) * __ldg(mu + h);
-        const int nx = sel4(__ldg(reinterpret_cast<const int4 *>(&p.m.rec32[h].adj)), fout);
+        const int nx = __float_as_int(__ldg(&p.m.rec32[h].v[fout].w));
         if (nx < 0) break;
         h = nx >> 2;
         fin = nx & 3;

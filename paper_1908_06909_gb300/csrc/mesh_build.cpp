@@ -371,10 +371,8 @@ tetproj_status build_host_mesh(const double *V, int64_t nv, const int32_t *T, in
         r.adj = make_int4(a[0], a[1], a[2], a[3]);
         r.extra = make_int4((int32_t)t, 0, 0, 0);
         TetRec32 &s = M.rec32[h];
-        s.q0 = make_float4(c[0], c[1], c[2], c[3]);
-        s.q1 = make_float4(c[4], c[5], c[6], c[7]);
-        s.q2 = make_float4(c[8], c[9], c[10], c[11]);
-        s.adj = r.adj;
+        for (int k = 0; k < 4; ++k)
+            s.v[k] = make_float4(c[3 * k], c[3 * k + 1], c[3 * k + 2], int_bits_as_float(a[k]));
     }
 
     // boundary faces + BVH
@@ -431,15 +429,12 @@ tetproj_status build_host_mesh(const double *V, int64_t nv, const int32_t *T, in
     M.bfaces.resize(M.nb);
     for (int64_t q = 0; q < M.nb; ++q) {
         const TetRec32 &s = M.rec32[F[q].h];
-        const float c[12] = {s.q0.x, s.q0.y, s.q0.z, s.q0.w, s.q1.x, s.q1.y,
-                             s.q1.z, s.q1.w, s.q2.x, s.q2.y, s.q2.z, s.q2.w};
         int a, b, cc;
         face_triple(F[q].f, a, b, cc);
         BFace32 &o = M.bfaces[q];
-        o.a = make_float4(c[3 * a], c[3 * a + 1], c[3 * a + 2],
-                          int_bits_as_float((F[q].h << 2) | F[q].f));
-        o.b = make_float4(c[3 * b], c[3 * b + 1], c[3 * b + 2], 0.f);
-        o.c = make_float4(c[3 * cc], c[3 * cc + 1], c[3 * cc + 2], 0.f);
+        o.a = make_float4(s.v[a].x, s.v[a].y, s.v[a].z, int_bits_as_float((F[q].h << 2) | F[q].f));
+        o.b = make_float4(s.v[b].x, s.v[b].y, s.v[b].z, 0.f);
+        o.c = make_float4(s.v[cc].x, s.v[cc].y, s.v[cc].z, 0.f);
     }
     return TETPROJ_OK;
 }

@@ -109,12 +109,19 @@ TP_HD double dotd(const d3 &a, const d3 &b) { return fma(a.x, b.x, fma(a.y, b.y,
 // |w| (small when n is near the ray) and the 1e-6 (X + Y) guard in Z2.  The
 // constant is 2^-24 * 1.0234: it covers the O(u^2) terms and the rounding of
 // the bound itself (non-negative terms, ~10 operations).
+//   Per edge the walk evaluates the bound in the folded form
+//     u [ Z . |e32| + c ],   Z = Z1 + 1.01 Z2,   c = 2.02 Z2 . |n|,
+// which is never below the one above: |k| <= |n| + |k - n| and
+// |k - n| <= (1 + 1.01u) |e32| (e32 = fl(k - n)), so |k| + |n| <= 2|n| +
+// (1 + 1.01u)|e32|; the 1.01 / 2.02 factors also cover the roundings of Z and
+// c.  Z and c are per vertex, so an edge costs one dot product and one FMA.
 struct Filt32Ray {
     f3 O, d;     // midpoint and direction, rounded to FP32
     float Oext;  // 1e-8 max_i(|S_i| + |P_i|): covers fl64 rounding of (S + P)/2
 };
 struct Filt32Vert {
-    f3 n, nabs, w, Z1, Z2;
+    f3 n, w, Z;
+    float c;
 };
 #define TP_FILT32_U 6.1e-8f
 #define TP_FILT32_TINY 1e-30f
@@ -131,43 +138,39 @@ TP_HD Filt32Ray filt32_ray(const d3 &S, const d3 &P) {
 TP_HD Filt32Vert filt32_vert(const Filt32Ray &r, const f3 &n) {
     Filt32Vert v;
     v.n = n;
-    v.nabs = fabs3(n);
+    const f3 nabs = fabs3(n);
     f3 a = sub(n, r.O);
     v.w = crossf(r.d, a);
     f3 aabs = fabs3(a), dabs = fabs3(r.d), Oabs = fabs3(r.O);
     f3 X = abscrossf(dabs, aabs);
-    f3 Ma = {fmaf(1.01f, v.nabs.x + Oabs.x, aabs.x + r.Oext),
-             fmaf(1.01f, v.nabs.y + Oabs.y, aabs.y + r.Oext),
-             fmaf(1.01f, v.nabs.z + Oabs.z, aabs.z + r.Oext)};
+    f3 Ma = {fmaf(1.01f, nabs.x + Oabs.x, aabs.x + r.Oext),
+             fmaf(1.01f, nabs.y + Oabs.y, aabs.y + r.Oext),
+             fmaf(1.01f, nabs.z + Oabs.z, aabs.z + r.Oext)};
     f3 Y = abscrossf(dabs, Ma);
     f3 wa = fabs3(v.w);
-    v.Z1 = {fmaf(3.02f, X.x, fmaf(4.01f, wa.x, Y.x)), fmaf(3.02f, X.y, fmaf(4.01f, wa.y, Y.y)),
-            fmaf(3.02f, X.z, fmaf(4.01f, wa.z, Y.z))};
-    v.Z2 = {fmaf(1.01f, wa.x, 1e-6f * (X.x + Y.x)), fmaf(1.01f, wa.y, 1e-6f * (X.y + Y.y)),
-            fmaf(1.01f, wa.z, 1e-6f * (X.z + Y.z))};
+    const f3 Z1 = {fmaf(3.02f, X.x, fmaf(4.01f, wa.x, Y.x)),
+                   fmaf(3.02f, X.y, fmaf(4.01f, wa.y, Y.y)),
+                   fmaf(3.02f, X.z, fmaf(4.01f, wa.z, Y.z))};
+    const f3 Z2 = {fmaf(1.01f, wa.x, 1e-6f * (X.x + Y.x)), fmaf(1.01f, wa.y, 1e-6f * (X.y + Y.y)),
+                   fmaf(1.01f, wa.z, 1e-6f * (X.z + Y.z))};
+    v.Z = {fmaf(1.01f, Z2.x, Z1.x), fmaf(1.01f, Z2.y, Z1.y), fmaf(1.01f, Z2.z, Z1.z)};
+    v.c = 2.02f * dotf(Z2, nabs);
     return v;
 }
-// side(n->k): value, its error bound, and the certain sign (+1/-1) or 0 when
-// |value| does not exceed the bound
-TP_HD int filt32_side(const Filt32Vert &v, const f3 &k, float &val, float &B) {
-    f3 e = sub(k, v.n);
+// side(n->k) with e = k - n already computed: value, its error bound, and the
+// certain sign (+1/-1) or 0 when |value| does not exceed the bound
+TP_HD int filt32_side_e(const Filt32Vert &v, const f3 &e, float &val, float &B) {
     val = dotf(v.w, e);
-    f3 kabs = fabs3(k);
-    f3 kn = {kabs.x + v.nabs.x, kabs.y + v.nabs.y, kabs.z + v.nabs.z};
-    B = fmaf(TP_FILT32_U, dotf(v.Z1, fabs3(e)) + dotf(v.Z2, kn), TP_FILT32_TINY);
+    const float m = fmaf(v.Z.x, fabsf(e.x), fmaf(v.Z.y, fabsf(e.y), fmaf(v.Z.z, fabsf(e.z), v.c)));
+    B = fmaf(TP_FILT32_U, m, TP_FILT32_TINY);
     return (val > B) - (val < -B);
+}
+TP_HD int filt32_side(const Filt32Vert &v, const f3 &k, float &val, float &B) {
+    return filt32_side_e(v, sub(k, v.n), val, B);
 }
 TP_HD int filt32_side(const Filt32Vert &v, const f3 &k, float &val) {
     float B;
     return filt32_side(v, k, val, B);
-}
-// the same with e = k - n already computed (the walk reuses it for the face normal)
-TP_HD int filt32_side_e(const Filt32Vert &v, const f3 &k, const f3 &e, float &val, float &B) {
-    val = dotf(v.w, e);
-    f3 kabs = fabs3(k);
-    f3 kn = {kabs.x + v.nabs.x, kabs.y + v.nabs.y, kabs.z + v.nabs.z};
-    B = fmaf(TP_FILT32_U, dotf(v.Z1, fabs3(e)) + dotf(v.Z2, kn), TP_FILT32_TINY);
-    return (val > B) - (val < -B);
 }
 
 // ------------------------------------------------------------------ FP64 stage

@@ -24,11 +24,12 @@
 
 namespace tp {
 
+// v[k].xyz: local vertex k in FP32; v[k].w: int bits of the neighbour across
+// the face opposite vertex k, (h << 2) | f (f: that face's index in the
+// neighbour), or -1 on the boundary.  A walk step loads v[f] and the face
+// triple of face f by index, so no per-coordinate selection is needed.
 struct __align__(16) TetRec32 {
-    float4 q0;  // v0.x v0.y v0.z v1.x
-    float4 q1;  // v1.y v1.z v2.x v2.y
-    float4 q2;  // v2.z v3.x v3.y v3.z
-    int4 adj;
+    float4 v[4];
 };
 static_assert(sizeof(TetRec32) == 64, "TetRec32 must be 64 bytes");
 
@@ -106,5 +107,12 @@ TP_HD void face_triple(int f, int &a, int &b, int &c) {
     b = (f == 0) ? 3 : (f == 1 ? 2 : (f == 2 ? 3 : 1));
     c = (f == 0) ? 2 : (f == 1 ? 3 : (f == 2 ? 1 : 2));
 }
+
+// The same table packed 2 bits per index: face f's triple is
+// (FACE_TRIPLES >> 6f) & 63 = a | b << 2 | c << 4.
+constexpr int kFaceTriple0 = 1 | 3 << 2 | 2 << 4, kFaceTriple1 = 0 | 2 << 2 | 3 << 4,
+              kFaceTriple2 = 0 | 3 << 2 | 1 << 4, kFaceTriple3 = 0 | 1 << 2 | 2 << 4;
+constexpr int FACE_TRIPLES = kFaceTriple0 | kFaceTriple1 << 6 | kFaceTriple2 << 12 |
+                             kFaceTriple3 << 18;
 
 }  // namespace tp
