@@ -448,7 +448,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
     if (valid) {
         d3 S, P;
         load_ray(p, ray, S, P);
-        fr = filt32_ray(S, P);
+        fr = filt32_ray(S, P, p.m.radius);
         il = rsqrtf(dotf(fr.d, fr.d));
         const bool from_entry = !ROBUST || qe->fs < 0;
         if (!ROBUST) cnt.rays = 1;
@@ -580,7 +580,9 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 // the ray nearly lies in the exit face: place the crossing exactly
                 fast = x < 0 || wy + wz >= (float)TP_WEIGHT_MARGIN * bw;
                 if (fast) {
-                    float iw = __frcp_rn(W);
+                    // approximate reciprocal (2 ulp): W only scales the crossing
+                    // offset, whose weights carry far larger certified errors
+                    float iw = __fdividef(1.0f, W);
                     Xout = f3axpy(wz * iw, ez, f3axpy(wy * iw, ey, n));
                 }
             }

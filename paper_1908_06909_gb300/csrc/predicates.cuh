@@ -109,15 +109,24 @@ TP_HD double dotd(const d3 &a, const d3 &b) { return fma(a.x, b.x, fma(a.y, b.y,
 // |w| (small when n is near the ray) and the 1e-6 (X + Y) guard in Z2.  The
 // constant is 2^-24 * 1.0234: it covers the O(u^2) terms and the rounding of
 // the bound itself (non-negative terms, ~10 operations).
-//   Per edge the walk evaluates the bound in the folded form
-//     u [ Z . |e32| + c ],   Z = Z1 + 1.01 Z2,   c = 2.02 Z2 . |n|,
-// which is never below the one above: |k| <= |n| + |k - n| and
-// |k - n| <= (1 + 1.01u) |e32| (e32 = fl(k - n)), so |k| + |n| <= 2|n| +
-// (1 + 1.01u)|e32|; the 1.01 / 2.02 factors also cover the roundings of Z and
-// c.  Z and c are per vertex, so an edge costs one dot product and one FMA.
+//   Per edge the walk evaluates a bound that is never below the one above,
+// in a folded form with per-vertex Z, c and a per-ray guard G:
+//     u [ Z . |e32| + c ],   Z = 3.03 X + 5.04 |w| + Y',   c = 2.05 |w| . |n| + G,
+// with Y' = |d| x Ma' and Ma' = 1.0101 (|n| + |O|) + 1.00002 |a| +
+// 1.00002e-8 max_i(|S_i| + |P_i|) >= 1.00002 Ma.  Why it dominates: |k| <=
+// |n| + |k - n| and |k - n| <= (1 + 1.01u)|e32| (e32 = fl(k - n)), so
+// Z2 . (|k| + |n|) <= 1.01 Z2 . |e32| + 2.02 Z2 . |n|; expanding Z1 + 1.01 Z2
+// gives 3.02 X + 5.0301 |w| + Y plus 1.01e-6 (X + Y), which 3.03 X and Y'
+// cover; 2.02 Z2 . |n| = 2.0402 |w| . |n| + 2.02e-6 (X + Y) . |n|, and the
+// second term is at most G = 2.03e-6 R sum_i (Xm + Ym)_i, where R >= every
+// |n32_i| of the mesh, Xm = |d| x A and Ym = |d| x (A + 1.01 (R + |O|) +
+// Oext) with A = 1.001 (R + |O|) >= |a32| (so X <= Xm, Y <= Ym).  The factors'
+// slack (>= 0.2%) covers the roundings of Z, c and G.  Per vertex this costs
+// about 50 operations, per edge one dot product and one FMA.
 struct Filt32Ray {
     f3 O, d;     // midpoint and direction, rounded to FP32
-    float Oext;  // 1e-8 max_i(|S_i| + |P_i|): covers fl64 rounding of (S + P)/2
+    float Oext;  // 1.00002e-8 max_i(|S_i| + |P_i|): covers fl64 rounding of (S + P)/2
+    float G;     // guard of the folded bound (see above)
 };
 struct Filt32Vert {
     f3 n, w, Z;
@@ -126,35 +135,38 @@ struct Filt32Vert {
 #define TP_FILT32_U 6.1e-8f
 #define TP_FILT32_TINY 1e-30f
 
-TP_HD Filt32Ray filt32_ray(const d3 &S, const d3 &P) {
+// R: an upper bound of |coordinate| over every FP32 vertex the ray is tested
+// against (the mesh radius, rounded up)
+TP_HD Filt32Ray filt32_ray(const d3 &S, const d3 &P, float R) {
     Filt32Ray r;
     d3 O = {(S.x + P.x) * 0.5, (S.y + P.y) * 0.5, (S.z + P.z) * 0.5};
     r.O = tof(O);
     r.d = tof(sub(P, S));
     double e = fmax(fmax(fabs(S.x) + fabs(P.x), fabs(S.y) + fabs(P.y)), fabs(S.z) + fabs(P.z));
-    r.Oext = 1e-8f * (float)e;
+    r.Oext = 1.00002e-8f * (float)e;
+    const f3 Oabs = fabs3(r.O), dabs = fabs3(r.d);
+    const f3 A = {1.001f * (R + Oabs.x), 1.001f * (R + Oabs.y), 1.001f * (R + Oabs.z)};
+    const f3 M = {fmaf(2.011f, R + Oabs.x, r.Oext), fmaf(2.011f, R + Oabs.y, r.Oext),
+                  fmaf(2.011f, R + Oabs.z, r.Oext)};
+    const f3 Xm = abscrossf(dabs, A), Ym = abscrossf(dabs, M);
+    r.G = 2.03e-6f * R * ((Xm.x + Ym.x) + (Xm.y + Ym.y) + (Xm.z + Ym.z));
     return r;
 }
 TP_HD Filt32Vert filt32_vert(const Filt32Ray &r, const f3 &n) {
     Filt32Vert v;
     v.n = n;
-    const f3 nabs = fabs3(n);
-    f3 a = sub(n, r.O);
+    const f3 a = sub(n, r.O);
     v.w = crossf(r.d, a);
-    f3 aabs = fabs3(a), dabs = fabs3(r.d), Oabs = fabs3(r.O);
-    f3 X = abscrossf(dabs, aabs);
-    f3 Ma = {fmaf(1.01f, nabs.x + Oabs.x, aabs.x + r.Oext),
-             fmaf(1.01f, nabs.y + Oabs.y, aabs.y + r.Oext),
-             fmaf(1.01f, nabs.z + Oabs.z, aabs.z + r.Oext)};
-    f3 Y = abscrossf(dabs, Ma);
-    f3 wa = fabs3(v.w);
-    const f3 Z1 = {fmaf(3.02f, X.x, fmaf(4.01f, wa.x, Y.x)),
-                   fmaf(3.02f, X.y, fmaf(4.01f, wa.y, Y.y)),
-                   fmaf(3.02f, X.z, fmaf(4.01f, wa.z, Y.z))};
-    const f3 Z2 = {fmaf(1.01f, wa.x, 1e-6f * (X.x + Y.x)), fmaf(1.01f, wa.y, 1e-6f * (X.y + Y.y)),
-                   fmaf(1.01f, wa.z, 1e-6f * (X.z + Y.z))};
-    v.Z = {fmaf(1.01f, Z2.x, Z1.x), fmaf(1.01f, Z2.y, Z1.y), fmaf(1.01f, Z2.z, Z1.z)};
-    v.c = 2.02f * dotf(Z2, nabs);
+    const f3 nabs = fabs3(n), aabs = fabs3(a), dabs = fabs3(r.d), Oabs = fabs3(r.O);
+    const f3 X = abscrossf(dabs, aabs);
+    const f3 Ma = {fmaf(1.0101f, nabs.x + Oabs.x, fmaf(1.00002f, aabs.x, r.Oext)),
+                   fmaf(1.0101f, nabs.y + Oabs.y, fmaf(1.00002f, aabs.y, r.Oext)),
+                   fmaf(1.0101f, nabs.z + Oabs.z, fmaf(1.00002f, aabs.z, r.Oext))};
+    const f3 Y = abscrossf(dabs, Ma);
+    const f3 wa = fabs3(v.w);
+    v.Z = {fmaf(3.03f, X.x, fmaf(5.04f, wa.x, Y.x)), fmaf(3.03f, X.y, fmaf(5.04f, wa.y, Y.y)),
+           fmaf(3.03f, X.z, fmaf(5.04f, wa.z, Y.z))};
+    v.c = fmaf(2.05f, dotf(wa, nabs), r.G);
     return v;
 }
 // side(n->k) with e = k - n already computed: value, its error bound, and the
@@ -376,10 +388,13 @@ TP_HDN int side_sign_robust64(const d3 S, const d3 P, const d3 p, const d3 q, in
 
 // Full cascade from FP64 inputs (used by the validation entry points).
 TP_HDN int side_sign_cascade(const d3 S, const d3 P, const d3 p, const d3 q, int *stage) {
-    Filt32Ray r = filt32_ray(S, P);
-    Filt32Vert v = filt32_vert(r, tof(p));
+    const f3 p32 = tof(p), q32 = tof(q);
+    const float R = fmaxf(fmaxf(fmaxf(fabsf(p32.x), fabsf(p32.y)), fabsf(p32.z)),
+                          fmaxf(fmaxf(fabsf(q32.x), fabsf(q32.y)), fabsf(q32.z)));
+    Filt32Ray r = filt32_ray(S, P, R);
+    Filt32Vert v = filt32_vert(r, p32);
     float val;
-    int s = filt32_side(v, tof(q), val);
+    int s = filt32_side(v, q32, val);
     if (s != 0) { *stage = 0; return s; }
     return side_sign_robust64(S, P, p, q, stage);
 }

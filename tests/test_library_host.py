@@ -182,6 +182,28 @@ def test_fp32_filter_sound_near_threshold(tp):
         assert sign[k] == exact.side_sign_int(S[k], P[k], p[k], q[k]), k
 
 
+def test_fp32_filter_sound_far_from_origin(tp):
+    """The same near-threshold packing for a mesh far from the origin, where
+    the FP32 rounding of the vertex coordinates (the |w| . |n| and guard terms
+    of the bound) dominates the error: every FP32-certain answer is exact."""
+    rng = np.random.default_rng(29)
+    n = 40000
+    centre = np.array([3.0e3, -2.0e3, 1.0e3])
+    p = centre + rng.uniform(-1, 1, size=(n, 3))
+    L = 10.0 ** rng.uniform(-3.5, -0.5, size=(n, 1))
+    q = p + rng.normal(size=(n, 3)) * L
+    X = p + rng.uniform(-0.2, 1.2, size=(n, 1)) * (q - p)
+    ang = rng.uniform(0, 2 * np.pi, size=n)
+    S = centre + np.stack([4 * np.cos(ang), 4 * np.sin(ang), rng.uniform(-0.3, 0.3, n)], axis=1)
+    off = rng.normal(size=(n, 3))
+    P = S + 2.0 * (X - S) + off * L * 10.0 ** rng.uniform(-6, 0, size=(n, 1))
+    sign, stage = tp.side_signs_host(S, P, p, q)
+    fp32 = np.nonzero(stage == 0)[0]
+    assert fp32.size > 2000 and (stage != 0).sum() > 2000
+    for k in fp32:
+        assert sign[k] == exact.side_sign_int(S[k], P[k], p[k], q[k]), k
+
+
 def test_batch_argument_errors(tp):
     """Batch entry points reject bad arguments before touching the device."""
     import ctypes as C
