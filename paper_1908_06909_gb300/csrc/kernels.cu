@@ -136,12 +136,27 @@ __device__ __forceinline__ int sel4(const int4 &v, int k) {
 __device__ __forceinline__ d3 rec64_vertex(const TetRec64 *r, int k) {
     return mk(__ldg(&r->v[3 * k]), __ldg(&r->v[3 * k + 1]), __ldg(&r->v[3 * k + 2]));
 }
-__device__ __forceinline__ int exit_rule(int sa, int sb, int sc) {
-    if (sb > 0 && sc < 0) return 0;
-    if (sc > 0 && sa < 0) return 1;
-    if (sa > 0 && sb < 0) return 2;
-    return -1;
+// Exit face of the walk from the signs of side(n->a), side(n->b), side(n->c)
+// (face opposite a, b or c; -1: none)
+__host__ __device__ constexpr int exit_rule(int sa, int sb, int sc) {
+    return (sb > 0 && sc < 0) ? 0 : (sc > 0 && sa < 0) ? 1 : (sa > 0 && sb < 0) ? 2 : -1;
 }
+// The same for three non-zero signs, as a table over the three "positive"
+// bits: 2 bits per entry, 3 = none.
+__host__ __device__ constexpr unsigned exit_rule_table() {
+    unsigned t = 0;
+    for (int c = 0; c < 8; ++c) {
+        const int x = exit_rule(c & 1 ? 1 : -1, c & 2 ? 1 : -1, c & 4 ? 1 : -1);
+        t |= (unsigned)(x < 0 ? 3 : x) << (2 * c);
+    }
+    return t;
+}
+constexpr unsigned EXIT_RULE_TABLE = exit_rule_table();
+__device__ __forceinline__ int exit_rule_pos(bool pa, bool pb, bool pc) {
+    const int v = (int)((EXIT_RULE_TABLE >> (2 * ((int)pa | (int)pb << 1 | (int)pc << 2))) & 3u);
+    return v == 3 ? -1 : v;
+}
+__device__ __forceinline__ int filt_sign(float v, float B) { return (v > B) - (v < -B); }
 
 // ------------------------------------------------ robust (FP64+) fallbacks
 //
@@ -544,10 +559,10 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
         if (alive) {
             // n = v_f and face f's canonical triple (a, b, c), loaded by index;
             // the .w of a, b, c are the neighbours across the faces opposite them
-            const float4 *g = rec[h].v;
-            const int tri = (FACE_TRIPLES >> (6 * f)) & 63;
-            const float4 vn = __ldg(g + f), va = __ldg(g + (tri & 3)),
-                         vb = __ldg(g + ((tri >> 2) & 3)), vc = __ldg(g + (tri >> 4));
+            const float4 *R4 = rec->v;
+            const unsigned h4 = (unsigned)h << 2, tri = (FACE_TRIPLES >> (6 * f)) & 63;
+            const float4 vn = __ldg(R4 + (h4 | f)), va = __ldg(R4 + (h4 | (tri & 3))),
+                         vb = __ldg(R4 + (h4 | ((tri >> 2) & 3))), vc = __ldg(R4 + (h4 | (tri >> 4)));
             float muv[C];
             if (MODE == MODE_FWD) {
                 if (C == 4) {
@@ -562,14 +577,15 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             Filt32Vert Vn = filt32_vert(fr, n);
             f3 ea = sub(a, n), eb = sub(b, n), ec = sub(c, n);
             float sa, sb, sc, ba, bb, bc;
-            int ga = filt32_side_e(Vn, ea, sa, ba);
-            int gb = filt32_side_e(Vn, eb, sb, bb);
-            int gc = filt32_side_e(Vn, ec, sc, bc);
+            filt32_side_e(Vn, ea, sa, ba);
+            filt32_side_e(Vn, eb, sb, bb);
+            filt32_side_e(Vn, ec, sc, bc);
             int x = -1;
             f3 Xout = Xin;
-            bool fast = (ga != 0) & (gb != 0) & (gc != 0);
+            // all three signs certain: each side exceeds its error bound
+            bool fast = (fabsf(sa) > ba) & (fabsf(sb) > bb) & (fabsf(sc) > bc);
             if (fast) {
-                x = exit_rule(ga, gb, gc);
+                x = exit_rule_pos(sa > 0.f, sb > 0.f, sc > 0.f);
                 // exit face (n, y, z): barycentric weights w_y = -side(n->z),
                 // w_z = side(n->y), and their sum = d . ((y - n) x (z - n))
                 const bool x0 = x == 0, x1 = x == 1;
@@ -590,6 +606,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 if (!ROBUST) {
                     defer_now = true;
                 } else {
+                    const int ga = filt_sign(sa, ba), gb = filt_sign(sb, bb), gc = filt_sign(sc, bc);
                     cnt.fp64 += (ga == 0) + (gb == 0) + (gc == 0);
                     int known[3] = {ga, gb, gc};
                     d3 X;
