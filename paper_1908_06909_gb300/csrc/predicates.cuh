@@ -113,7 +113,9 @@ TP_HD double dotd(const d3 &a, const d3 &b) { return fma(a.x, b.x, fma(a.y, b.y,
 // in a folded form with per-vertex Z, c and a per-ray guard G:
 //     u [ Z . |e32| + c ],   Z = 3.03 X + 5.04 |w| + Y',   c = 2.05 |w| . |n| + G,
 // with Y' = |d| x Ma' and Ma' = 1.0101 (|n| + |O|) + 1.00002 |a| +
-// 1.00002e-8 max_i(|S_i| + |P_i|) >= 1.00002 Ma.  Why it dominates: |k| <=
+// 1.00002e-8 max_i(|S_i| + |P_i|) >= 1.00002 Ma.  As x is linear in its second
+// argument, 3.03 X + Y' = |d| x M2 with M2 = 4.031 |a| + 1.0101 (|n| + |O|) +
+// 1.00002e-8 max_i(|S_i| + |P_i|), one product instead of two.  Why it dominates: |k| <=
 // |n| + |k - n| and |k - n| <= (1 + 1.01u)|e32| (e32 = fl(k - n)), so
 // Z2 . (|k| + |n|) <= 1.01 Z2 . |e32| + 2.02 Z2 . |n|; expanding Z1 + 1.01 Z2
 // gives 3.02 X + 5.0301 |w| + Y plus 1.01e-6 (X + Y), which 3.03 X and Y'
@@ -158,14 +160,14 @@ TP_HD Filt32Vert filt32_vert(const Filt32Ray &r, const f3 &n) {
     const f3 a = sub(n, r.O);
     v.w = crossf(r.d, a);
     const f3 nabs = fabs3(n), aabs = fabs3(a), dabs = fabs3(r.d), Oabs = fabs3(r.O);
-    const f3 X = abscrossf(dabs, aabs);
-    const f3 Ma = {fmaf(1.0101f, nabs.x + Oabs.x, fmaf(1.00002f, aabs.x, r.Oext)),
-                   fmaf(1.0101f, nabs.y + Oabs.y, fmaf(1.00002f, aabs.y, r.Oext)),
-                   fmaf(1.0101f, nabs.z + Oabs.z, fmaf(1.00002f, aabs.z, r.Oext))};
-    const f3 Y = abscrossf(dabs, Ma);
+    const f3 M2 = {fmaf(4.031f, aabs.x, fmaf(1.0101f, nabs.x + Oabs.x, r.Oext)),
+                   fmaf(4.031f, aabs.y, fmaf(1.0101f, nabs.y + Oabs.y, r.Oext)),
+                   fmaf(4.031f, aabs.z, fmaf(1.0101f, nabs.z + Oabs.z, r.Oext))};
     const f3 wa = fabs3(v.w);
-    v.Z = {fmaf(3.03f, X.x, fmaf(5.04f, wa.x, Y.x)), fmaf(3.03f, X.y, fmaf(5.04f, wa.y, Y.y)),
-           fmaf(3.03f, X.z, fmaf(5.04f, wa.z, Y.z))};
+    // Z = |d| x M2 + 5.04 |w|
+    v.Z = {fmaf(dabs.y, M2.z, fmaf(dabs.z, M2.y, 5.04f * wa.x)),
+           fmaf(dabs.z, M2.x, fmaf(dabs.x, M2.z, 5.04f * wa.y)),
+           fmaf(dabs.x, M2.y, fmaf(dabs.y, M2.x, 5.04f * wa.z))};
     v.c = fmaf(2.05f, dotf(wa, nabs), r.G);
     return v;
 }
