@@ -393,14 +393,16 @@ __device__ __forceinline__ void rstar_search(const MeshView &m, const f3 &S, con
 //
 // Two kernels share one body.  The FAST kernel (ROBUST = false) takes only
 // decisions the FP32 filter certifies; a ray that meets an undecided side
-// product (or an undecided entry face) is appended to the deferral queue with
-// the number of segments it has already produced, and stops.  The fast kernel
-// therefore contains no call to the FP64 / exact / symbolic stages and fits in
-// 64 registers without spilling.  The RESUME kernel (ROBUST = true) re-walks
-// each queued ray from its start with the full cascade; every decision the
-// fast kernel took was exact, so the resumed walk visits the same tets in the
-// same order and simply skips the backprojection contributions (or trace
-// entries) that were already written.
+// product (or an undecided entry face) stops, and when the warp's walk loop
+// ends it is appended to the deferral queue with its walk state.  The fast
+// kernel therefore contains no call to the FP64 / exact / symbolic stages;
+// it is capped at 56 registers (no spills), so 36 warps fit on an SM.  The
+// RESUME kernel (ROBUST = true) continues each queued walk from that state
+// with the full cascade.  Every decision the fast kernel took was exact, so
+// the two parts together visit the same tets, in the same order, as one
+// robust walk.  (Running the FP64 steps in place, inside the fast warps, was
+// measured 1.7x slower on the full-size workload: GB300's FP64 rate is low and
+// the other 31 lanes wait.)
 
 // Warp-aggregated append to the deferral queue.  All 32 lanes must call it
 // (converged); lanes with want = true write their entry.
@@ -490,6 +492,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                     Xin = f3axpy(sca * iw, sub(b, a), f3axpy(sab * iw, sub(c, a), a));
                 } else if (!ROBUST) {
                     deferred = true;  // undecided entry face: finish the ray robustly
+                    h = -1;           // (queued with fs = -1: resume from the entry search)
                     return true;
                 } else {
                     int known[3] = {gab, gbc, gca};
@@ -542,7 +545,6 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
     // MODE_SEG: this ray's next slot in the segment buffer
     int64_t spos = 0;
     if (MODE == MODE_SEG && valid) spos = seg_slot(p, ray) + steps;
-    if (!ROBUST) defer_append<C>(p, deferred, ray, 0, -1, Xin, 0, acc, comp);
     flush_counters(p.m.counters, cnt);
     cnt = {0, 0, 0, 0, 0, 0, 0, 0};
 
@@ -723,10 +725,14 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                     atomicAdd(accbuf + hcur, len * yv[0]);
             }
         }
-        if (!ROBUST)
-            defer_append<C>(p, defer_now, ray, hcur, fcur | ((int)clip0 << 2) | (steps << 3), Xin,
-                            nvis, acc, comp);
     }
+    // rays that stopped at an uncertain decision go to the resume kernel with
+    // their walk state (h, f, clip flag, step count, entry point, partial sums;
+    // none of these changes once a lane defers), or with fs = -1 when the
+    // entry face itself was uncertain
+    if (!ROBUST)
+        defer_append<C>(p, deferred, ray, h < 0 ? 0 : h,
+                        h < 0 ? -1 : f | ((int)clip0 << 2) | (steps << 3), Xin, nvis, acc, comp);
 
     if (valid && !deferred) {
         if (MODE == MODE_FWD) {
@@ -758,7 +764,7 @@ __device__ __forceinline__ const BvhNode *stage_bvh_top(const KParams &p, float4
 }
 
 template <int C, int MODE, int ENTRY = ENTRY_BVH>
-__global__ void __launch_bounds__(256, 4) k_walk32(const __grid_constant__ KParams p) {
+__global__ void __maxnreg__(56) k_walk32(const __grid_constant__ KParams p) {
     extern __shared__ float4 smem[];
     const BvhNode *snodes = stage_bvh_top(p, smem);
     int64_t ray = 0;
