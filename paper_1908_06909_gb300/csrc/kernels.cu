@@ -158,6 +158,20 @@ __device__ __forceinline__ int exit_rule_pos(bool pa, bool pb, bool pc) {
 }
 __device__ __forceinline__ int filt_sign(float v, float B) { return (v > B) - (v < -B); }
 
+// Accumulator reductions in the .global state space.  The accumulator
+// pointers of the batched walk come from shared memory (the per-warp
+// parameter slot), so the compiler cannot infer their space on its own.
+__device__ __forceinline__ void red_add_global(float *a, float v) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(a)), "f"(v));
+}
+__device__ __forceinline__ void red_add_global(float4 *a, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_global(a)),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
+}
+__device__ __forceinline__ void red_add_global(double *a, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(a)), "d"(v));
+}
+
 // ------------------------------------------------ robust (FP64+) fallbacks
 //
 // Used by both walks when a fast sign is uncertain.  They reload the exact
@@ -685,7 +699,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
         if (MODE == MODE_BWD64 && did) {  // FP64 accumulation: no drift with many segments
             double *acc64 = reinterpret_cast<double *>(p.out) + (int64_t)hcur * C;
 #pragma unroll
-            for (int cc = 0; cc < C; ++cc) atomicAdd(acc64 + cc, (double)(len * yv[cc]));
+            for (int cc = 0; cc < C; ++cc) red_add_global(acc64 + cc, (double)(len * yv[cc]));
         }
         if (MODE == MODE_BWD) {
             if (!ROBUST && p.scatter == TETPROJ_SCATTER_WARP) {
@@ -710,19 +724,19 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                     }
                     if (lane == __ffs(peers) - 1) {
                         if (C == 4)
-                            atomicAdd(reinterpret_cast<float4 *>(accbuf) + hcur,
-                                      make_float4(v[0], v[1 % C], v[2 % C], v[3 % C]));
+                            red_add_global(reinterpret_cast<float4 *>(accbuf) + hcur,
+                                           make_float4(v[0], v[1 % C], v[2 % C], v[3 % C]));
                         else
-                            atomicAdd(accbuf + hcur, v[0]);
+                            red_add_global(accbuf + hcur, v[0]);
                     }
                 }
             } else if (did) {
                 if (C == 4)
-                    atomicAdd(reinterpret_cast<float4 *>(accbuf) + hcur,
-                              make_float4(len * yv[0], len * yv[1 % C], len * yv[2 % C],
-                                          len * yv[3 % C]));
+                    red_add_global(reinterpret_cast<float4 *>(accbuf) + hcur,
+                                   make_float4(len * yv[0], len * yv[1 % C], len * yv[2 % C],
+                                               len * yv[3 % C]));
                 else
-                    atomicAdd(accbuf + hcur, len * yv[0]);
+                    red_add_global(accbuf + hcur, len * yv[0]);
             }
         }
     }
