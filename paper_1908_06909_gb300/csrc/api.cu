@@ -589,6 +589,22 @@ static bool use_acc64(const tetproj_options &o) {
     return o.channels == 1;
 }
 
+// Dense problems (few tets, many rays) at C = 4: a tet collects up to ~10^5
+// FP32 reductions per call, and their rounding drifts toward 1e-5 relative.
+// There the default FP32 accumulation is two-level: the walk's FP32
+// accumulator is moved into an FP64 one after every chunk of at most
+// dense_chunk_rays rays, so no FP32 sum holds more than a few thousand terms
+// (FP64 reductions instead cost 1.7-2.6x at C = 4, four 8-byte reductions per
+// segment).  Dense: nt C <= 2^20 elements and >= 64 rays per element.
+static bool dense_acc(int64_t nt, int channels, int64_t nrays) {
+    const int64_t n = nt * channels;
+    return n <= (int64_t(1) << 20) && nrays >= 64 * n;
+}
+static int64_t dense_chunk_rays(int64_t nt) {
+    const int64_t c = 64 * nt;
+    return c < (int64_t(1) << 18) ? (int64_t(1) << 18) : c;
+}
+
 static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
                                    const void *y, void *mu_out, cudaStream_t s) {
     if (rstar_unsupported(o)) return TETPROJ_ERR_ARG;
@@ -618,6 +634,19 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
     TP_CUDA(cudaMemsetAsync(ws, 0, (size_t)m->ws_bytes[f64][o.channels == 4], s));
     p.in = y;
     p.out = ws;
+    if (!f64 && !(o.flags & TETPROJ_FLAG_ACC32) && dense_acc(m->nt, o.channels, p.nrays)) {
+        st = ensure_ws(m, TETPROJ_PLAIN_FP64, o.channels);
+        if (st != TETPROJ_OK) return st;
+        void *ws64 = m->ws[1][o.channels == 4];
+        TP_CUDA(cudaMemsetAsync(ws64, 0, (size_t)m->ws_bytes[1][o.channels == 4], s));
+        AccMerge mg{reinterpret_cast<float *>(ws), reinterpret_cast<double *>(ws64),
+                    m->nt * o.channels, dense_chunk_rays(m->nt)};
+        TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s, overlap_of(m), &mg));
+        TP_CUDA(launch_scatter_perm_d2f(m->perm, m->nt, o.channels,
+                                        reinterpret_cast<const double *>(ws64),
+                                        reinterpret_cast<float *>(mu_out), s));
+        return TETPROJ_OK;
+    }
     TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s, overlap_of(m)));
     TP_CUDA(launch_scatter_perm(m->perm, m->nt, o.channels, f64, ws, mu_out, s));
     return TETPROJ_OK;
@@ -993,12 +1022,18 @@ struct tetproj_batch {
     bool bound = false;
     ResumeOverlap ov{};  // second queue + auxiliary stream when there are several rounds
     bool ov_ready = false;
+    // dense problems at C = 4: FP32 scratch the walk reduces into, merged into
+    // the FP64 accumulator (ws_acc) after every round
+    std::vector<float *> acc32;   // per problem, null unless dense
+    std::vector<AccMerge> merges; // the dense problems' merges
+    int64_t round_rays = 0;       // rays per round (<= q_cap)
 };
 
 static void batch_free(tetproj_batch *b) {
     if (!b) return;
     for (void *p : b->ws_in) cudaFree(p);
     for (void *p : b->ws_acc) cudaFree(p);
+    for (float *p : b->acc32) cudaFree(p);
     cudaFree(b->d_fwd);
     cudaFree(b->d_bwd);
     cudaFree(b->d_item_begin);
@@ -1059,6 +1094,11 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
         b->ws_in.push_back(a);
         b->ws_acc.push_back(c);
         b->ws_bytes.push_back(bytes);
+        float *s32 = nullptr;
+        const int64_t prays = (int64_t)p.g.na * p.g.nu * p.g.nv;
+        if (e == cudaSuccess && channels == 4 && dense_acc(meshes[k]->nt, channels, prays))
+            e = cudaMalloc((void **)&s32, (size_t)bytes);
+        b->acc32.push_back(s32);
         if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
     }
     if (b->item_begin.back() >= (int64_t(1) << 40)) { batch_free(b); return TETPROJ_ERR_TOO_LARGE; }
@@ -1080,6 +1120,14 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
     }
     if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
     b->q_cap = need;
+    b->round_rays = need;
+    for (int k = 0; k < n; ++k)
+        if (b->acc32[k]) {
+            const int64_t c = dense_chunk_rays(meshes[k]->nt);
+            if (c < b->round_rays) b->round_rays = c;
+            b->merges.push_back(AccMerge{b->acc32[k], reinterpret_cast<double *>(b->ws_acc[k]),
+                                         meshes[k]->nt * channels, 0});
+        }
     // launch shapes are fixed here so that forward/backward issue stream work only
     int snodes = 0;
     for (auto &p : b->base) snodes = p.smem_nodes > snodes ? p.smem_nodes : snodes;
@@ -1120,7 +1168,7 @@ extern "C" tetproj_status tetproj_batch_bind(tetproj_batch *b, const void *const
         f[k].p.qtag = (int64_t)k << 40;
         g[k].p = b->base[k];
         g[k].p.in = b->y[k];
-        g[k].p.out = b->ws_acc[k];
+        g[k].p.out = b->acc32[k] ? (void *)b->acc32[k] : b->ws_acc[k];
         g[k].p.qtag = (int64_t)k << 40;
     }
     TP_CUDA(cudaMemcpy(b->d_fwd, f.data(), sizeof(BatchProblem) * b->n, cudaMemcpyHostToDevice));
@@ -1139,7 +1187,7 @@ extern "C" tetproj_status tetproj_batch_forward(tetproj_batch *b, void *stream) 
                                    b->ws_in[k], s));
     TP_CUDA(launch_batch(b->d_fwd, b->d_item_begin, b->n, b->item_begin.back(),
                          b->channels, MODE_FWD, b->grid_fwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
-                         b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr));
+                         b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr, b->q_cap, nullptr, 0));
     return TETPROJ_OK;
 }
 
@@ -1148,13 +1196,17 @@ extern "C" tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream)
     for (int k = 0; k < b->n; ++k)
         if (!b->y[k] || !b->mu_out[k]) return TETPROJ_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    for (int k = 0; k < b->n; ++k)
-        TP_CUDA(cudaMemsetAsync(b->ws_acc[k], 0, (size_t)(b->acc64 ? 2 : 1) * b->ws_bytes[k], s));
+    for (int k = 0; k < b->n; ++k) {
+        const bool wide = b->acc64 || b->acc32[k];
+        TP_CUDA(cudaMemsetAsync(b->ws_acc[k], 0, (size_t)(wide ? 2 : 1) * b->ws_bytes[k], s));
+        if (b->acc32[k]) TP_CUDA(cudaMemsetAsync(b->acc32[k], 0, (size_t)b->ws_bytes[k], s));
+    }
     TP_CUDA(launch_batch(b->d_bwd, b->d_item_begin, b->n, b->item_begin.back(),
                          b->channels, b->acc64 ? MODE_BWD64 : MODE_BWD, b->grid_bwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
-                         b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr));
+                         b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr, b->round_rays,
+                         b->merges.empty() ? nullptr : b->merges.data(), (int)b->merges.size()));
     for (int k = 0; k < b->n; ++k) {
-        if (b->acc64)
+        if (b->acc64 || b->acc32[k])
             TP_CUDA(launch_scatter_perm_d2f(b->meshes[k]->perm, b->meshes[k]->nt, b->channels,
                                             reinterpret_cast<const double *>(b->ws_acc[k]),
                                             reinterpret_cast<float *>(b->mu_out[k]), s));

@@ -1231,10 +1231,18 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
                                      unsigned rgrid, QEntry *q, unsigned long long *q_count,
                                      int64_t q_cap, unsigned *item_counter,
                                      int smem_nodes, cudaStream_t stream,
-                                     const ResumeOverlap *ov) {
-    // rounds of whole chunks of warp items (32 rays each), at most q_cap rays
-    const int64_t round_items = (q_cap / (32 * kBatchChunk)) * kBatchChunk;
+                                     const ResumeOverlap *ov, int64_t round_rays,
+                                     const AccMerge *merges, int nmerge) {
+    // rounds of whole chunks of warp items (32 rays each), at most round_rays rays
+    if (round_rays > q_cap || (nmerge > 0 && MODE != MODE_BWD)) return cudaErrorInvalidValue;
+    const int64_t round_items = (round_rays / (32 * kBatchChunk)) * kBatchChunk;
     if (round_items < 1) return cudaErrorInvalidValue;
+    auto merge_all = [&](cudaStream_t st) {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < nmerge && e == cudaSuccess; ++i)
+            e = launch_acc_merge(merges[i].acc32, merges[i].acc64, merges[i].n, st);
+        return e;
+    };
     if (ov && nitems > round_items) {
         // resume of round r on ov->aux while round r + 1 runs (queues alternate)
         cudaError_t e = cudaEventRecord(ov->ev_start, stream);
@@ -1259,6 +1267,7 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
             k_batch_resume32<C, MODE><<<rgrid, 128, 0, ov->aux>>>(probs, qj, cj, q_cap);
             note_launch();
             e = cudaGetLastError();
+            if (e == cudaSuccess) e = merge_all(ov->aux);
             if (e == cudaSuccess) e = cudaEventRecord(ov->ev_res[j], ov->aux);
             used |= 1 << j;
         }
@@ -1277,6 +1286,7 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
         k_batch_resume32<C, MODE><<<rgrid, 128, 0, stream>>>(probs, q, q_count, q_cap);
         note_launch();
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = merge_all(stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1286,11 +1296,12 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
                          int64_t nitems, int channels, int mode, unsigned grid,
                          unsigned rgrid, QEntry *q, unsigned long long *q_count, int64_t q_cap,
                          unsigned *item_counter, int smem_nodes, cudaStream_t stream,
-                         const ResumeOverlap *ov) {
+                         const ResumeOverlap *ov, int64_t round_rays, const AccMerge *merges,
+                         int nmerge) {
     if (nitems <= 0) return cudaSuccess;
     if (grid < 1 || rgrid < 1) return cudaErrorInvalidValue;
 #define TP_BATCH_ARGS probs, item_begin, nprob, nitems, grid, rgrid, q, q_count, q_cap, \
-                      item_counter, smem_nodes, stream, ov
+                      item_counter, smem_nodes, stream, ov, round_rays, merges, nmerge
     if (mode == MODE_FWD)
         return channels == 4 ? launch_batch_mode<4, MODE_FWD>(TP_BATCH_ARGS)
                              : launch_batch_mode<1, MODE_FWD>(TP_BATCH_ARGS);
@@ -1565,7 +1576,8 @@ __global__ void k_side(const double *S, const double *P, const double *p, const 
 
 template <int C, int MODE, int ENTRY = ENTRY_BVH>
 static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks, int threads,
-                               size_t smem, cudaStream_t stream, const ResumeOverlap *ov) {
+                               size_t smem, cudaStream_t stream, const ResumeOverlap *ov,
+                               const AccMerge *mg) {
     KParams p = p0;
     if constexpr (ENTRY == ENTRY_BVH && MODE != MODE_BWD64 && MODE != MODE_ENTRY) {
         if (precision != TETPROJ_FILTERED) {
@@ -1577,8 +1589,11 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
     } else {
         if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;
     }
-    // chunks of at most q_cap rays, each followed by the resume kernel
+    // chunks of at most q_cap rays (and mg->chunk_rays), each followed by
+    // the resume kernel (and the accumulator merge)
+    if (mg && MODE != MODE_BWD) return cudaErrorInvalidValue;
     int64_t chunk = p.q_cap / threads;
+    if (mg && mg->chunk_rays / threads < chunk) chunk = mg->chunk_rays / threads;
     if (chunk < 1) return cudaErrorInvalidValue;
     const unsigned rgrid = (unsigned)(4 * sm_count());
     if (ov && nblocks > chunk) {
@@ -1606,6 +1621,7 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
             k_resume32<C, MODE><<<rgrid, 128, smem, ov->aux>>>(pc);
             note_launch();
             e = cudaGetLastError();
+            if (e == cudaSuccess && mg) e = launch_acc_merge(mg->acc32, mg->acc64, mg->n, ov->aux);
             if (e == cudaSuccess) e = cudaEventRecord(ov->ev_res[j], ov->aux);
             used |= 1 << j;
         }
@@ -1623,9 +1639,28 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
         k_resume32<C, MODE><<<rgrid, 128, smem, stream>>>(p);
         note_launch();
         e = cudaGetLastError();
+        if (e == cudaSuccess && mg) e = launch_acc_merge(mg->acc32, mg->acc64, mg->n, stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+__global__ void k_acc_merge(float *acc32, double *acc64, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float v = atomicExch(acc32 + i, 0.f);
+        if (v != 0.f) acc64[i] += (double)v;
+    }
+}
+
+cudaError_t launch_acc_merge(float *acc32, double *acc64, int64_t n, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)8 * sm_count();
+    if (blocks > cap) blocks = cap;
+    k_acc_merge<<<(unsigned)blocks, 256, 0, stream>>>(acc32, acc64, n);
+    note_launch();
+    return cudaGetLastError();
 }
 
 template <int C, int MODE>
@@ -1700,7 +1735,8 @@ cudaError_t launch_block_offsets(const KParams &p, const int32_t *count, int32_t
 }
 
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
-                        cudaStream_t stream, const ResumeOverlap *ov) {
+                        cudaStream_t stream, const ResumeOverlap *ov, const AccMerge *mg) {
+    if (mg && mode != MODE_BWD) return cudaErrorInvalidValue;
     int64_t nblocks;
     int threads;
     if (p.src_kind == 0) {
@@ -1716,27 +1752,27 @@ cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
     if (mode == MODE_FWD) {
         if (p.entry == ENTRY_RSTAR) {  // the paper's entry structure: FP32, C = 1
             if (precision != TETPROJ_FILTERED || channels != 1) return cudaErrorInvalidValue;
-            return launch_mode<1, MODE_FWD, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream, ov);
+            return launch_mode<1, MODE_FWD, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream, ov, mg);
         }
-        return channels == 4 ? launch_mode<4, MODE_FWD>(p, precision, nblocks, threads, smem, stream, ov)
-                             : launch_mode<1, MODE_FWD>(p, precision, nblocks, threads, smem, stream, ov);
+        return channels == 4 ? launch_mode<4, MODE_FWD>(p, precision, nblocks, threads, smem, stream, ov, mg)
+                             : launch_mode<1, MODE_FWD>(p, precision, nblocks, threads, smem, stream, ov, mg);
     }
     if (mode == MODE_BWD) {
-        return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, nblocks, threads, smem, stream, ov)
-                             : launch_mode<1, MODE_BWD>(p, precision, nblocks, threads, smem, stream, ov);
+        return channels == 4 ? launch_mode<4, MODE_BWD>(p, precision, nblocks, threads, smem, stream, ov, mg)
+                             : launch_mode<1, MODE_BWD>(p, precision, nblocks, threads, smem, stream, ov, mg);
     }
     if (mode == MODE_BWD64) {
         if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;
-        return channels == 4 ? launch_mode<4, MODE_BWD64>(p, precision, nblocks, threads, smem, stream, ov)
-                             : launch_mode<1, MODE_BWD64>(p, precision, nblocks, threads, smem, stream, ov);
+        return channels == 4 ? launch_mode<4, MODE_BWD64>(p, precision, nblocks, threads, smem, stream, ov, mg)
+                             : launch_mode<1, MODE_BWD64>(p, precision, nblocks, threads, smem, stream, ov, mg);
     }
     if (mode == MODE_ENTRY) {
         if (precision != TETPROJ_FILTERED) return cudaErrorInvalidValue;
         return p.entry == ENTRY_RSTAR
-                   ? launch_mode<1, MODE_ENTRY, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream, ov)
-                   : launch_mode<1, MODE_ENTRY>(p, precision, nblocks, threads, smem, stream, ov);
+                   ? launch_mode<1, MODE_ENTRY, ENTRY_RSTAR>(p, precision, nblocks, threads, smem, stream, ov, mg)
+                   : launch_mode<1, MODE_ENTRY>(p, precision, nblocks, threads, smem, stream, ov, mg);
     }
-    return launch_mode<1, MODE_TRACE>(p, precision, nblocks, threads, smem, stream, ov);
+    return launch_mode<1, MODE_TRACE>(p, precision, nblocks, threads, smem, stream, ov, mg);
 }
 
 cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, int f64,

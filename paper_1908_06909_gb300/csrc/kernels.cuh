@@ -91,14 +91,18 @@ constexpr int kBatchChunk = 8;
 // rounds of at most q_cap rays: per round one persistent work-queue launch of
 // `grid` CTAs and one resume launch of `rgrid` CTAs.  `smem_nodes`: BVH nodes
 // staged per warp.  With `ov` (its q2 holding q_cap entries) and more than one
-// round, round r's resume runs on ov->aux beside round r + 1's walk.  Only
-// stream and event operations (graph-capturable).
+// round, round r's resume runs on ov->aux beside round r + 1's walk.  Rounds
+// hold at most round_rays (<= q_cap) rays; after each round's resume the
+// `nmerge` accumulator merges run (MODE_BWD).  Only stream and event
+// operations (graph-capturable).
 struct ResumeOverlap;
+struct AccMerge;
 cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, int nprob,
                          int64_t nitems, int channels, int mode, unsigned grid, unsigned rgrid,
                          QEntry *q, unsigned long long *q_count, int64_t q_cap,
                          unsigned *item_counter, int smem_nodes, cudaStream_t stream,
-                         const ResumeOverlap *ov = nullptr);
+                         const ResumeOverlap *ov, int64_t round_rays, const AccMerge *merges,
+                         int nmerge);
 // Persistent grid for the batched walk: resident CTAs per SM x SM count.
 cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid);
 int device_sm_count();
@@ -156,9 +160,25 @@ struct ResumeOverlap {
     cudaEvent_t ev_fast[2], ev_res[2], ev_start;
 };
 
-// one launch of the walk; returns a cudaError_t
+// Two-level accumulation of the FP32 backprojection: the walk reduces into
+// acc32 (FP32, n floats) and, after each chunk of at most chunk_rays rays
+// (and its resume kernel), acc32 is moved into acc64 and zeroed, so that no
+// FP32 sum collects more than one chunk's contributions.  The move reads
+// acc32 with atomic exchanges: reductions of a chunk running at the same time
+// (overlapped resume) land either before or after it and are never lost.
+struct AccMerge {
+    float *acc32;
+    double *acc64;
+    int64_t n;
+    int64_t chunk_rays;
+};
+cudaError_t launch_acc_merge(float *acc32, double *acc64, int64_t n, cudaStream_t stream);
+
+// one launch of the walk; returns a cudaError_t.  `mg` (MODE_BWD only): the
+// walk's p.out is mg->acc32, merged into mg->acc64 after every chunk.
 cudaError_t launch_walk(const KParams &p, int precision, int channels, int mode,
-                        cudaStream_t stream, const ResumeOverlap *ov = nullptr);
+                        cudaStream_t stream, const ResumeOverlap *ov = nullptr,
+                        const AccMerge *mg = nullptr);
 cudaError_t launch_gather_perm(const int32_t *perm, int64_t nt, int channels, int f64,
                                const void *src_user, void *dst_h, cudaStream_t stream);
 cudaError_t launch_scatter_perm(const int32_t *perm, int64_t nt, int channels, int f64,

@@ -89,21 +89,27 @@ def test_sort_several_chunks(tp):
     a = tp.backward(mesh, geo, y, options=o_sort)
     b = tp.backward(mesh, geo, y, options=o_sort)
     ref = tp.backward(mesh, geo, y, options=_opts(tp, tp.SCATTER_ATOMIC, 4, tile=(16, 8)))
+    flat = tp.backward(mesh, geo, y, options=tp.make_options(
+        channels=4, tile=(16, 8), scatter=tp.SCATTER_ATOMIC, flags=tp.FLAG_ACC32))
     torch.cuda.synchronize()
     assert mesh.stats()["error"] == 0
     assert torch.equal(a, b)
     # sampled tets against the oracle (y >= 0: the reference is its own scale).
     # ~10^5 segments reach each tet here; the sorted runs are summed with
-    # compensation, the atomic scatter's FP32 sums are not (reported only).
+    # compensation, the default atomic scatter is two-level here (FP32 sums of
+    # one chunk merged into FP64), plain FP32 atomic sums drift (reported only).
     rng = np.random.default_rng(12)
     ts = rng.choice(tets.shape[0], 6, replace=False)
     want = oracle.backward_cone_subset(verts, tets, y.double().cpu().numpy().reshape(-1, 4), g, ts)
     idx = torch.tensor(ts, device="cuda")
     got = a[idx].double().cpu().numpy()
     got_atomic = ref[idx].double().cpu().numpy()
+    got_flat = flat[idx].double().cpu().numpy()
     print(f"sort max rel {np.max(np.abs(got - want) / want):.2e}, "
-          f"atomic max rel {np.max(np.abs(got_atomic - want) / want):.2e}")
+          f"atomic two-level max rel {np.max(np.abs(got_atomic - want) / want):.2e}, "
+          f"atomic FP32 max rel {np.max(np.abs(got_flat - want) / want):.2e}")
     assert np.all(np.abs(got - want) <= TOL["f32"] * want)
+    assert np.all(np.abs(got_atomic - want) <= TOL["f32"] * want)
 
 
 def test_sort_full_size_bench_workload(tp):
