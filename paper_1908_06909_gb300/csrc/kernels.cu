@@ -1379,8 +1379,8 @@ template <typename T>
 __device__ __forceinline__ MtV<T> mt_vertex(const MeshView &m, int h, int k);
 template <>
 __device__ __forceinline__ MtV<float> mt_vertex<float>(const MeshView &m, int h, int k) {
-    const float *r = reinterpret_cast<const float *>(m.rec32 + h);  // v0..v3 xyz first
-    return {__ldg(r + 3 * k), __ldg(r + 3 * k + 1), __ldg(r + 3 * k + 2)};
+    const float4 v = __ldg(m.rec32[h].v + k);  // xyz of local vertex k
+    return {v.x, v.y, v.z};
 }
 template <>
 __device__ __forceinline__ MtV<double> mt_vertex<double>(const MeshView &m, int h, int k) {
