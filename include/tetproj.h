@@ -96,8 +96,14 @@ typedef int32_t tetproj_status;
 #define TETPROJ_FLAG_ACC32 4       /* the same into an FP32 accumulator (faster for
                                       C = 4: one 16-byte red per segment instead
                                       of four 8-byte ones; FP32 sums drift like
-                                      sqrt(segments per tet) * 2^-24).  Default
-                                      for C = 4.  At most one ACC flag.        */
+                                      sqrt(segments per tet) * 2^-24).  With
+                                      neither ACC flag, C = 4 uses FP32 too, but
+                                      two-level on dense meshes (nt * C <= 2^20
+                                      and >= 64 rays per element): the FP32
+                                      accumulator is merged into an FP64 one
+                                      after every chunk of at most
+                                      max(2^18, 64 nt) rays.  ACC32 keeps it
+                                      single-level.  At most one ACC flag.     */
 
 typedef struct tetproj_mesh tetproj_mesh;
 typedef struct tetproj_geometry tetproj_geometry;
@@ -271,7 +277,9 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
  * The batch owns per-problem workspace and one deferral queue (allocated
  * here); it keeps pointers into the meshes and geometries, which must outlive
  * it.  Backprojections add into FP64 accumulators at C = 1 (each problem's
- * scatter choice then does not apply) and into FP32 ones at C = 4.  Rays are processed in rounds of at most 2^23 rays.
+ * scatter choice then does not apply) and into FP32 ones at C = 4, two-level
+ * for dense problems (as TETPROJ_FLAG_ACC32 describes; merged after every
+ * round).  Rays are processed in rounds of at most 2^23 rays.
  * Errors: TETPROJ_ERR_ARG (null handle, n < 1, bad channels or tiles),
  * TETPROJ_ERR_TOO_LARGE (2^40 work items or more), CUDA
  * errors of the allocations; *out is NULL on error. */
