@@ -368,24 +368,48 @@ def run_batch(args, tp, torch, dist, rank, world, local):
         del p64, x64, p32, x32, mu64
 
     # end to end with host buffers: H2D of every mu, D2H of every projection
-    # and backprojection (the graphs read and write the bound tensors)
+    # and backprojection (the graphs read and write the bound tensors).  The
+    # copies run on a second stream beside the walks: the projections' D2H
+    # and the next step's H2D during the backprojection, the backprojections'
+    # D2H during the next forward projection; events keep every buffer's
+    # writer after its previous copy.
     mu_h = [torch.empty_like(x, device="cpu").pin_memory() for x in b.mu]
     for k in range(b.n):
         mu_h[k].copy_(b.mu[k])
     proj_h = [torch.empty_like(x, device="cpu").pin_memory() for x in b.proj]
     back_h = [torch.empty_like(x, device="cpu").pin_memory() for x in b.mu_out]
+    cs = torch.cuda.Stream()
+    ev_f, ev_b, ev_c1, ev_c2 = (torch.cuda.Event() for _ in range(4))
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
-        for k in range(b.n):
-            b.mu[k].copy_(mu_h[k], non_blocking=True)
+    for k in range(b.n):
+        b.mu[k].copy_(mu_h[k], non_blocking=True)
+    for step in range(args.steps):
+        if step > 0:
+            stream.wait_event(ev_c1)  # next mu in, previous projections out
         gf.replay()
+        ev_f.record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_f)
+            for k in range(b.n):
+                proj_h[k].copy_(b.proj[k], non_blocking=True)
+            if step + 1 < args.steps:
+                for k in range(b.n):
+                    b.mu[k].copy_(mu_h[k], non_blocking=True)
+            ev_c1.record(cs)
         for k in range(b.n):
             b.y[k].copy_(b.proj[k])
+        if step > 0:
+            stream.wait_event(ev_c2)  # previous backprojections out
         gb.replay()
-        for k in range(b.n):
-            proj_h[k].copy_(b.proj[k], non_blocking=True)
-            back_h[k].copy_(b.mu_out[k], non_blocking=True)
+        ev_b.record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_b)
+            for k in range(b.n):
+                back_h[k].copy_(b.mu_out[k], non_blocking=True)
+            ev_c2.record(cs)
+    stream.wait_event(ev_c1)
+    stream.wait_event(ev_c2)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
@@ -601,16 +625,38 @@ def main():
     mu_h.copy_(mu.cpu())
     proj_h = torch.empty(geo.shape, dtype=torch.float32, pin_memory=True)
     back_h = torch.empty(mesh.nt, dtype=torch.float32, pin_memory=True)
-    mu_d = torch.empty_like(mu)
+    # The copies run on a second stream beside the walks: the projection's D2H
+    # and the next step's H2D (into the other of two input buffers) during the
+    # backprojection, the backprojection's D2H during the next forward
+    # projection; events keep every buffer's writer after its previous copy.
+    mu_d = [torch.empty_like(mu), torch.empty_like(mu)]
+    cs = torch.cuda.Stream()
+    ev_f, ev_b, ev_c1, ev_c2 = (torch.cuda.Event() for _ in range(4))
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(args.steps):
-        mu_d.copy_(mu_h, non_blocking=True)
-        tp.forward(mesh, geo, mu_d, out=proj, options=opt)
+    mu_d[0].copy_(mu_h, non_blocking=True)
+    for step in range(args.steps):
+        if step > 0:
+            stream.wait_event(ev_c1)  # this step's mu in, previous projection out
+        tp.forward(mesh, geo, mu_d[step % 2], out=proj, options=opt)
+        ev_f.record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_f)
+            proj_h.copy_(proj, non_blocking=True)
+            if step + 1 < args.steps:
+                mu_d[(step + 1) % 2].copy_(mu_h, non_blocking=True)
+            ev_c1.record(cs)
+        if step > 0:
+            stream.wait_event(ev_c2)  # previous backprojection out
         tp.backward(mesh, geo, proj, out=back, options=opt)
-        proj_h.copy_(proj, non_blocking=True)
-        back_h.copy_(back, non_blocking=True)
+        ev_b.record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_b)
+            back_h.copy_(back, non_blocking=True)
+            ev_c2.record(cs)
+    stream.wait_event(ev_c1)
+    stream.wait_event(ev_c2)
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / args.steps
