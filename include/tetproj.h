@@ -279,7 +279,9 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
  * it.  Backprojections add into FP64 accumulators at C = 1 (each problem's
  * scatter choice then does not apply) and into FP32 ones at C = 4, two-level
  * for dense problems (as TETPROJ_FLAG_ACC32 describes; merged after every
- * round).  Rays are processed in rounds of at most 2^23 rays.
+ * round).  Rays are processed in rounds of at most 2^23 rays; backprojection
+ * rounds are cut further inside dense problems (every max(2^18, 64 nt) of
+ * their rays).
  * Errors: TETPROJ_ERR_ARG (null handle, n < 1, bad channels or tiles),
  * TETPROJ_ERR_TOO_LARGE (2^40 work items or more), CUDA
  * errors of the allocations; *out is NULL on error. */

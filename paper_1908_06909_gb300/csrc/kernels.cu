@@ -1231,28 +1231,46 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
                                      unsigned rgrid, QEntry *q, unsigned long long *q_count,
                                      int64_t q_cap, unsigned *item_counter,
                                      int smem_nodes, cudaStream_t stream,
-                                     const ResumeOverlap *ov, int64_t round_rays,
-                                     const AccMerge *merges, int nmerge) {
-    // rounds of whole chunks of warp items (32 rays each), at most round_rays rays
-    if (round_rays > q_cap || (nmerge > 0 && MODE != MODE_BWD)) return cudaErrorInvalidValue;
-    const int64_t round_items = (round_rays / (32 * kBatchChunk)) * kBatchChunk;
+                                     const ResumeOverlap *ov, const int64_t *cuts,
+                                     int ncuts, const AccMerge *merges, int nmerge) {
+    // rounds of warp items (32 rays each), at most q_cap rays: uniform, or
+    // [cuts[i], cuts[i + 1]) when cuts are given
+    if (nmerge > 0 && MODE != MODE_BWD) return cudaErrorInvalidValue;
+    const int64_t round_items = (q_cap / (32 * kBatchChunk)) * kBatchChunk;
     if (round_items < 1) return cudaErrorInvalidValue;
+    const int64_t nrounds = cuts ? (int64_t)ncuts - 1 : (nitems + round_items - 1) / round_items;
+    if (cuts) {
+        if (ncuts < 2 || cuts[0] != 0 || cuts[ncuts - 1] != nitems) return cudaErrorInvalidValue;
+        for (int i = 0; i + 1 < ncuts; ++i)
+            if (cuts[i + 1] <= cuts[i] || cuts[i + 1] - cuts[i] > round_items)
+                return cudaErrorInvalidValue;
+    }
+    auto round_of = [&](int64_t i, int64_t &r0, int64_t &r1) {
+        if (cuts) {
+            r0 = cuts[i];
+            r1 = cuts[i + 1];
+        } else {
+            r0 = i * round_items;
+            r1 = nitems - r0 < round_items ? nitems : r0 + round_items;
+        }
+    };
     auto merge_all = [&](cudaStream_t st) {
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < nmerge && e == cudaSuccess; ++i)
             e = launch_acc_merge(merges[i].acc32, merges[i].acc64, merges[i].n, st);
         return e;
     };
-    if (ov && nitems > round_items) {
+    if (ov && nrounds > 1) {
         // resume of round r on ov->aux while round r + 1 runs (queues alternate)
         cudaError_t e = cudaEventRecord(ov->ev_start, stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->ev_start, 0);
         int used = 0;
-        for (int64_t r0 = 0, i = 0; r0 < nitems && e == cudaSuccess; r0 += round_items, ++i) {
+        for (int64_t i = 0; i < nrounds && e == cudaSuccess; ++i) {
             const int j = (int)(i & 1);
             QEntry *qj = j ? ov->q2 : q;
             unsigned long long *cj = j ? ov->q2_count : q_count;
-            const int64_t r1 = nitems - r0 < round_items ? nitems : r0 + round_items;
+            int64_t r0, r1;
+            round_of(i, r0, r1);
             if (i >= 2) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
             if (e == cudaSuccess) e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(cj, 0, sizeof(unsigned long long), stream);
@@ -1275,8 +1293,9 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
             if (used & (1 << j)) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
         return e;
     }
-    for (int64_t r0 = 0; r0 < nitems; r0 += round_items) {
-        const int64_t r1 = nitems - r0 < round_items ? nitems : r0 + round_items;
+    for (int64_t i = 0; i < nrounds; ++i) {
+        int64_t r0, r1;
+        round_of(i, r0, r1);
         cudaError_t e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(q_count, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
@@ -1296,12 +1315,12 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
                          int64_t nitems, int channels, int mode, unsigned grid,
                          unsigned rgrid, QEntry *q, unsigned long long *q_count, int64_t q_cap,
                          unsigned *item_counter, int smem_nodes, cudaStream_t stream,
-                         const ResumeOverlap *ov, int64_t round_rays, const AccMerge *merges,
-                         int nmerge) {
+                         const ResumeOverlap *ov, const int64_t *cuts, int ncuts,
+                         const AccMerge *merges, int nmerge) {
     if (nitems <= 0) return cudaSuccess;
     if (grid < 1 || rgrid < 1) return cudaErrorInvalidValue;
 #define TP_BATCH_ARGS probs, item_begin, nprob, nitems, grid, rgrid, q, q_count, q_cap, \
-                      item_counter, smem_nodes, stream, ov, round_rays, merges, nmerge
+                      item_counter, smem_nodes, stream, ov, cuts, ncuts, merges, nmerge
     if (mode == MODE_FWD)
         return channels == 4 ? launch_batch_mode<4, MODE_FWD>(TP_BATCH_ARGS)
                              : launch_batch_mode<1, MODE_FWD>(TP_BATCH_ARGS);

@@ -92,7 +92,8 @@ constexpr int kBatchChunk = 8;
 // `grid` CTAs and one resume launch of `rgrid` CTAs.  `smem_nodes`: BVH nodes
 // staged per warp.  With `ov` (its q2 holding q_cap entries) and more than one
 // round, round r's resume runs on ov->aux beside round r + 1's walk.  Rounds
-// hold at most round_rays (<= q_cap) rays; after each round's resume the
+// hold at most q_cap rays: uniform, or the item ranges [cuts[i], cuts[i + 1])
+// (cuts[0] = 0, cuts[ncuts - 1] = nitems); after each round's resume the
 // `nmerge` accumulator merges run (MODE_BWD).  Only stream and event
 // operations (graph-capturable).
 struct ResumeOverlap;
@@ -101,8 +102,8 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
                          int64_t nitems, int channels, int mode, unsigned grid, unsigned rgrid,
                          QEntry *q, unsigned long long *q_count, int64_t q_cap,
                          unsigned *item_counter, int smem_nodes, cudaStream_t stream,
-                         const ResumeOverlap *ov, int64_t round_rays, const AccMerge *merges,
-                         int nmerge);
+                         const ResumeOverlap *ov, const int64_t *cuts, int ncuts,
+                         const AccMerge *merges, int nmerge);
 // Persistent grid for the batched walk: resident CTAs per SM x SM count.
 cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid);
 int device_sm_count();

@@ -207,6 +207,36 @@ def test_batch_several_rounds_and_shared_mesh(tp):
     b1.close()
 
 
+def test_batch_dense_two_level_accumulation(tp):
+    """A dense 4-channel problem (1296 tets, 512 x 512 x 34 rays: ~10^5
+    segments per tet, two rounds of the queue) through the batched launch and
+    a single call: both backprojections use two-level accumulation (FP32
+    reductions merged into FP64 after every round / chunk) and meet the FP32
+    target on sampled tets against the oracle's FP64 sums."""
+    import torch
+    n = 6
+    verts, tets = W.kuhn_cube(n)
+    verts = W.jitter_interior(verts, tets, n, W.rng_for(4, 900))
+    mesh = tp.Mesh(verts, tets)
+    g = W.ConeBeam(4.0, 8.0, 512, 512, 6.4 / 512, 6.4 / 512, W.uniform_angles(34))
+    geo = tp.Geometry.from_cone(g)
+    b = tp.Batch([mesh], [geo], channels=4, tiles=[(16, 8, tp.ORDER_MORTON, tp.SCATTER_ATOMIC)])
+    gen = torch.Generator(device="cuda").manual_seed(17)
+    b.y[0].copy_(torch.rand(b.y[0].shape, device="cuda", generator=gen))
+    b.backward()
+    single = tp.backward(mesh, geo, b.y[0], options=tp.make_options(channels=4, tile=(16, 8)))
+    torch.cuda.synchronize()
+    assert mesh.stats()["error"] == 0
+    rng = np.random.default_rng(19)
+    ts = rng.choice(tets.shape[0], 5, replace=False)
+    want = oracle.backward_cone_subset(verts, tets, b.y[0].double().cpu().numpy().reshape(-1, 4), g, ts)
+    idx = torch.tensor(ts, device="cuda")
+    for got in (b.mu_out[0][idx], single[idx]):
+        got = got.double().cpu().numpy()
+        assert np.all(np.abs(got - want) <= TOL["f32"] * want), np.max(np.abs(got - want) / want)
+    b.close()
+
+
 def test_batch_argument_errors(tp, probs):
     ws, meshes, geos = probs
     with pytest.raises(tp.TetprojError):  # fewer than 32 rays per tile
