@@ -102,7 +102,9 @@ typedef int32_t tetproj_status;
                                       and >= 64 rays per element): the FP32
                                       accumulator is merged into an FP64 one
                                       after every chunk of at most
-                                      max(2^18, 64 nt) rays.  ACC32 keeps it
+                                      max(2^18, 8192 nt / s) rays, s = 1.5
+                                      (nt / 6)^(1/3) + 1 (segments per ray
+                                      estimate).  ACC32 keeps it
                                       single-level.  At most one ACC flag.     */
 
 typedef struct tetproj_mesh tetproj_mesh;
@@ -280,8 +282,8 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
  * scatter choice then does not apply) and into FP32 ones at C = 4, two-level
  * for dense problems (as TETPROJ_FLAG_ACC32 describes; merged after every
  * round).  Rays are processed in rounds of at most 2^23 rays; backprojection
- * rounds are cut further inside dense problems (every max(2^18, 64 nt) of
- * their rays).
+ * rounds are cut further inside dense problems (at most max(2^18,
+ * 8192 nt / s) of their rays per round, as above).
  * Errors: TETPROJ_ERR_ARG (null handle, n < 1, bad channels or tiles),
  * TETPROJ_ERR_TOO_LARGE (2^40 work items or more), CUDA
  * errors of the allocations; *out is NULL on error. */

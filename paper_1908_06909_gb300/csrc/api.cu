@@ -601,9 +601,14 @@ static bool dense_acc(int64_t nt, int channels, int64_t nrays) {
     const int64_t n = nt * channels;
     return n <= (int64_t(1) << 20) && nrays >= 64 * n;
 }
+// Rays per merge interval: about 8192 FP32 reductions per tet, estimating a
+// ray's segments through a compact mesh of nt tets as 1.5 (nt / 6)^(1/3) + 1
+// (a cube of n^3 cells has 6 n^3 tets); at least 2^18 rays.
 static int64_t dense_chunk_rays(int64_t nt) {
-    const int64_t c = 64 * nt;
-    return c < (int64_t(1) << 18) ? (int64_t(1) << 18) : c;
+    const double spr = 1.5 * std::cbrt((double)nt / 6.0) + 1.0;
+    const double c = 8192.0 * (double)nt / spr;
+    return c < (double)(int64_t(1) << 18) ? (int64_t(1) << 18)
+                                          : (c > 1e15 ? (int64_t)1e15 : (int64_t)c);
 }
 
 static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
@@ -1131,21 +1136,28 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
             b->merges.push_back(AccMerge{b->acc32[k], reinterpret_cast<double *>(b->ws_acc[k]),
                                          meshes[k]->nt * channels, 0});
     if (!b->merges.empty()) {
+        // greedy: each round ends at the queue capacity or where a dense
+        // problem would exceed its merge interval inside the round
         const int64_t total = b->item_begin.back();
         const int64_t round_items = (need / (32 * kBatchChunk)) * kBatchChunk;
-        std::vector<int64_t> c;
-        for (int64_t r = 0; r < total; r += round_items) c.push_back(r);
-        for (int k = 0; k < n; ++k) {
-            if (!b->acc32[k]) continue;
-            int64_t step = dense_chunk_rays(meshes[k]->nt) / (32 * kBatchChunk) * kBatchChunk;
-            if (step < kBatchChunk) step = kBatchChunk;
-            for (int64_t i = b->item_begin[k] + step; i < b->item_begin[k + 1]; i += step)
-                c.push_back(i);
+        std::vector<int64_t> step(n, 0);
+        for (int k = 0; k < n; ++k)
+            if (b->acc32[k]) {
+                step[k] = dense_chunk_rays(meshes[k]->nt) / (32 * kBatchChunk) * kBatchChunk;
+                if (step[k] < kBatchChunk) step[k] = kBatchChunk;
+            }
+        for (int64_t r = 0; r < total;) {
+            int64_t e = total - r < round_items ? total : r + round_items;
+            for (int k = 0; k < n; ++k) {
+                const int64_t b0 = b->item_begin[k], b1 = b->item_begin[k + 1];
+                if (!step[k] || b1 <= r || b0 >= e) continue;
+                const int64_t lim = (b0 > r ? b0 : r) + step[k];
+                if (lim < e && lim < b1) e = lim;
+            }
+            b->cuts.push_back(r);
+            r = e;
         }
-        c.push_back(total);
-        std::sort(c.begin(), c.end());
-        c.erase(std::unique(c.begin(), c.end()), c.end());
-        b->cuts = c;
+        b->cuts.push_back(total);
     }
     // launch shapes are fixed here so that forward/backward issue stream work only
     int snodes = 0;
