@@ -170,7 +170,12 @@ tetproj_status tetproj_mesh_destroy(tetproj_mesh *mesh);
 tetproj_status tetproj_mesh_get_info(const tetproj_mesh *mesh, tetproj_mesh_info *out);
 
 /* Allocates the mesh's workspace for (precision, channels) now instead of on
- * the first compute call.  Synchronous. */
+ * the first compute call: operand/accumulator buffers and the deferral queue,
+ * for the filtered path also the FP64 accumulator its backprojection uses by
+ * default at C = 1 (and at C = 4 when nt * 4 <= 2^20).  Calls of more than
+ * 2^23 rays add a second queue and a stream on first use to overlap their
+ * chunks; under CUDA-graph capture they run without them rather than
+ * allocate.  Synchronous. */
 tetproj_status tetproj_mesh_reserve(tetproj_mesh *mesh, int32_t precision, int32_t channels);
 
 /* Host-only topology of a mesh, in the user's tet order (no device needed):

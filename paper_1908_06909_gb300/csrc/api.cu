@@ -315,12 +315,24 @@ static tetproj_status ensure_ws(tetproj_mesh *m, int precision, int channels) {
     return TETPROJ_OK;
 }
 
-// Deferral queue able to hold one launch chunk of up to min(nrays, kQueueMax) rays.
-static tetproj_status ensure_queue(tetproj_mesh *m, int64_t nrays) {
+// True while `s` is being captured into a CUDA graph: no allocation then (a
+// query that fails counts as capturing).
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Deferral queue able to hold one launch chunk of up to min(nrays, kQueueMax)
+// rays; with allow_ov, also the overlap resources when there are several chunks.
+static tetproj_status ensure_queue(tetproj_mesh *m, int64_t nrays, bool allow_ov) {
     int64_t need = nrays < kQueueMax ? nrays : kQueueMax;
     need = ((need + 4095) / 4096) * 4096;
     // the second queue and the auxiliary stream only pay off with several chunks
-    const bool want_ov = nrays > kQueueMax;
+    const bool want_ov = allow_ov && nrays > kQueueMax;
     if (m->q_cap >= need && m->q_count && (!want_ov || m->ov_ready)) return TETPROJ_OK;
     if (m->q_cap < need || !m->q_count) {
         cudaDeviceSynchronize();  // the queues may be in use by earlier calls
@@ -349,7 +361,12 @@ tetproj_status tetproj_mesh_reserve(tetproj_mesh *m, int32_t precision, int32_t 
         (channels != 1 && channels != 4))
         return TETPROJ_ERR_ARG;
     tetproj_status st = ensure_ws(m, precision, channels);
-    if (st == TETPROJ_OK && precision == TETPROJ_FILTERED) st = ensure_queue(m, kQueueMax);
+    if (st == TETPROJ_OK && precision == TETPROJ_FILTERED) st = ensure_queue(m, kQueueMax, false);
+    // the FP64 accumulator the filtered backprojection uses by default at C = 1,
+    // and at C = 4 on meshes small enough to be dense (two-level accumulation)
+    if (st == TETPROJ_OK && precision == TETPROJ_FILTERED &&
+        (channels == 1 || m->nt * channels <= (int64_t(1) << 20)))
+        st = ensure_ws(m, TETPROJ_PLAIN_FP64, channels);
     return st;
 }
 
@@ -550,9 +567,12 @@ static void set_cone(KParams &p, const tetproj_geometry *g) {
     p.nrays = (int64_t)g->na * g->nu * g->nv;
 }
 
-static tetproj_status attach_queue(tetproj_mesh *m, KParams &p, const tetproj_options &o) {
+static tetproj_status attach_queue(tetproj_mesh *m, KParams &p, const tetproj_options &o,
+                                   cudaStream_t s) {
     if (o.precision != TETPROJ_FILTERED) return TETPROJ_OK;
-    tetproj_status st = ensure_queue(m, p.nrays);
+    // under graph capture a call without the overlap resources runs its
+    // chunks on one stream instead of allocating them
+    tetproj_status st = ensure_queue(m, p.nrays, !capturing(s));
     if (st != TETPROJ_OK) return st;
     p.q = m->q;
     p.q_count = m->q_count;
@@ -568,7 +588,7 @@ static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_opt
         if (st != TETPROJ_OK) return st;
     }
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
-    if (st == TETPROJ_OK) st = attach_queue(m, p, o);
+    if (st == TETPROJ_OK) st = attach_queue(m, p, o, s);
     if (st != TETPROJ_OK) return st;
     void *ws = m->ws[o.precision == TETPROJ_PLAIN_FP64][o.channels == 4];
     int f64 = o.precision == TETPROJ_PLAIN_FP64;
@@ -620,7 +640,7 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
     if (use_acc64(o)) {
         // FP32 walk, FP64 accumulator (the plain path's workspace), one rounding at the end
         tetproj_status st = ensure_ws(m, TETPROJ_PLAIN_FP64, o.channels);
-        if (st == TETPROJ_OK) st = attach_queue(m, p, o);
+        if (st == TETPROJ_OK) st = attach_queue(m, p, o, s);
         if (st != TETPROJ_OK) return st;
         void *ws = m->ws[1][o.channels == 4];
         TP_CUDA(cudaMemsetAsync(ws, 0, (size_t)m->ws_bytes[1][o.channels == 4], s));
@@ -633,7 +653,7 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
         return TETPROJ_OK;
     }
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
-    if (st == TETPROJ_OK) st = attach_queue(m, p, o);
+    if (st == TETPROJ_OK) st = attach_queue(m, p, o, s);
     if (st != TETPROJ_OK) return st;
     void *ws = m->ws[o.precision == TETPROJ_PLAIN_FP64][o.channels == 4];
     int f64 = o.precision == TETPROJ_PLAIN_FP64;
@@ -760,7 +780,7 @@ static tetproj_status run_backward_sort(tetproj_mesh *m, const tetproj_geometry 
                                         const tetproj_options &o, const void *y, void *mu_out,
                                         cudaStream_t s) {
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
-    if (st == TETPROJ_OK) st = attach_queue(m, p, o);
+    if (st == TETPROJ_OK) st = attach_queue(m, p, o, s);
     if (st == TETPROJ_OK) st = ensure_plan(m, geo, p, o.channels, s);
     if (st == TETPROJ_OK) st = ensure_sort_ws(m, m->plan.max_chunk, o.channels);
     if (st != TETPROJ_OK) return st;
@@ -890,7 +910,7 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
     p.tr_count = out_count;
     p.max_visits = max_visits;
     if (rstar_unsupported(o)) return TETPROJ_ERR_ARG;
-    st = attach_queue(m, p, o);
+    st = attach_queue(m, p, o, (cudaStream_t)stream);
     if (st != TETPROJ_OK) return st;
     TP_CUDA(launch_walk(p, o.precision, 1, MODE_TRACE, (cudaStream_t)stream));
     return TETPROJ_OK;
@@ -1320,7 +1340,7 @@ extern "C" tetproj_status tetproj_entry(const tetproj_mesh *mesh, const tetproj_
     KParams p = base_params(m, o);
     set_cone(p, geo);
     if (p.entry == ENTRY_RSTAR) st = ensure_rstar(m, p);
-    if (st == TETPROJ_OK) st = attach_queue(m, p, o);
+    if (st == TETPROJ_OK) st = attach_queue(m, p, o, (cudaStream_t)stream);
     if (st != TETPROJ_OK) return st;
     p.tr_count = entry_tet;
     TP_CUDA(launch_walk(p, TETPROJ_FILTERED, 1, MODE_ENTRY, (cudaStream_t)stream));

@@ -367,3 +367,37 @@ def test_backward_fp64_accumulator_c1(tp, c1, C):
     for kw in bad:
         with pytest.raises(tp.TetprojError):
             tp.backward(c1.mesh, c1.geo, yt, options=tp.make_options(channels=C, **kw))
+
+
+def test_single_calls_graph_capture_after_reserve(tp):
+    """A forward projection and a backprojection of a two-chunk scan (> 2^23
+    rays) captured in one CUDA graph on a mesh that only had
+    tetproj_mesh_reserve: nothing is allocated under capture (the chunks run
+    without the overlap stream), and the replay equals eager calls."""
+    import torch
+    n = 6
+    verts, tets = W.kuhn_cube(n)
+    verts = W.jitter_interior(verts, tets, n, W.rng_for(4, 900))
+    mu_np = W.rng_for(4, 901).uniform(0, 1, tets.shape[0])
+    mesh = tp.Mesh(verts, tets)
+    mesh.reserve(tp.FILTERED, 1)
+    g = W.ConeBeam(4.0, 8.0, 512, 512, 6.4 / 512, 6.4 / 512, W.uniform_angles(34))
+    assert g.nrays > 2 ** 23
+    geo = tp.Geometry.from_cone(g)
+    mu = torch.tensor(mu_np, dtype=torch.float32, device="cuda")
+    proj = torch.empty(geo.shape, dtype=torch.float32, device="cuda")
+    back = torch.empty(mesh.nt, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        tp.forward(mesh, geo, mu, out=proj)
+        tp.backward(mesh, geo, proj, out=back)
+    graph.replay()
+    torch.cuda.synchronize()
+    ref_p = tp.forward(mesh, geo, mu)
+    ref_b = tp.backward(mesh, geo, ref_p)
+    torch.cuda.synchronize()
+    assert mesh.stats()["error"] == 0
+    assert torch.equal(proj, ref_p)  # per-ray sums: deterministic
+    assert torch.allclose(back, ref_b, rtol=1e-6, atol=0)  # FP64 accumulators, any order
+    mesh.close()
