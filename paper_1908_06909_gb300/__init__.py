@@ -10,6 +10,19 @@ Operators (Biguri et al., Sec. II-A):
     backward  x_i = sum_j a_ij y_j       (Eq. 3, the exact adjoint)
 with a_ij the length of ray j inside tet i (Eq. 1).  float32 tensors select
 the filtered-precision path, float64 tensors the plain FP64 path.
+
+Example::
+
+    import torch
+    import paper_1908_06909_gb300 as tp
+    from paper_1908_06909_gb300 import solvers
+    mesh = tp.Mesh(vertices, tets)          # numpy (nv, 3) float64, (nt, 4) int
+    geo = tp.Geometry(dso, dsd, nu, nv, du, dv, angles)   # cone beam, radians
+    mu = torch.rand(mesh.nt, device="cuda")               # (nt,) or (nt, 4)
+    proj = tp.forward(mesh, geo, mu)                      # [nangles, nv, nu(, 4)]
+    back = tp.backward(mesh, geo, proj)                   # [nt(, 4)]
+    x = solvers.ossart(mesh, geo, proj, niter=50, block=20)
+    # many problems at once: tp.Batch(meshes, geos, channels=4, tiles=...)
 """
 from __future__ import annotations
 
