@@ -194,17 +194,56 @@ def forward_rays_range(verts, tets, mu, S, P, t0, t1, side=None, threads=None):
 def sos_side_direction():
     """A concrete direction ordered like the symbolic perturbation of the ray
     source (e, e^2, e^4): its sign against a plane normal n is that of the first
-    non-zero component of n (for normals with components not below 1e-6 of the
-    leading one)."""
+    non-zero component of n whenever the components of n are not below 1e-6 of
+    the leading one.  ``forward_rays_exact_planar`` checks that condition, in
+    exact arithmetic, for every plane it uses the direction on."""
     return np.array([1.0, 1e-6, 1e-12])
+
+
+class PlanarSideError(ValueError):
+    """The concrete side direction does not reproduce the symbolic side."""
+
+
+def check_side_direction(normals, w=None):
+    """Raise PlanarSideError unless, for every exact integer plane normal n,
+    n . w has the sign of the first non-zero component of n by more than the
+    FP64 error of the clipper's own n . w.  ``normals`` is a list of integer
+    triples or a dict {normal: kappa} (see exact.face_planes_containing); the
+    clipper's normal is a cross product of FP64 edge vectors, off by at most
+    ~2u kappa |n| per component, and its dot product with w adds ~3u."""
+    from fractions import Fraction as Fr
+    from oracle import exact
+    w = sos_side_direction() if w is None else np.asarray(w, float)
+    wf = [Fr(float(x)) for x in w]
+    wn = float(sum(abs(x) for x in wf))
+    kap = normals if isinstance(normals, dict) else {tuple(n): 1.0 for n in normals}
+    for n, kappa in kap.items():
+        want = exact.sos_side_sign(n)
+        dot = sum(Fr(int(a)) * b for a, b in zip(n, wf))
+        err = 8.0 * 2.0 ** -53 * (kappa + 1.0) * max(abs(int(a)) for a in n) * wn
+        if want == 0 or exact.sign(dot) != want or abs(float(dot)) <= err:
+            raise PlanarSideError(f"side direction {w} does not reproduce the symbolic "
+                                  f"side of the plane with normal {n}")
 
 
 def forward_rays_exact_planar(verts, tets, mu, S, P, threads=None):
     """Integral of rays lying EXACTLY in a face plane, as the limit of the
     symbolically perturbed line S + (e, e^2, e^4), P + (e^8, ...): on [0, 1) the
     line sits on the side of the source perturbation, beyond t = 1 (the point P)
-    on the opposite side."""
-    n = np.asarray(S).shape[0]
+    on the opposite side.  The side is realised by a concrete direction
+    (``sos_side_direction``); every plane containing each ray is found exactly
+    and the direction is checked against the symbolic sign first.  Raises
+    PlanarSideError for a ray in no face plane, or where the direction would
+    pick the wrong side."""
+    from oracle import exact
+    S = np.atleast_2d(np.asarray(S, float))
+    P = np.atleast_2d(np.asarray(P, float))
+    n = S.shape[0]
+    for k in range(n):
+        normals = exact.face_planes_containing(verts, tets, S[k], P[k], return_kappa=True)
+        if not normals:
+            raise PlanarSideError(f"ray {k} lies in no face plane")
+        check_side_direction(normals)
     w = np.broadcast_to(sos_side_direction(), (n, 3)).copy()
     a = forward_rays_range(verts, tets, mu, S, P, 0.0, 1.0, side=w, threads=threads)
     b = forward_rays_range(verts, tets, mu, S, P, 1.0, np.inf, side=-w, threads=threads)

@@ -271,29 +271,44 @@ class DegenerateRay(ValueError):
     """The ray meets an edge or vertex exactly: crossing faces are not unique."""
 
 
+def _bbox_candidates(V, S, P, pad, half_line):
+    """Indices of tets whose padded bounding box meets the line S + t (P - S)
+    (t >= 0 only when half_line).  A coarse float filter: pad widens every box
+    so that rounding in the slab test cannot drop a tet the line touches."""
+    import numpy as np
+    d = P - S
+    lo = V.min(axis=1) - pad
+    hi = V.max(axis=1) + pad
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        inv = np.where(d != 0, 1.0 / np.where(d != 0, d, 1.0), np.inf)
+        t1 = (lo - S) * inv
+        t2 = (hi - S) * inv
+    tmin = np.where(d != 0, np.minimum(t1, t2), np.where((S >= lo) & (S <= hi), -np.inf, np.inf))
+    tmax = np.where(d != 0, np.maximum(t1, t2), np.where((S >= lo) & (S <= hi), np.inf, -np.inf))
+    keep = tmin.max(axis=1) <= tmax.min(axis=1) * (1 + 1e-12) + 1e-12
+    if half_line:
+        keep &= tmax.min(axis=1) >= -1e-12
+    return np.nonzero(keep)[0]
+
+
 def ray_integral_exact(verts, tets, mu, S, P, pad=1e-9):
     """Exact sum_i a_ij mu_i for one ray (Eq. 2) with a_ij from exact integer
     arithmetic: each tet's crossing points come from barycentric weights given
     by exact side products (as in plucker_interval), clipped to t >= 0.  Only
-    tets whose bounding box meets the ray (padded) are examined.  Raises
-    DegenerateRay if a crossing is not unique (a zero side product on a crossed
-    face).  Returns a float (the exact rational sum, rounded)."""
+    tets whose bounding box meets the ray (padded by ``pad``) are examined;
+    ``pad=None`` examines every tet (used to check that the filter drops none).
+    Raises DegenerateRay if a crossing is not unique (a zero side product on a
+    crossed face).  Returns a float (the exact rational sum, rounded)."""
     import math
     import numpy as np
     S = np.asarray(S, float)
     P = np.asarray(P, float)
     d = P - S
     V = np.asarray(verts, float)[np.asarray(tets)]          # [nt, 4, 3]
-    lo = V.min(axis=1) - pad
-    hi = V.max(axis=1) + pad
-    with np.errstate(divide="ignore", invalid="ignore"):
-        inv = np.where(d != 0, 1.0 / np.where(d != 0, d, 1.0), np.inf)
-        t1 = (lo - S) * inv
-        t2 = (hi - S) * inv
-    tmin = np.where(d != 0, np.minimum(t1, t2), np.where((S >= lo) & (S <= hi), -np.inf, np.inf))
-    tmax = np.where(d != 0, np.maximum(t1, t2), np.where((S >= lo) & (S <= hi), np.inf, -np.inf))
-    cand = np.nonzero((tmin.max(axis=1) <= tmax.min(axis=1) * (1 + 1e-12) + 1e-12) &
-                      (tmax.min(axis=1) >= -1e-12))[0]
+    if pad is None:
+        cand = np.arange(V.shape[0])
+    else:
+        cand = _bbox_candidates(V, S, P, pad, half_line=True)
     # common integer scaling of every coordinate involved
     vals = list(S) + list(P) + list(V[cand].reshape(-1))
     I = _int_scale([float(x) for x in vals])
@@ -343,31 +358,33 @@ def ray_integral_exact(verts, tets, mu, S, P, pad=1e-9):
     return float(total) * math.sqrt(float(d @ d))
 
 
-def ray_in_face_plane(verts, tets, S, P, pad=1e-9):
-    """True if the line S->P lies exactly in the plane of a face of a tet whose
-    bounding box it meets (exact integer orientation tests)."""
+def _int_det(a, b, c):
+    return (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
+            + a[2] * (b[0] * c[1] - b[1] * c[0]))
+
+
+def face_planes_containing(verts, tets, S, P, pad=1e-9, return_kappa=False):
+    """Normals of the face planes that contain the line S->P exactly.
+
+    Exact integer orientation tests over the tets whose (padded) bounding box
+    meets the line.  Each normal is the integer triple (b - a) x (c - a) of the
+    face's vertices on a common integer grid, divided by the gcd of its
+    components, with a positive first non-zero component, so its components
+    (their signs and ratios) are exact; faces in one plane give one normal.
+    With ``return_kappa`` a dict {normal: kappa} is returned instead, kappa the
+    largest |b - a| |c - a| / |(b - a) x (c - a)| over the plane's faces: the
+    factor by which rounding in an FP64 cross product of those edges can exceed
+    u |normal|."""
+    import math
     import numpy as np
     S = np.asarray(S, float)
     P = np.asarray(P, float)
     V = np.asarray(verts, float)[np.asarray(tets)]
-    lo = V.min(axis=1) - pad
-    hi = V.max(axis=1) + pad
-    d = P - S
-    with np.errstate(divide="ignore", invalid="ignore"):
-        inv = np.where(d != 0, 1.0 / np.where(d != 0, d, 1.0), np.inf)
-        t1 = (lo - S) * inv
-        t2 = (hi - S) * inv
-    tmin = np.where(d != 0, np.minimum(t1, t2), np.where((S >= lo) & (S <= hi), -np.inf, np.inf))
-    tmax = np.where(d != 0, np.maximum(t1, t2), np.where((S >= lo) & (S <= hi), np.inf, -np.inf))
-    cand = np.nonzero(tmin.max(axis=1) <= tmax.min(axis=1) * (1 + 1e-12) + 1e-12)[0]
+    cand = _bbox_candidates(V, S, P, pad, half_line=False)
     vals = list(S) + list(P) + list(V[cand].reshape(-1))
     I = _int_scale([float(x) for x in vals])
     Si, Pi = I[0:3], I[3:6]
-
-    def det(a, b, c):
-        return (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
-                + a[2] * (b[0] * c[1] - b[1] * c[0]))
-
+    out = {}
     for q in range(cand.size):
         base = 6 + 12 * q
         v = [I[base + 3 * k: base + 3 * k + 3] for k in range(4)]
@@ -375,7 +392,35 @@ def ray_in_face_plane(verts, tets, S, P, pad=1e-9):
             a, b, c = [v[k] for k in range(4) if k != f]
             e1 = [b[m] - a[m] for m in range(3)]
             e2 = [c[m] - a[m] for m in range(3)]
-            if det(e1, e2, [Si[m] - a[m] for m in range(3)]) == 0 and \
-                    det(e1, e2, [Pi[m] - a[m] for m in range(3)]) == 0:
-                return True
-    return False
+            if _int_det(e1, e2, [Si[m] - a[m] for m in range(3)]) == 0 and \
+                    _int_det(e1, e2, [Pi[m] - a[m] for m in range(3)]) == 0:
+                n = [e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                     e1[0] * e2[1] - e1[1] * e2[0]]
+                kappa = math.sqrt(float(sum(x * x for x in e1)) * float(sum(x * x for x in e2))
+                                  / float(sum(x * x for x in n)))
+                g = math.gcd(math.gcd(abs(n[0]), abs(n[1])), abs(n[2]))
+                n = [x // g for x in n]
+                lead = next(x for x in n if x != 0)
+                if lead < 0:
+                    n = [-x for x in n]
+                key = tuple(n)
+                out[key] = max(out.get(key, 0.0), kappa)
+    if return_kappa:
+        return out
+    return sorted(out)
+
+
+def ray_in_face_plane(verts, tets, S, P, pad=1e-9):
+    """True if the line S->P lies exactly in the plane of a face of a tet whose
+    bounding box it meets (exact integer orientation tests)."""
+    return len(face_planes_containing(verts, tets, S, P, pad)) > 0
+
+
+def sos_side_sign(n) -> int:
+    """Sign of n . (e, e^2, e^4) as e -> 0+: the sign of the first non-zero
+    component of n.  This is the side of a plane with normal n that the
+    symbolically perturbed source S + (e, e^2, e^4) lies on."""
+    for x in n:
+        if x != 0:
+            return 1 if x > 0 else -1
+    return 0
