@@ -232,17 +232,25 @@ tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry
                                 void *stream);
 
 /* tetproj_backward without any allocation.  It computes the same x = A^T y as
- * tetproj_backward (same arguments and layouts), for callers that cannot call
- * cudaMalloc when they backproject: code whose device memory is wholly owned by
- * another allocator (e.g. a framework's caching pool that has reserved the
- * device), or a latency-critical loop that must not pay cudaMalloc's implicit
- * synchronisation.  The paper has no counterpart; this is a library facility.
+ * tetproj_backward (same arguments, layouts, options and accumulator: FP64 at
+ * C = 1 on the filtered path unless TETPROJ_FLAG_ACC32, two-level FP32 -> FP64
+ * for dense problems at C = 4, FP32 otherwise, FP64 on the plain path), for
+ * callers that cannot call cudaMalloc when they backproject: code whose device
+ * memory is wholly owned by another allocator (e.g. a framework's caching pool
+ * that has reserved the device), or a latency-critical loop that must not pay
+ * cudaMalloc's implicit synchronisation.  The paper has no counterpart; this
+ * is a library facility.  TETPROJ_SCATTER_SORT is not offered
+ * (TETPROJ_ERR_ARG): its buffers grow with the number of segments.
  * Its scratch (accumulator and deferral queue) is a fixed device array inside
  * the library, present on every GPU that loads it until the process exits:
- *   - limit: nt * C * sizeof(element) <= TETPROJ_NOALLOC_ACC_BYTES, else
- *     TETPROJ_ERR_TOO_LARGE (e.g. FP32, C = 1: up to 8,388,608 tets);
- *   - the first call on a device looks up the array's device address (no
- *     allocation); make that first call before any stream capture;
+ *   - limit: the accumulator must fit TETPROJ_NOALLOC_ACC_BYTES, else
+ *     TETPROJ_ERR_TOO_LARGE: nt * C * 8 bytes with an FP64 accumulator (the
+ *     filtered C = 1 default: up to 4,194,304 tets; plain FP64), nt * C * 4
+ *     with FP32 (C = 4 sparse problems, TETPROJ_FLAG_ACC32), and 12 nt C for
+ *     the dense two-level case (always fits: dense means nt C <= 2^20);
+ *   - the first call on a device (and the first after that device's context
+ *     was destroyed and created again) looks up the array's device address
+ *     (no allocation); make that first call before any stream capture;
  *   - all calls share the array and it keeps the last call's contents (each
  *     call clears what must start at zero); calls that overlap on the GPU
  *     (unordered streams) race on it. */
@@ -308,6 +316,18 @@ tetproj_status tetproj_batch_bind(tetproj_batch *b, const void *const *mu, void 
 tetproj_status tetproj_batch_forward(tetproj_batch *b, void *stream);
 tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream);
 tetproj_status tetproj_batch_destroy(tetproj_batch *b);
+/* The persistent launch hands work to the warps of a CTA through two waits on
+ * shared-memory words that other warps of the CTA write (this build's work
+ * queue, not the paper's).  Each wait gives up after a bounded number of polls
+ * (2^22, tens of milliseconds): the call then completes with incomplete
+ * results and the mesh statistics report TETPROJ_ERR_TIMEOUT, and the context
+ * stays usable.  This sets the bound for later calls of this batch (a CUDA
+ * graph keeps the value it was captured with): max_polls > 0 polls, 0 the
+ * default.  never_satisfied != 0 makes every wait wait for a value no warp
+ * writes, so each runs out after max_polls polls: a test of the timeout path,
+ * not for production use.  Errors: TETPROJ_ERR_ARG (null batch, max_polls < 0). */
+tetproj_status tetproj_batch_set_wait(tetproj_batch *b, int32_t max_polls,
+                                      int32_t never_satisfied);
 
 /* ------------------------------------------------- the paper's own walk --
  * Alg. 1 and 2 as printed (Sec. II-C..E): Moller-Trumbore ray-triangle tests

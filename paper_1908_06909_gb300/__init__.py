@@ -475,6 +475,13 @@ class Batch:
         check(_lib.load().tetproj_batch_backward(self._h, _stream()), "tetproj_batch_backward")
         return self.mu_out
 
+    def set_wait(self, max_polls: int = 0, never_satisfied: bool = False):
+        """tetproj_batch_set_wait: the poll bound of the persistent kernel's
+        inter-warp waits (0: the default); never_satisfied makes every wait run
+        out (a test of the timeout path)."""
+        check(_lib.load().tetproj_batch_set_wait(self._h, int(max_polls), int(bool(never_satisfied))),
+              "tetproj_batch_set_wait")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().tetproj_batch_destroy(self._h)

@@ -92,6 +92,7 @@ SIGNATURES = {
     "tetproj_batch_bind": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tetproj_batch_forward": (c_i32, [c_vp, c_vp]),
     "tetproj_batch_backward": (c_i32, [c_vp, c_vp]),
+    "tetproj_batch_set_wait": (c_i32, [c_vp, c_i32, c_i32]),
     "tetproj_batch_destroy": (c_i32, [c_vp]),
     "tetproj_forward_mt": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tetproj_forward_rays_mt": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),

@@ -3,6 +3,7 @@
 // Host-side glue only: argument checks, ownership of device memory, the
 // user-order <-> Hilbert-order permutations around each walk, and launch
 // configuration.  Every step of the projection itself runs in kernels.cu.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -941,46 +942,90 @@ tetproj_status tetproj_side_device(const double *S, const double *P, const doubl
 
 // ------------------------------------------------ allocation-free backprojection
 //
-// tetproj_backward_noalloc computes exactly what tetproj_backward computes, for
-// callers that cannot call cudaMalloc at that point -- for instance code whose
-// device memory is entirely owned by another allocator (a framework's caching
-// pool that has already reserved the device), or a latency-critical loop that
-// must not pay cudaMalloc's implicit device synchronisation.  tetproj_backward
+// tetproj_backward_noalloc computes what tetproj_backward computes, with the
+// same accumulator (FP64 at C = 1 on the filtered path, two-level FP32 -> FP64
+// for dense problems, FP32 otherwise, FP64 on the plain path), for callers
+// that cannot call cudaMalloc at that point -- for instance code whose device
+// memory is entirely owned by another allocator (a framework's caching pool
+// that has already reserved the device), or a latency-critical loop that must
+// not pay cudaMalloc's implicit device synchronisation.  tetproj_backward
 // allocates the mesh's workspace on its first call; this variant instead uses
 // the file-scope device array below, so it never allocates or frees anything.
 //
-// Its scratch is the tet-ordered accumulator (up to kNoAllocAccBytes) and the
-// deferral queue of the filtered walk (kNoAllocQueue entries; launches are
+// Its scratch is the tet-ordered accumulator (up to kNoAllocAccBytes; the
+// two-level case holds the FP32 and the FP64 accumulator side by side) and
+// the deferral queue of the filtered walk (kNoAllocQueue entries; launches are
 // chunked to fit it).  The array is part of the library image, so every GPU
 // that loads libtetproj.so holds it (48 MB) until the process exits.
 // Every call shares it and it keeps the previous call's contents: the
-// accumulator is cleared at the start of each call, and calls that overlap on
-// the GPU (different streams, no ordering) race on it.
-static const int64_t kNoAllocAccBytes = int64_t(32) << 20;
+// accumulators are cleared at the start of each call, and calls that overlap
+// on the GPU (different streams, no ordering) race on it.
+static const int64_t kNoAllocAccBytes = TETPROJ_NOALLOC_ACC_BYTES;
+static_assert(kNoAllocAccBytes % 256 == 0, "accumulator region keeps the queue 256-byte aligned");
 static const int64_t kNoAllocQueue = int64_t(1) << 18;
 static const int64_t kNoAllocBytes = kNoAllocAccBytes + kNoAllocQueue * (int64_t)sizeof(QEntry) + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 static std::mutex g_noalloc_mutex;
-static void *g_noalloc_addr[128] = {nullptr};
+struct NoAllocAddr {
+    void *addr;
+    unsigned long long ctx;  // cuCtxGetId of the context the address belongs to; 0 unknown
+};
+static NoAllocAddr g_noalloc_addr[128] = {};
+
+// Unique id of the calling thread's current CUDA context (0 when there is none
+// or the driver does not export the query).  Resolved through the runtime's
+// driver entry points, so the library does not link libcuda itself.
+static unsigned long long current_context_id() {
+    typedef CUresult (*GetCurrentFn)(CUcontext *);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetIdFn>(f);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of the scratch array on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached together with the id of the
+// context it belongs to.  A new context on the device (after cudaDeviceReset,
+// or a primary context released and created again) reloads the module, so the
+// address is looked up again when the id changes; when the id cannot be read
+// it is looked up on every call.
 static tetproj_status noalloc_scratch(unsigned char **out) {
     int dev = 0;
     TP_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 128) return TETPROJ_ERR_TOO_LARGE;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    NoAllocAddr &slot = g_noalloc_addr[dev];
+    const unsigned long long ctx = current_context_id();
+    if (!slot.addr || ctx == 0 || ctx != slot.ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
-        g_noalloc_addr[dev] = p;
+        slot.addr = p;
+        slot.ctx = current_context_id();  // the lookup makes the primary context current
     }
-    *out = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    *out = static_cast<unsigned char *>(slot.addr);
     return TETPROJ_OK;
 }
+
+static int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
 
 extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
                                                    const tetproj_geometry *geo, const void *proj,
@@ -989,30 +1034,55 @@ extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
     if (!mesh || !geo || !proj || !mu_out) return TETPROJ_ERR_ARG;
     tetproj_options o;
     tetproj_status st = check_opts(opt, o);
-    if (st == TETPROJ_OK && (o.scatter == TETPROJ_SCATTER_SORT || o.flags != 0))
-        st = TETPROJ_ERR_ARG;  // FP32 atomics into the fixed scratch only
     if (st != TETPROJ_OK) return st;
+    // the sort-and-reduce scatter needs buffers sized by the segment count
+    if (o.scatter == TETPROJ_SCATTER_SORT || rstar_unsupported(o)) return TETPROJ_ERR_ARG;
+    if ((o.flags & TETPROJ_FLAG_ACC64) && o.precision == TETPROJ_FILTERED &&
+        o.scatter != TETPROJ_SCATTER_ATOMIC)
+        return TETPROJ_ERR_ARG;  // FP64 accumulation is an atomic-scatter variant
     const int f64 = o.precision == TETPROJ_PLAIN_FP64;
-    const int64_t acc_bytes = mesh->nt * o.channels * (f64 ? 8 : 4);
-    if (acc_bytes > kNoAllocAccBytes) return TETPROJ_ERR_TOO_LARGE;
+    KParams p = base_params(mesh, o);
+    set_cone(p, geo);
+    // the accumulator tetproj_backward would use
+    const int64_t n = mesh->nt * o.channels;
+    const bool acc64 = use_acc64(o);
+    const bool two_level = !f64 && !acc64 && !(o.flags & TETPROJ_FLAG_ACC32) &&
+                           dense_acc(mesh->nt, o.channels, p.nrays);
+    const int64_t off64 = two_level ? align256(4 * n) : 0;
+    const int64_t need = (f64 || acc64) ? 8 * n : (two_level ? off64 + 8 * n : 4 * n);
+    if (need > kNoAllocAccBytes) return TETPROJ_ERR_TOO_LARGE;
     unsigned char *base = nullptr;
     st = noalloc_scratch(&base);
     if (st != TETPROJ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    KParams p = base_params(mesh, o);
-    set_cone(p, geo);
-    void *acc = base;
     if (!f64) {
         p.q = reinterpret_cast<QEntry *>(base + kNoAllocAccBytes);
         p.q_count = reinterpret_cast<unsigned long long *>(
             base + kNoAllocAccBytes + kNoAllocQueue * (int64_t)sizeof(QEntry));
         p.q_cap = kNoAllocQueue;
     }
-    TP_CUDA(cudaMemsetAsync(acc, 0, (size_t)acc_bytes, s));
     p.in = proj;
-    p.out = acc;
-    TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s));
-    TP_CUDA(launch_scatter_perm(mesh->perm, mesh->nt, o.channels, f64, acc, mu_out, s));
+    p.out = base;
+    TP_CUDA(cudaMemsetAsync(base, 0, (size_t)need, s));
+    if (f64) {
+        TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s));
+        TP_CUDA(launch_scatter_perm(mesh->perm, mesh->nt, o.channels, 1, base, mu_out, s));
+    } else if (acc64) {
+        TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD64, s));
+        TP_CUDA(launch_scatter_perm_d2f(mesh->perm, mesh->nt, o.channels,
+                                        reinterpret_cast<const double *>(base),
+                                        reinterpret_cast<float *>(mu_out), s));
+    } else if (two_level) {
+        AccMerge mg{reinterpret_cast<float *>(base), reinterpret_cast<double *>(base + off64), n,
+                    dense_chunk_rays(mesh->nt)};
+        TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s, nullptr, &mg));
+        TP_CUDA(launch_scatter_perm_d2f(mesh->perm, mesh->nt, o.channels,
+                                        reinterpret_cast<const double *>(base + off64),
+                                        reinterpret_cast<float *>(mu_out), s));
+    } else {
+        TP_CUDA(launch_walk(p, o.precision, o.channels, MODE_BWD, s));
+        TP_CUDA(launch_scatter_perm(mesh->perm, mesh->nt, o.channels, 0, base, mu_out, s));
+    }
     return TETPROJ_OK;
 }
 
@@ -1053,6 +1123,7 @@ struct tetproj_batch {
     std::vector<float *> acc32;   // per problem, null unless dense
     std::vector<AccMerge> merges; // the dense problems' merges
     std::vector<int64_t> cuts;    // backprojection rounds (item boundaries; empty: uniform)
+    BatchWait wait{kBatchWaitPolls, 0};  // bounded waits of the persistent kernel
 };
 
 static void batch_free(tetproj_batch *b) {
@@ -1238,7 +1309,8 @@ extern "C" tetproj_status tetproj_batch_forward(tetproj_batch *b, void *stream) 
                                    b->ws_in[k], s));
     TP_CUDA(launch_batch(b->d_fwd, b->d_item_begin, b->n, b->item_begin.back(),
                          b->channels, MODE_FWD, b->grid_fwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
-                         b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr, nullptr, 0, nullptr, 0));
+                         b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr, nullptr, 0, nullptr, 0,
+                         b->wait));
     return TETPROJ_OK;
 }
 
@@ -1256,7 +1328,8 @@ extern "C" tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream)
                          b->channels, b->acc64 ? MODE_BWD64 : MODE_BWD, b->grid_bwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
                          b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr,
                          b->cuts.empty() ? nullptr : b->cuts.data(), (int)b->cuts.size(),
-                         b->merges.empty() ? nullptr : b->merges.data(), (int)b->merges.size()));
+                         b->merges.empty() ? nullptr : b->merges.data(), (int)b->merges.size(),
+                         b->wait));
     for (int k = 0; k < b->n; ++k) {
         if (b->acc64 || b->acc32[k])
             TP_CUDA(launch_scatter_perm_d2f(b->meshes[k]->perm, b->meshes[k]->nt, b->channels,
@@ -1266,6 +1339,14 @@ extern "C" tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream)
             TP_CUDA(launch_scatter_perm(b->meshes[k]->perm, b->meshes[k]->nt, b->channels, 0,
                                         b->ws_acc[k], b->mu_out[k], s));
     }
+    return TETPROJ_OK;
+}
+
+extern "C" tetproj_status tetproj_batch_set_wait(tetproj_batch *b, int32_t max_polls,
+                                                 int32_t never_satisfied) {
+    if (!b || max_polls < 0) return TETPROJ_ERR_ARG;
+    b->wait.limit = max_polls == 0 ? kBatchWaitPolls : max_polls;
+    b->wait.offset = never_satisfied ? (1 << 30) : 0;
     return TETPROJ_OK;
 }
 

@@ -1066,7 +1066,6 @@ static int sm_count() {
 #define TP_BATCH_TAG_SHIFT 40
 #define TP_BATCH_THREADS 128
 #define TP_BATCH_RING 4
-#define TP_BATCH_SPIN_LIMIT (1 << 22)
 
 #ifndef TP_BATCH_MIN_BLOCKS
 #define TP_BATCH_MIN_BLOCKS 8
@@ -1074,10 +1073,12 @@ static int sm_count() {
 
 constexpr int kBatchParamVec = (int)((sizeof(KParams) + 15) / 16);
 
-// bounded wait for *a == v on a shared-memory word written by another warp
-__device__ __forceinline__ bool batch_wait_eq(volatile int *a, int v) {
-    for (int i = 0; i < TP_BATCH_SPIN_LIMIT; ++i) {
-        if (*a == v) return true;
+// bounded wait for *a == v on a shared-memory word written by another warp:
+// at most `limit` polls.  A test of the timeout path passes a non-zero
+// `offset`, so that the awaited value is one no warp ever writes.
+__device__ __forceinline__ bool batch_wait_eq(volatile int *a, int v, BatchWait w) {
+    for (int i = 0; i < w.limit; ++i) {
+        if (*a == v + w.offset) return true;
         __nanosleep(32);
     }
     return false;
@@ -1087,7 +1088,7 @@ template <int C, int MODE>
 __global__ void __launch_bounds__(TP_BATCH_THREADS, TP_BATCH_MIN_BLOCKS)
     k_batch32(const BatchProblem *__restrict__ probs, const int64_t *__restrict__ item_begin,
               int nprob, int64_t round_begin, int64_t round_end, unsigned *chunk_counter,
-              int nsm_max, QEntry *q, unsigned long long *q_count) {
+              int nsm_max, QEntry *q, unsigned long long *q_count, BatchWait wait) {
     extern __shared__ float4 smem[];
     __shared__ unsigned s_ticket;
     __shared__ long long s_base[TP_BATCH_RING];
@@ -1117,7 +1118,7 @@ __global__ void __launch_bounds__(TP_BATCH_THREADS, TP_BATCH_MIN_BLOCKS)
             bool ok = true;
             if (o == 0) {
                 // claim chunk c: wait until slot r's previous chunk is fully read
-                ok = batch_wait_eq(&s_used[r], kBatchChunk);
+                ok = batch_wait_eq(&s_used[r], kBatchChunk, wait);
                 if (ok) {
                     s_used[r] = 0;
                     const unsigned g = atomicAdd(chunk_counter, 1u);
@@ -1126,7 +1127,7 @@ __global__ void __launch_bounds__(TP_BATCH_THREADS, TP_BATCH_MIN_BLOCKS)
                     *(volatile int *)&s_gen[r] = c;
                 }
             }
-            if (ok) ok = batch_wait_eq(&s_gen[r], c);
+            if (ok) ok = batch_wait_eq(&s_gen[r], c, wait);
             if (ok) {
                 __threadfence_block();
                 it = *(volatile long long *)&s_base[r] + o;
@@ -1232,7 +1233,8 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
                                      int64_t q_cap, unsigned *item_counter,
                                      int smem_nodes, cudaStream_t stream,
                                      const ResumeOverlap *ov, const int64_t *cuts,
-                                     int ncuts, const AccMerge *merges, int nmerge) {
+                                     int ncuts, const AccMerge *merges, int nmerge,
+                                     BatchWait wait) {
     // rounds of warp items (32 rays each), at most q_cap rays: uniform, or
     // [cuts[i], cuts[i + 1]) when cuts are given
     if (nmerge > 0 && MODE != MODE_BWD) return cudaErrorInvalidValue;
@@ -1276,7 +1278,7 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
             if (e == cudaSuccess) e = cudaMemsetAsync(cj, 0, sizeof(unsigned long long), stream);
             if (e != cudaSuccess) break;
             k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
-                probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, qj, cj);
+                probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, qj, cj, wait);
             note_launch();
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaEventRecord(ov->ev_fast[j], stream);
@@ -1300,7 +1302,7 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
         if (e == cudaSuccess) e = cudaMemsetAsync(q_count, 0, sizeof(unsigned long long), stream);
         if (e != cudaSuccess) return e;
         k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
-            probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, q, q_count);
+            probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, q, q_count, wait);
         note_launch();
         k_batch_resume32<C, MODE><<<rgrid, 128, 0, stream>>>(probs, q, q_count, q_cap);
         note_launch();
@@ -1316,11 +1318,12 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
                          unsigned rgrid, QEntry *q, unsigned long long *q_count, int64_t q_cap,
                          unsigned *item_counter, int smem_nodes, cudaStream_t stream,
                          const ResumeOverlap *ov, const int64_t *cuts, int ncuts,
-                         const AccMerge *merges, int nmerge) {
+                         const AccMerge *merges, int nmerge, BatchWait wait) {
     if (nitems <= 0) return cudaSuccess;
+    if (wait.limit < 1) return cudaErrorInvalidValue;
     if (grid < 1 || rgrid < 1) return cudaErrorInvalidValue;
 #define TP_BATCH_ARGS probs, item_begin, nprob, nitems, grid, rgrid, q, q_count, q_cap, \
-                      item_counter, smem_nodes, stream, ov, cuts, ncuts, merges, nmerge
+                      item_counter, smem_nodes, stream, ov, cuts, ncuts, merges, nmerge, wait
     if (mode == MODE_FWD)
         return channels == 4 ? launch_batch_mode<4, MODE_FWD>(TP_BATCH_ARGS)
                              : launch_batch_mode<1, MODE_FWD>(TP_BATCH_ARGS);

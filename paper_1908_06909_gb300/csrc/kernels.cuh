@@ -98,12 +98,21 @@ constexpr int kBatchChunk = 8;
 // operations (graph-capturable).
 struct ResumeOverlap;
 struct AccMerge;
+// The bounded waits between the warps of a batched CTA: at most `limit` polls
+// each (kBatchWaitPolls by default), then TETPROJ_ERR_TIMEOUT and the warp
+// stops.  A non-zero `offset` makes every wait wait for a value no warp
+// writes (a test of the timeout path).
+struct BatchWait {
+    int limit;
+    int offset;
+};
+constexpr int kBatchWaitPolls = 1 << 22;
 cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, int nprob,
                          int64_t nitems, int channels, int mode, unsigned grid, unsigned rgrid,
                          QEntry *q, unsigned long long *q_count, int64_t q_cap,
                          unsigned *item_counter, int smem_nodes, cudaStream_t stream,
                          const ResumeOverlap *ov, const int64_t *cuts, int ncuts,
-                         const AccMerge *merges, int nmerge);
+                         const AccMerge *merges, int nmerge, BatchWait wait);
 // Persistent grid for the batched walk: resident CTAs per SM x SM count.
 cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid);
 int device_sm_count();

@@ -281,3 +281,37 @@ def test_autotune_batch_and_cache(tp, probs, tmp_path):
         single = tp.forward(meshes[k], geos[k], b.mu[k], options=_single_opts(tp, choices[k].row(), 4))
         assert torch.equal(b.proj[k], single)
     b.close()
+
+
+def test_batch_bounded_wait_times_out_and_recovers(tp, probs):
+    """The persistent kernel's inter-warp waits are bounded.  Made to wait for a
+    value no warp writes (a test-only setting), every wait runs out after 16
+    polls: the launch still completes, the statistics report
+    TETPROJ_ERR_TIMEOUT, and the next call with the default bound succeeds and
+    equals the single-problem calls."""
+    import torch
+    ws, meshes, geos = probs
+    ms, gs, wk = meshes[:3], geos[:3], ws[:3]
+    b = tp.Batch(ms, gs, channels=4)
+    for k in range(3):
+        b.mu[k].copy_(torch.tensor(wk[k].mu, dtype=torch.float32))
+    for m in ms:
+        m.stats_reset()
+    b.set_wait(max_polls=16, never_satisfied=True)
+    b.forward()
+    torch.cuda.synchronize()
+    errs = [m.stats()["error"] for m in ms]
+    assert tp._lib.ERR_TIMEOUT in errs and all(e in (0, tp._lib.ERR_TIMEOUT) for e in errs), errs
+    with pytest.raises(tp.TetprojError):
+        b.set_wait(max_polls=-1)
+    b.set_wait()  # the default bound
+    for m in ms:
+        m.stats_reset()
+    b.proj[0].zero_()
+    b.forward()
+    torch.cuda.synchronize()
+    assert all(m.stats()["error"] == 0 for m in ms)
+    for k in range(3):
+        single = tp.forward(ms[k], gs[k], b.mu[k], options=tp.make_options(channels=4))
+        assert torch.equal(single, b.proj[k])
+    b.close()
