@@ -20,7 +20,7 @@ import pytest
 import oracle
 import workloads as W
 
-from test_gpu_parity import TOL, floor_abs, planar_reference
+from test_gpu_parity import TOL, check_rays, floor_abs, planar_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -124,10 +124,10 @@ def test_batch_matches_single_calls_and_oracle(tp, probs, threads):
         planar = planar_all[k][idx]
         ref, skipped = _reference_channels(w, S, P, want, planar)
         got = b.proj[k].reshape(-1, 4)[torch.tensor(idx, device="cuda")].double().cpu().numpy()
-        ok = np.ones(idx.size, bool)
-        ok[skipped] = False
         fl = floor_abs("f32", w.verts, w.mu)
-        assert np.all((np.abs(got - ref) <= TOL["f32"] * scale + fl)[ok]), k
+        for c in range(4):
+            check_rays(f"batch problem {k} channel {c}", got[:, c], ref[:, c], scale[:, c],
+                       TOL["f32"], fl, skipped, max_floor_frac=0.05)
         # sampled tets against the oracle's backprojection of the same y
         y = b.y[k].double().cpu().numpy().reshape(-1, 4)
         tets = rng.choice(w.tets.shape[0], min(8, w.tets.shape[0]), replace=False)
@@ -195,8 +195,8 @@ def test_batch_several_rounds_and_shared_mesh(tp):
     got = b.proj[0].reshape(-1)[torch.tensor(idx, device="cuda")].double().cpu().numpy()
     S, P = oracle.cone_rays(g_big, idx)
     _, _, _, _, _, planar = oracle.trace_rays(verts, tets, S, P, max_visits=2)
-    ok = ~planar
-    assert np.all((np.abs(got - want) <= TOL["f32"] * scale + floor_abs("f32", verts, mu))[ok])
+    check_rays("batch several rounds", got, want, scale, TOL["f32"], floor_abs("f32", verts, mu),
+               np.nonzero(planar)[0], max_floor_frac=0.05)
     # a one-problem batch
     b1 = tp.Batch([mesh], geos[1:], channels=1, tiles=tiles[1:])
     b1.mu[0].copy_(b.mu[1])
