@@ -1,8 +1,7 @@
 #!/usr/bin/env python
-"""Benchmark: forward + back projection on the jittered Kuhn 96^3 workload
-(default), or on the batched workload (--workload batch24: 24 problems of
-uneven size, 4 channels, one persistent launch per direction under a CUDA
-graph).
+"""Benchmark: forward + back projection on the jittered Kuhn 96^3 workload,
+with the batched workload (24 problems of uneven size, 4 channels, one
+persistent launch per direction under a CUDA graph) nested in the same line.
 
 One step = tetproj_forward (b = A mu) followed by tetproj_backward of that
 projection (x = A^T b): 512 x 512 x 360 = 94,371,840 cone-beam rays through
@@ -10,9 +9,17 @@ projection (x = A^T b): 512 x 512 x 360 = 94,371,840 cone-beam rays through
 device (inputs resident in HBM); `e2e` is the same through the C ABI with host
 buffers (pinned H2D of mu, D2H of the projection and the backprojection every
 step).  The filtered FP32 path is the product; the plain FP64 path is timed
-beside it for the ratio.  Under torchrun every rank runs an independent
-replica (the operator shards over rays with no exchange in the forward; this
-build has no cross-GPU step), so value = all ranks' rays / max time.
+beside it for the ratio, with its FP64-ALU roofline.  `batched` times the
+24-problem workload the same way (--no-batched leaves it out).  Under
+torchrun every rank runs an independent replica (the operator shards over
+rays with no exchange in the forward; this build has no cross-GPU step), so
+value = all ranks' rays / max time.
+
+Other workloads (--workload): kuhn8 (the tiny plain-method case), cubic64 (the
+robustness case, with its 1M adversarial rays timed separately), recon64 (the
+differentiation case: ms per Adam iteration through the autograd wrapper),
+batch24 / batch6s (the batched workload alone), kuhn24 / kuhn64 / kuhn64s /
+kuhn96s (smaller copies for profiling).
 
 --impl reference times the CPU oracle (brute-force FP64 clipping) on a bounded
 sample of the same rays, on the host cores.
@@ -45,38 +52,47 @@ BYTES_BOX = 32                       # one BVH child box (half of a 64-byte node
 BYTES_FACE = 48                      # one boundary face record
 # what this layout actually moves per step: one 64-byte record + mu / RMW
 LAYOUT_STEP = {("fwd", 1): 68, ("fwd", 4): 80, ("bwd", 1): 72, ("bwd", 4): 96}
+# ... and with the FP64 accumulator of the default C = 1 backprojection: one
+# 64-byte record + an 8-byte read-modify-write of the accumulator (red.f64)
+LAYOUT_STEP_ACC64 = 80
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk32_kuhn96_traffic.md")
+PROFILES = os.path.join(ROOT, "profiles")
+# DRAM bytes per segment of the filtered walk kernels, from an ncu capture of
+# a smaller launch of the same mesh (profiles/walk32_kuhn96s_traffic.md), and
+# FP64 operations per segment of the plain walk (profiles/walk64_kuhn64s_fp64.md);
+# both are used only while the walk sources hash to the value recorded there.
+TRAFFIC_FILE = os.path.join(PROFILES, "walk32_kuhn96s_traffic.md")
+FP64OPS_FILE = os.path.join(PROFILES, "walk64_kuhn64s_fp64.md")
 WALK_SOURCES = ["kernels.cu", "kernels.cuh", "predicates.cuh", "tetproj_internal.h"]
 
 
-def measured_traffic(workload, tile, order, scatter):
-    """DRAM bytes per call {fwd, bwd} from the committed ncu capture of the bench
-    workload, or None if the walk sources changed since it was taken or the
-    launch configuration differs."""
+def walk_sources_sha():
     import hashlib
-    try:
-        text = open(TRAFFIC_FILE).read()
-    except OSError:
-        return None
     h = hashlib.sha256()
     for f in WALK_SOURCES:
         with open(os.path.join(ROOT, "paper_1908_06909_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    return h.hexdigest()
+
+
+def profile_per_segment(path, key):
+    """{fwd, bwd} per-segment figures recorded under `key` in a committed
+    profile summary, or None if the walk sources changed since the capture."""
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
     vals = {}
     for line in text.splitlines():
         parts = line.split()
         if len(parts) == 2 and parts[0] == "source_sha256":
             vals["sha"] = parts[1]
-        if parts and parts[0] == "workload":
-            vals["cfg"] = parts[1:]
-        if parts and parts[0] == "traffic_bytes_per_call":
-            vals["t"] = {k: int(v) for k, v in (p.split("=") for p in parts[1:])}
-    want = [workload, "tile", tile, "order", order, "scatter", scatter, "channels", "1"]
-    if vals.get("sha") != h.hexdigest() or vals.get("cfg") != want or "t" not in vals:
+        if parts and parts[0] == key:
+            vals["v"] = {k: float(v) for k, v in (q.split("=") for q in parts[1:])}
+    if vals.get("sha") != walk_sources_sha() or "v" not in vals:
         return None
-    return vals["t"]
+    return vals["v"]
 
 
 def max_over_ranks(ms, dist, device="cuda"):
@@ -448,6 +464,7 @@ def run_batch(args, tp, torch, dist, rank, world, local):
         cpu = {"value": n_cpu / dt, "unit": "rays/s", "cores": oracle.default_threads(),
                "kind": "oracle", "sample": f"{per} rays of each of {len(ws)} problems (fwd + back, "
                                            f"4 channels), brute-force FP64 clipping, {dt:.1f} s"}
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
@@ -479,8 +496,10 @@ def run_batch(args, tp, torch, dist, rank, world, local):
             "host_s": {"build": t_build, "tune": t_tune},
             "stats": {"fwd": sf, "bwd": sb},
         }
-        print(json.dumps(line), flush=True)
     b.close()
+    del b, meshes, geos
+    torch.cuda.empty_cache()
+    return line
 
 
 def _sum_stats(rows):
@@ -491,7 +510,7 @@ def _sum_stats(rows):
     return out
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -501,6 +520,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload: leave out the nested batched measurement")
+    ap.add_argument("--batched-workload", default="batch24")
     ap.add_argument("--scatter", default="atomic", choices=["atomic", "warp", "sort"])
     ap.add_argument("--tile", default="8x8")
     ap.add_argument("--tune-cache", default=None)
@@ -508,8 +530,11 @@ def main():
                     help="accumulator of the filtered backprojection (auto: FP64 at C = 1)")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workloads: fixed --tile/--scatter instead of the autotuner")
-    args = ap.parse_args()
+    return ap.parse_args(argv)
 
+
+def main():
+    args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -530,12 +555,46 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     if args.workload.startswith("batch"):
-        run_batch(args, tp, torch, dist, rank, world, local)
-        if dist:
-            dist.destroy_process_group()
-        return
+        line = run_batch(args, tp, torch, dist, rank, world, local)
+    elif args.workload == "recon64":
+        line = run_recon(args, tp, torch, dist, rank, world, local)
+    else:
+        line = run_single(args, tp, torch, dist, rank, world, local)
+        if args.workload == "kuhn96" and not args.no_batched:
+            # the batched workload, timed the same way, nested in the same line
+            bargs = parse_args([])
+            bargs.workload = args.batched_workload
+            bargs.steps = max(3, min(args.steps, 5))
+            bargs.warmup = 3
+            bargs.no_cpu = True
+            bargs.tune_cache = args.tune_cache
+            bl = run_batch(bargs, tp, torch, dist, rank, world, local)
+            if bl is not None:
+                keep = ["value", "unit", "ms_per_step", "steps", "warmup", "config",
+                        "gsegments_per_s", "segments_per_step", "unbatched", "plain_fp64",
+                        "roofline", "e2e", "gpu_launches", "clocks", "host_s"]
+                line["batched"] = {k: bl[k] for k in keep if k in bl}
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
-    w = build_workload(args)
+
+def build_single_workload(args):
+    import workloads as W
+    if args.workload == "kuhn8":       # the tiny plain-method case (8^3 Kuhn, 64^2 x 32)
+        return W.config1()
+    if args.workload == "cubic64":     # the robustness case (detector rays; adversarial below)
+        return W.config3()
+    if args.workload == "kuhn96s":     # the bench mesh, 8 angles: profiler-sized launches
+        return W.config2(nangles=8)
+    return build_workload(args)
+
+
+def run_single(args, tp, torch, dist, rank, world, local):
+    """One problem: forward + backward per step, filtered FP32 (the product),
+    the plain FP64 path beside it, e2e with host buffers, roofline, oracle."""
+    w = build_single_workload(args)
     mesh = tp.Mesh(w.verts, w.tets)
     geo = tp.Geometry.from_cone(w.geom)
     tu, tv = (int(x) for x in args.tile.split("x"))
@@ -543,6 +602,7 @@ def main():
                                                   "warp": tp.SCATTER_WARP,
                                                   "sort": tp.SCATTER_SORT}[args.scatter],
                           flags={"auto": 0, "f64": tp.FLAG_ACC64, "f32": tp.FLAG_ACC32}[args.acc])
+    acc = ("f64" if args.scatter == "atomic" else "f32") if args.acc == "auto" else args.acc
     C = 1
     mu = torch.tensor(w.mu, dtype=torch.float32, device="cuda")
     proj = torch.empty(geo.shape, dtype=torch.float32, device="cuda")
@@ -596,28 +656,55 @@ def main():
     value = job_throughput(world, nrays, ms_step)
     segs = sf["segments"] + sb["segments"]
 
-    # plain FP64 path (the ratio's denominator), same step
+    # plain FP64 path (the ratio's denominator), same step, with its FP64-ALU
+    # roofline: FP64 operations per segment (ncu capture) x segments over the
+    # timed call, against the measured FP64 FMA rate
     plain = None
     if args.plain_steps > 0:
         mu64 = mu.double()
         proj64 = torch.empty(geo.shape, dtype=torch.float64, device="cuda")
         back64 = torch.empty(mesh.nt, dtype=torch.float64, device="cuda")
         o64 = tp.make_options(precision=tp.PLAIN_FP64, tile=(tu, tv), scatter=opt.scatter)
+        mesh.stats_reset()
         tp.forward(mesh, geo, mu64, out=proj64, options=o64)
+        sf64 = mesh.stats()
+        mesh.stats_reset()
         tp.backward(mesh, geo, proj64, out=back64, options=o64)
+        sb64 = mesh.stats()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        pf = pb = 0.0
         for _ in range(args.plain_steps):
+            a.record(stream)
             tp.forward(mesh, geo, mu64, out=proj64, options=o64)
+            b.record(stream)
             tp.backward(mesh, geo, proj64, out=back64, options=o64)
-        b.record(stream)
-        torch.cuda.synchronize()
-        pms = a.elapsed_time(b) / args.plain_steps
+            c.record(stream)
+            torch.cuda.synchronize()
+            pf += a.elapsed_time(b)
+            pb += b.elapsed_time(c)
+        pf /= args.plain_steps
+        pb /= args.plain_steps
+        pms = pf + pb
         rel = float(((proj.double() - proj64).abs().sum() / proj64.abs().sum()).item())
+        fp64_peak = tp.fma64_peak_tflops()
+        ops = profile_per_segment(FP64OPS_FILE, "fp64_ops_per_segment")
+        pdom = "bwd" if pb >= pf else "fwd"
+        pdom_ms = pb if pdom == "bwd" else pf
+        proof = {"bound": "alu", "kernel": f"k_walk64<1,{'MODE_BWD' if pdom == 'bwd' else 'MODE_FWD'}>",
+                 "peak": fp64_peak, "unit": "TFLOP/s", "peak_kind": "measured (FP64 FMA probe)",
+                 "ms_per_launch": pdom_ms, "fwd_ms": pf, "bwd_ms": pb}
+        if ops is not None:
+            flops = ops[pdom] * (sb64 if pdom == "bwd" else sf64)["segments"]
+            proof.update(achieved=flops / (pdom_ms / 1e3) / 1e12, frac=flops / (pdom_ms / 1e3) / 1e12 / fp64_peak,
+                         flops_per_launch=flops, ops_per_segment=ops[pdom],
+                         ops_note="FP64 operations per segment (2 per FMA) from profiles/walk64_kuhn64s_fp64.md")
+        else:
+            proof.update(achieved=None, frac=None, ops_note="no FP64 operation count for this build")
         plain = {"value": nrays / (pms / 1e3), "unit": "rays/s", "ms_per_step": pms,
                  "speedup_filtered_vs_plain": (nrays / (ms_step / 1e3)) / (nrays / (pms / 1e3)),
-                 "filtered_vs_plain_rel_l1_diff": rel}
+                 "filtered_vs_plain_rel_l1_diff": rel, "roofline": proof,
+                 "segments": {"fwd": sf64["segments"], "bwd": sb64["segments"]}}
         del proj64, back64, mu64
 
     # end to end through the public API with host buffers
@@ -663,26 +750,40 @@ def main():
     e2e = {"value": job_throughput(world, nrays, max_over_ranks(e2e_ms, dist)), "unit": "rays/s",
            "h2d_bytes_per_step": mu_h.numel() * 4,
            "d2h_bytes_per_step": proj_h.numel() * 4 + back_h.numel() * 4}
+    del mu_h, proj_h, back_h, mu_d
 
     # roofline of the dominant walk (events around each call; the O(nt)
-    # permutation kernels inside the call are < 0.1% of it)
+    # permutation kernels inside the call are < 0.1% of it).  The default
+    # backprojection at C = 1 reduces into an FP64 accumulator: the kernel is
+    # k_walk32<1,MODE_BWD64>, and its layout moves 8-byte reductions.
     hbm, peak_kind = peaks()
     def alg_bytes(s, kind, table=BYTES_STEP):
         return (s["segments"] * table[(kind, C)] + s["rays"] * BYTES_RAY(C) +
                 s["bvh_nodes"] * BYTES_BOX + s["bvh_faces"] * BYTES_FACE)
+    layout = dict(LAYOUT_STEP)
+    if acc == "f64":
+        layout[("bwd", 1)] = LAYOUT_STEP_ACC64
     dom = "bwd" if bwd_ms >= fwd_ms else "fwd"
     dom_ms = bwd_ms if dom == "bwd" else fwd_ms
-    dom_bytes = alg_bytes(sb if dom == "bwd" else sf, dom)
+    dom_stats = sb if dom == "bwd" else sf
+    dom_bytes = alg_bytes(dom_stats, dom)
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    tr = measured_traffic(w.name, args.tile, "morton", args.scatter)
-    roof = {"bound": "hbm", "kernel": f"k_walk32<1,{'MODE_BWD' if dom == 'bwd' else 'MODE_FWD'}>",
+    bwd_mode = "MODE_BWD64" if acc == "f64" else "MODE_BWD"
+    tr = None
+    if args.tile == "8x8" and args.scatter == "atomic" and args.acc == "auto":
+        per_seg = profile_per_segment(TRAFFIC_FILE, "dram_bytes_per_segment")
+        if per_seg is not None:
+            tr = per_seg[dom] * dom_stats["segments"]
+    roof = {"bound": "hbm",
+            "kernel": f"k_walk32<1,{bwd_mode if dom == 'bwd' else 'MODE_FWD'}> + k_resume32",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None if tr is None else tr[dom], "peak_kind": peak_kind,
-            "traffic_note": ("DRAM read+write bytes per call, ncu capture in "
-                             "profiles/walk32_kuhn96_traffic.md (cold cache per launch)")
-                            if tr is not None else "no capture for this build/configuration",
+            "traffic": tr, "peak_kind": peak_kind,
+            "traffic_note": ("DRAM read+write bytes per call: bytes per segment of an ncu capture on "
+                             "the same mesh at 8 angles (profiles/walk32_kuhn96s_traffic.md) x this "
+                             "call's segments") if tr is not None
+                            else "no capture for this build/configuration",
             "bytes_per_launch": dom_bytes, "ms_per_launch": dom_ms,
-            "layout_gbs": alg_bytes(sb if dom == "bwd" else sf, dom, LAYOUT_STEP) / (dom_ms / 1e3) / 1e9,
+            "layout_gbs": alg_bytes(dom_stats, dom, layout) / (dom_ms / 1e3) / 1e9,
             "fwd_ms": fwd_ms, "bwd_ms": bwd_ms}
 
     cpu = None
@@ -693,30 +794,111 @@ def main():
         cpu = {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle",
                "sample": f"{ns} of {nrays} rays (fwd + back), brute-force FP64 clipping, {dt:.1f} s"}
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": w.name, "nt": mesh.nt, "rays_per_step": nrays,
-                       "channels": C, "precision": "filtered", "tile": args.tile,
-                       "scatter": args.scatter, "accumulator": ("f64" if args.scatter == "atomic" else "f32") if args.acc == "auto" else args.acc,
-                       "l2": l2_note(mesh.nt, nrays, C),
-                       "parallelism": f"replicas{world}"},
-            "gsegments_per_s": job_throughput(world, segs, ms_step) / 1e9,
-            "segments_per_step": segs,
-            "plain_fp64": plain,
-            "roofline": roof,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk.summary(),
-            "stats": {"fwd": sf, "bwd": sb},
-        }
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    line = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nt": mesh.nt, "rays_per_step": nrays,
+                   "channels": C, "precision": "filtered", "tile": args.tile,
+                   "scatter": args.scatter, "accumulator": acc,
+                   "l2": l2_note(mesh.nt, nrays, C),
+                   "parallelism": f"replicas{world}"},
+        "gsegments_per_s": job_throughput(world, segs, ms_step) / 1e9,
+        "segments_per_step": segs,
+        "plain_fp64": plain,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "stats": {"fwd": sf, "bwd": sb},
+    }
+    if args.workload == "cubic64":
+        line["adversarial"] = run_adversarial(args, tp, torch, w, mesh, opt, stream)
+    return line
+
+
+def run_adversarial(args, tp, torch, w, mesh, opt, stream):
+    """The robustness case's 1M adversarial rays (explicit rays aimed exactly
+    at vertices, edge midpoints and face points): forward + backward through
+    tetproj_forward_rays / tetproj_backward_rays, filtered and plain FP64."""
+    src = torch.tensor(w.extra["adv_src"], device="cuda")
+    dst = torch.tensor(w.extra["adv_target"], device="cuda")
+    n = src.shape[0]
+    out = {}
+    for prec, dt in (("filtered", torch.float32), ("plain_fp64", torch.float64)):
+        mu = torch.tensor(w.mu, dtype=dt, device="cuda")
+        o = tp.make_options(precision=tp.FILTERED if prec == "filtered" else tp.PLAIN_FP64)
+        mesh.stats_reset()
+        b = tp.forward_rays(mesh, src, dst, mu, options=o)
+        tp.backward_rays(mesh, src, dst, b, options=o)
+        st = mesh.stats()
+        steps = args.steps if prec == "filtered" else 1
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            b = tp.forward_rays(mesh, src, dst, mu, options=o)
+            tp.backward_rays(mesh, src, dst, b, options=o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"value": n / (ms / 1e3), "unit": "rays/s", "ms_per_step": ms, "rays": n,
+                     "segments_per_step": st["segments"], "errors": st["error_count"],
+                     "sos": st["sos"], "deferred": st["deferred"]}
+    return out
+
+
+def run_recon(args, tp, torch, dist, rank, world, local):
+    """The differentiation case: b = A mu_true (plain FP64) + noise, then Adam
+    (lr 1e-2) on FP32 mu through TetProject (forward kernel, backward = the
+    backprojection kernel).  One step = one Adam iteration."""
+    import workloads as W
+    w = W.config4()
+    mesh = tp.Mesh(w.verts, w.tets)
+    geo = tp.Geometry.from_cone(w.geom)
+    b64 = tp.forward(mesh, geo, torch.tensor(w.mu, dtype=torch.float64, device="cuda"))
+    sigma = 0.01 * float(b64.max())
+    b = (b64 + torch.tensor(w.extra["noise_rng"].normal(0, sigma, size=geo.shape),
+                            device="cuda")).float()
+    del b64
+    mu = torch.zeros(mesh.nt, dtype=torch.float32, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([mu], lr=1e-2)
+    stream = torch.cuda.current_stream()
+
+    def iteration():
+        opt.zero_grad(set_to_none=False)
+        r = tp.TetProject.apply(mu, mesh, geo) - b
+        loss = 0.5 * (r * r).sum()
+        loss.backward()
+        opt.step()
+        return loss
+
+    for _ in range(args.warmup):
+        iteration()
+    torch.cuda.synchronize()
+    launches0 = tp.launch_count()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            loss = iteration()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = tp.launch_count() - launches0
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
+    return {
+        "metric": METRIC, "value": job_throughput(world, geo.nrays, ms), "unit": "rays/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nt": mesh.nt, "rays_per_step": geo.nrays,
+                   "step": "one Adam iteration (forward + backprojection + update)",
+                   "parallelism": f"replicas{world}"},
+        "ms_per_adam_iteration": ms, "loss": float(loss), "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
 
 
 if __name__ == "__main__":

@@ -392,6 +392,15 @@ int32_t tetproj_version(void);
  * Kernels replayed from a captured CUDA graph are counted once, at capture. */
 int64_t tetproj_launch_count(void);
 
+/* FP64 FMA throughput probe (for benchmarks; no counterpart in the paper).
+ * Launches 8 x SM-count CTAs of 256 threads on `stream`, each thread running
+ * 8 independent chains of `iters` FP64 FMAs; *flops receives the
+ * floating-point operations launched (2 per FMA), so flops / (event-timed
+ * duration) is the device's FP64 FMA rate, the roofline of the plain FP64
+ * walk.  sink: device buffer of 8 x SM-count doubles (never written in
+ * practice).  Errors: TETPROJ_ERR_ARG (iters < 1, NULL pointers), CUDA. */
+tetproj_status tetproj_fma64_probe(int64_t iters, double *sink, double *flops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -208,19 +208,22 @@ def check_side_direction(normals, w=None):
     """Raise PlanarSideError unless, for every exact integer plane normal n,
     n . w has the sign of the first non-zero component of n by more than the
     FP64 error of the clipper's own n . w.  ``normals`` is a list of integer
-    triples or a dict {normal: kappa} (see exact.face_planes_containing); the
-    clipper's normal is a cross product of FP64 edge vectors, off by at most
-    ~2u kappa |n| per component, and its dot product with w adds ~3u."""
+    triples (their cross products taken as exact) or the dict {normal: E} of
+    exact.face_planes_containing: the clipper's normal is a cross product of
+    FP64 edge vectors, off by at most ~4 u E_k in component k (nothing where
+    both of its products are exactly zero), and its dot product with w adds
+    ~3 u sum |n_k w_k|."""
     from fractions import Fraction as Fr
     from oracle import exact
+    u = 2.0 ** -53
     w = sos_side_direction() if w is None else np.asarray(w, float)
     wf = [Fr(float(x)) for x in w]
-    wn = float(sum(abs(x) for x in wf))
-    kap = normals if isinstance(normals, dict) else {tuple(n): 1.0 for n in normals}
-    for n, kappa in kap.items():
+    bound = normals if isinstance(normals, dict) else {tuple(n): (0.0, 0.0, 0.0) for n in normals}
+    for n, E in bound.items():
         want = exact.sos_side_sign(n)
         dot = sum(Fr(int(a)) * b for a, b in zip(n, wf))
-        err = 8.0 * 2.0 ** -53 * (kappa + 1.0) * max(abs(int(a)) for a in n) * wn
+        err = sum(8.0 * u * E[k] * abs(float(w[k])) + 4.0 * u * abs(int(n[k]) * float(w[k]))
+                  for k in range(3))
         if want == 0 or exact.sign(dot) != want or abs(float(dot)) <= err:
             raise PlanarSideError(f"side direction {w} does not reproduce the symbolic "
                                   f"side of the plane with normal {n}")

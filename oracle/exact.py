@@ -371,10 +371,12 @@ def face_planes_containing(verts, tets, S, P, pad=1e-9, return_kappa=False):
     face's vertices on a common integer grid, divided by the gcd of its
     components, with a positive first non-zero component, so its components
     (their signs and ratios) are exact; faces in one plane give one normal.
-    With ``return_kappa`` a dict {normal: kappa} is returned instead, kappa the
-    largest |b - a| |c - a| / |(b - a) x (c - a)| over the plane's faces: the
-    factor by which rounding in an FP64 cross product of those edges can exceed
-    u |normal|."""
+    With ``return_kappa`` a dict {normal: E} is returned instead: per component
+    k, E_k is the largest |e1_i e2_j| + |e1_j e2_i| ((i, j) the other two
+    components; e1, e2 two edges of a face of the plane from any of its
+    vertices, on the same scale as the normal), so that an FP64 cross product
+    of FP64 edge vectors differs from the normal by at most ~4 u E_k in
+    component k -- and by nothing where both products are exactly zero."""
     import math
     import numpy as np
     S = np.asarray(S, float)
@@ -396,15 +398,20 @@ def face_planes_containing(verts, tets, S, P, pad=1e-9, return_kappa=False):
                     _int_det(e1, e2, [Pi[m] - a[m] for m in range(3)]) == 0:
                 n = [e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
                      e1[0] * e2[1] - e1[1] * e2[0]]
-                kappa = math.sqrt(float(sum(x * x for x in e1)) * float(sum(x * x for x in e2))
-                                  / float(sum(x * x for x in n)))
+                E = [0, 0, 0]
+                for p0, p1, p2 in ((a, b, c), (b, c, a), (c, a, b)):
+                    f1 = [p1[m] - p0[m] for m in range(3)]
+                    f2 = [p2[m] - p0[m] for m in range(3)]
+                    for k_, (i, j) in enumerate(((1, 2), (2, 0), (0, 1))):
+                        E[k_] = max(E[k_], abs(f1[i] * f2[j]) + abs(f1[j] * f2[i]))
                 g = math.gcd(math.gcd(abs(n[0]), abs(n[1])), abs(n[2]))
                 n = [x // g for x in n]
                 lead = next(x for x in n if x != 0)
                 if lead < 0:
                     n = [-x for x in n]
                 key = tuple(n)
-                out[key] = max(out.get(key, 0.0), kappa)
+                prev = out.get(key, (0.0, 0.0, 0.0))
+                out[key] = tuple(max(prev[m], E[m] / g) for m in range(3))
     if return_kappa:
         return out
     return sorted(out)

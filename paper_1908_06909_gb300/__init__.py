@@ -69,6 +69,28 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def fma64_peak_tflops(iters: int = 1 << 16, reps: int = 3) -> float:
+    """The device's FP64 FMA rate in TFLOP/s, timed with CUDA events around
+    tetproj_fma64_probe (best of `reps` launches after one warm-up)."""
+    torch = _torch()
+    L = _lib.load()
+    sink = torch.empty(8 * torch.cuda.get_device_properties(0).multi_processor_count,
+                       dtype=torch.float64, device="cuda")
+    flops = ctypes.c_double()
+    stream = _stream()
+    check(L.tetproj_fma64_probe(iters, _ptr(sink), ctypes.byref(flops), stream), "tetproj_fma64_probe")
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        check(L.tetproj_fma64_probe(iters, _ptr(sink), ctypes.byref(flops), stream),
+              "tetproj_fma64_probe")
+        b.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return flops.value / (best / 1e3) / 1e12
+
+
 def make_options(precision=FILTERED, channels=1, tile=(8, 8), order=ORDER_MORTON,
                  scatter=SCATTER_ATOMIC, max_steps=0, flags=0) -> Options:
     o = Options()

@@ -98,6 +98,7 @@ SIGNATURES = {
     "tetproj_forward_rays_mt": (c_i32, [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tetproj_entry": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tetproj_rstar_build_host": (c_i32, [c_vp, c_i64, c_vp, c_i64, c_vp]),
+    "tetproj_fma64_probe": (c_i32, [c_i64, c_vp, ctypes.POINTER(ctypes.c_double), c_vp]),
     "tetproj_side_host": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp]),
     "tetproj_side_device": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]),
 }

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtetproj.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "kernels.cu", "segsort.cu"]
+CU_SOURCES = ["api.cu", "kernels.cu", "segsort.cu", "peak.cu"]
 CPP_SOURCES = ["mesh_build.cpp", "rstar.cpp"]
 
 
