@@ -18,8 +18,9 @@ value = all ranks' rays / max time.
 Other workloads (--workload): kuhn8 (the tiny plain-method case), cubic64 (the
 robustness case, with its 1M adversarial rays timed separately), recon64 (the
 differentiation case: ms per Adam iteration through the autograd wrapper),
-batch24 / batch6s (the batched workload alone), kuhn24 / kuhn64 / kuhn64s /
-kuhn96s (smaller copies for profiling).
+batch24 / batch6s (the batched workload alone), c5pK (problem K of the
+batched workload alone, one channel), kuhn24 / kuhn64 / kuhn64s / kuhn96s
+(smaller copies for profiling).
 
 --impl reference times the CPU oracle (brute-force FP64 clipping) on a bounded
 sample of the same rays, on the host cores.
@@ -588,6 +589,12 @@ def build_single_workload(args):
         return W.config3()
     if args.workload == "kuhn96s":     # the bench mesh, 8 angles: profiler-sized launches
         return W.config2(nangles=8)
+    if args.workload.startswith("c5p"):  # one problem of the batched workload, one channel
+        k = int(args.workload[3:])
+        n, N, na = W.config5_specs()[k]
+        w = W.config5_problem(k, n, N, na, channels=1)
+        w.mu = w.mu[:, 0].copy()
+        return w
     return build_workload(args)
 
 
@@ -602,7 +609,7 @@ def run_single(args, tp, torch, dist, rank, world, local):
                                                   "warp": tp.SCATTER_WARP,
                                                   "sort": tp.SCATTER_SORT}[args.scatter],
                           flags={"auto": 0, "f64": tp.FLAG_ACC64, "f32": tp.FLAG_ACC32}[args.acc])
-    acc = ("f64" if args.scatter == "atomic" else "f32") if args.acc == "auto" else args.acc
+    acc = ("f32" if args.scatter == "sort" else "f64") if args.acc == "auto" else args.acc
     C = 1
     mu = torch.tensor(w.mu, dtype=torch.float32, device="cuda")
     proj = torch.empty(geo.shape, dtype=torch.float32, device="cuda")

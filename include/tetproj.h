@@ -88,9 +88,12 @@ typedef int32_t tetproj_status;
                                       instead of the binary BVH: filtered forward
                                       (C = 1) and tetproj_entry only; the tree is
                                       built on first use (synchronous)          */
-#define TETPROJ_FLAG_ACC64 2       /* filtered backprojection with atomic scatter:
-                                      add the FP32 segment contributions into an
-                                      FP64 accumulator (red.global.add.f64) and
+#define TETPROJ_FLAG_ACC64 2       /* filtered backprojection with atomic or
+                                      warp-aggregated scatter: add the FP32
+                                      segment contributions into an FP64
+                                      accumulator (red.global.add.f64; with
+                                      _SCATTER_WARP, lanes at one tet are summed
+                                      in FP64 first, one reduction per tet) and
                                       round once: ~1e-7 for any number of
                                       segments per tet.  Default for C = 1.    */
 #define TETPROJ_FLAG_ACC32 4       /* the same into an FP32 accumulator (faster for
@@ -133,6 +136,7 @@ typedef struct tetproj_stats {
     int64_t deferred;    /* rays the fast FP32 walk handed to the robust resume walk   */
     int32_t error;       /* first device-side error code, 0 if none                    */
     int32_t error_count; /* rays that hit a device-side error                          */
+    int64_t grazing;     /* crossings at a grazing angle placed again from FP64 records */
 } tetproj_stats;
 
 typedef struct tetproj_mesh_info {
@@ -291,8 +295,8 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
  *   channels: C = 1 or 4 for every problem.
  * The batch owns per-problem workspace and one deferral queue (allocated
  * here); it keeps pointers into the meshes and geometries, which must outlive
- * it.  Backprojections add into FP64 accumulators at C = 1 (each problem's
- * scatter choice then does not apply) and into FP32 ones at C = 4, two-level
+ * it.  Backprojections add into FP64 accumulators at C = 1 (with each problem's
+ * atomic or warp-aggregated scatter) and into FP32 ones at C = 4, two-level
  * for dense problems (as TETPROJ_FLAG_ACC32 describes; merged after every
  * round).  Rays are processed in rounds of at most 2^23 rays; backprojection
  * rounds are cut further inside dense problems (at most max(2^18,

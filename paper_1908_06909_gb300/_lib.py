@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("rays", c_i64), ("hits", c_i64), ("segments", c_i64), ("fp64_filter", c_i64),
                 ("exact", c_i64), ("sos", c_i64), ("bvh_nodes", c_i64), ("bvh_faces", c_i64),
-                ("deferred", c_i64), ("error", c_i32), ("error_count", c_i32)]
+                ("deferred", c_i64), ("error", c_i32), ("error_count", c_i32), ("grazing", c_i64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

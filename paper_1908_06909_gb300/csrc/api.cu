@@ -126,7 +126,7 @@ static cudaError_t upload(T **dst, const std::vector<T> &src) {
 
 extern "C" {
 
-int32_t tetproj_version(void) { return 200; }
+int32_t tetproj_version(void) { return 201; }
 
 int64_t tetproj_launch_count(void) { return (int64_t)launch_count(); }
 
@@ -198,8 +198,8 @@ static void overlap_release(ResumeOverlap &o) {
 static cudaError_t overlap_create(ResumeOverlap &o, int64_t cap) {
     o = ResumeOverlap{};
     int lo = 0, hi = 0;
-    cudaError_t e = cudaMalloc((void **)&o.q2, (size_t)cap * sizeof(QEntry));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&o.q2_count, sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc((void **)&o.q2, (size_t)queue_bytes(cap));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&o.q2_count, kQueueCountBytes);
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&o.aux, cudaStreamNonBlocking, hi);
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
@@ -295,8 +295,8 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *m, tetproj_mesh_info *o
     o->nboundary = m->nb;
     o->nbvh_nodes = m->nnodes;
     o->nflipped = m->nflipped;
-    int64_t b = m->base_bytes + m->q_cap * (int64_t)sizeof(QEntry) * (m->ov_ready ? 2 : 1) +
-                (m->q_count ? 8 : 0) +
+    int64_t b = m->base_bytes + queue_bytes(m->q_cap) * (m->ov_ready ? 2 : 1) +
+                (m->q_count ? (int64_t)kQueueCountBytes : 0) +
                 m->plan.bytes + m->sort.bytes + m->rstar_bytes;
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) b += m->ws_bytes[i][j];
@@ -341,8 +341,8 @@ static tetproj_status ensure_queue(tetproj_mesh *m, int64_t nrays, bool allow_ov
         cudaFree(m->q);
         m->q = nullptr;
         m->q_cap = 0;
-        TP_CUDA(cudaMalloc((void **)&m->q, (size_t)need * sizeof(QEntry)));
-        if (!m->q_count) TP_CUDA(cudaMalloc((void **)&m->q_count, sizeof(unsigned long long)));
+        TP_CUDA(cudaMalloc((void **)&m->q, (size_t)queue_bytes(need)));
+        if (!m->q_count) TP_CUDA(cudaMalloc((void **)&m->q_count, kQueueCountBytes));
         m->q_cap = need;
     }
     if (want_ov && !m->ov_ready) {
@@ -404,6 +404,7 @@ tetproj_status tetproj_mesh_stats_read(tetproj_mesh *m, void *stream, tetproj_st
     o->deferred = (int64_t)c.deferred;
     o->error = c.error;
     o->error_count = c.error_count;
+    o->grazing = (int64_t)c.grazing;
     return TETPROJ_OK;
 }
 
@@ -600,12 +601,12 @@ static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_opt
     return TETPROJ_OK;
 }
 
-// Accumulator of the filtered backprojection with atomic scatter: FP64 unless
-// TETPROJ_FLAG_ACC32, or C = 4 without TETPROJ_FLAG_ACC64 (measured on GB300:
+// Accumulator of the filtered backprojection with atomic or warp-aggregated
+// scatter: FP64 unless TETPROJ_FLAG_ACC32, or C = 4 without TETPROJ_FLAG_ACC64 (measured on GB300:
 // at C = 1 the FP64 reduction is also the faster one; at C = 4 it needs four
 // 8-byte reductions per segment against one 16-byte FP32 one).
 static bool use_acc64(const tetproj_options &o) {
-    if (o.precision != TETPROJ_FILTERED || o.scatter != TETPROJ_SCATTER_ATOMIC) return false;
+    if (o.precision != TETPROJ_FILTERED || o.scatter == TETPROJ_SCATTER_SORT) return false;
     if (o.flags & TETPROJ_FLAG_ACC64) return true;
     if (o.flags & TETPROJ_FLAG_ACC32) return false;
     return o.channels == 1;
@@ -636,7 +637,7 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
                                    const void *y, void *mu_out, cudaStream_t s) {
     if (rstar_unsupported(o)) return TETPROJ_ERR_ARG;
     if ((o.flags & TETPROJ_FLAG_ACC64) && o.precision == TETPROJ_FILTERED &&
-        o.scatter != TETPROJ_SCATTER_ATOMIC)
+        o.scatter == TETPROJ_SCATTER_SORT)
         return TETPROJ_ERR_ARG;  // FP64 accumulation is an atomic-scatter variant
     if (use_acc64(o)) {
         // FP32 walk, FP64 accumulator (the plain path's workspace), one rounding at the end
@@ -954,16 +955,19 @@ tetproj_status tetproj_side_device(const double *S, const double *P, const doubl
 //
 // Its scratch is the tet-ordered accumulator (up to kNoAllocAccBytes; the
 // two-level case holds the FP32 and the FP64 accumulator side by side) and
-// the deferral queue of the filtered walk (kNoAllocQueue entries; launches are
-// chunked to fit it).  The array is part of the library image, so every GPU
-// that loads libtetproj.so holds it (48 MB) until the process exits.
+// the deferral queue of the filtered walk with its crossing fixes
+// (kNoAllocQueue entries; launches are chunked to fit it).  The array is part
+// of the library image, so every GPU that loads libtetproj.so holds it (52 MB)
+// until the process exits.
 // Every call shares it and it keeps the previous call's contents: the
 // accumulators are cleared at the start of each call, and calls that overlap
 // on the GPU (different streams, no ordering) race on it.
 static const int64_t kNoAllocAccBytes = TETPROJ_NOALLOC_ACC_BYTES;
 static_assert(kNoAllocAccBytes % 256 == 0, "accumulator region keeps the queue 256-byte aligned");
 static const int64_t kNoAllocQueue = int64_t(1) << 18;
-static const int64_t kNoAllocBytes = kNoAllocAccBytes + kNoAllocQueue * (int64_t)sizeof(QEntry) + 256;
+static const int64_t kNoAllocQueueBytes = ((int64_t)kNoAllocQueue * (int64_t)sizeof(QEntry) +
+                                           ((int64_t)kNoAllocQueue / 2) * (int64_t)sizeof(XFix));
+static const int64_t kNoAllocBytes = kNoAllocAccBytes + kNoAllocQueueBytes + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 static std::mutex g_noalloc_mutex;
@@ -1038,7 +1042,7 @@ extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
     // the sort-and-reduce scatter needs buffers sized by the segment count
     if (o.scatter == TETPROJ_SCATTER_SORT || rstar_unsupported(o)) return TETPROJ_ERR_ARG;
     if ((o.flags & TETPROJ_FLAG_ACC64) && o.precision == TETPROJ_FILTERED &&
-        o.scatter != TETPROJ_SCATTER_ATOMIC)
+        o.scatter == TETPROJ_SCATTER_SORT)
         return TETPROJ_ERR_ARG;  // FP64 accumulation is an atomic-scatter variant
     const int f64 = o.precision == TETPROJ_PLAIN_FP64;
     KParams p = base_params(mesh, o);
@@ -1058,7 +1062,7 @@ extern "C" tetproj_status tetproj_backward_noalloc(const tetproj_mesh *mesh,
     if (!f64) {
         p.q = reinterpret_cast<QEntry *>(base + kNoAllocAccBytes);
         p.q_count = reinterpret_cast<unsigned long long *>(
-            base + kNoAllocAccBytes + kNoAllocQueue * (int64_t)sizeof(QEntry));
+            base + kNoAllocAccBytes + kNoAllocQueueBytes);
         p.q_cap = kNoAllocQueue;
     }
     p.in = proj;
@@ -1114,7 +1118,7 @@ struct tetproj_batch {
     int64_t q_cap = 0;
     int smem_nodes = 64;
     unsigned grid_fwd = 0, grid_bwd = 0, rgrid = 0;
-    bool acc64 = false;  // C = 1: FP64 accumulators (the per-problem scatter choice is for C = 4)
+    bool acc64 = false;  // C = 1: FP64 accumulators (atomic or warp-aggregated per problem)
     bool bound = false;
     ResumeOverlap ov{};  // second queue + auxiliary stream when there are several rounds
     bool ov_ready = false;
@@ -1201,8 +1205,8 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
     if (b->item_begin.back() >= (int64_t(1) << 40)) { batch_free(b); return TETPROJ_ERR_TOO_LARGE; }
     int64_t need = total_rays < kQueueMax ? total_rays : kQueueMax;
     need = ((need + 4095) / 4096) * 4096;
-    cudaError_t e = cudaMalloc((void **)&b->q, (size_t)need * sizeof(QEntry));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->q_count, sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc((void **)&b->q, (size_t)queue_bytes(need));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->q_count, kQueueCountBytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->item_counter, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_fwd, sizeof(BatchProblem) * n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bwd, sizeof(BatchProblem) * n);

@@ -35,7 +35,7 @@ namespace tp {
 #define FULL_MASK 0xffffffffu
 
 struct LocalCnt {
-    unsigned rays, hits, segs, fp64, exact, sos, nodes, faces;
+    unsigned rays, hits, segs, fp64, exact, sos, nodes, faces, graze;
 };
 
 __device__ __forceinline__ void report_error(DevCounters *C, int code) {
@@ -44,12 +44,12 @@ __device__ __forceinline__ void report_error(DevCounters *C, int code) {
 }
 
 __device__ __forceinline__ void flush_counters(DevCounters *C, const LocalCnt &c) {
-    unsigned v[8] = {c.rays, c.hits, c.segs, c.fp64, c.exact, c.sos, c.nodes, c.faces};
-    unsigned long long *dst[8] = {&C->rays, &C->hits, &C->segments, &C->fp64,
-                                  &C->exact, &C->sos, &C->bvh_nodes, &C->bvh_faces};
+    unsigned v[9] = {c.rays, c.hits, c.segs, c.fp64, c.exact, c.sos, c.nodes, c.faces, c.graze};
+    unsigned long long *dst[9] = {&C->rays, &C->hits, &C->segments, &C->fp64, &C->exact,
+                                  &C->sos, &C->bvh_nodes, &C->bvh_faces, &C->grazing};
     int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 9; ++k) {
         unsigned s = __reduce_add_sync(FULL_MASK, v[k]);
         if (lane == 0 && s) atomicAdd(dst[k], (unsigned long long)s);
     }
@@ -255,6 +255,62 @@ __device__ __noinline__ int step_robust(const KParams *p, int64_t ray, int h, in
     return x;
 }
 
+// Exit point of a step whose signs are certain but whose exit face the ray
+// meets at a grazing angle.  The FP32 vertices carry rounding of ~u |v|, which
+// moves the face plane by that much and the crossing by ~u |v| / sin(angle)
+// along the ray (measured: 2e-5 at sin = 1e-3 on a unit cube); the FP64
+// vertices and weights place it to FP64 accuracy.  Weights as in step_robust:
+// exit face (n, k_y, k_z), w_y = -side(n->k_z), w_z = side(n->k_y),
+// w_n = side(k_y->k_z).
+__device__ __forceinline__ d3 crossing64d(const KParams &p, const d3 &S, const d3 &P, int h, int f,
+                                          int x) {
+    const TetRec64 *r = p.m.rec64 + h;
+    int k3[3];
+    face_triple(f, k3[0], k3[1], k3[2]);
+    const d3 n = rec64_vertex(r, f);
+    const d3 ky = rec64_vertex(r, k3[(x + 1) % 3]), kz = rec64_vertex(r, k3[(x + 2) % 3]);
+    const d3 d = sub(P, S);
+    const Filt64Vert Vn = filt64_vert(S, d, n), Vy = filt64_vert(S, d, ky);
+    double sy, sz, sn;
+    filt64_side(Vn, ky, sy);
+    filt64_side(Vn, kz, sz);
+    filt64_side(Vy, kz, sn);
+    const double wy = fmax(0.0, -sz), wz = fmax(0.0, sy), wn = fmax(0.0, sn);
+    const double W = wn + wy + wz;
+    if (W == 0.0) return P;
+    const double iw = 1.0 / W;
+    return d3axpy(wz * iw, sub(kz, n), d3axpy(wy * iw, sub(ky, n), n));
+}
+// The same for the robust walk (which calls out of line anyway), in FP32.
+__device__ __noinline__ f3 crossing64(const KParams *p, int64_t ray, int h, int f, int x) {
+    d3 S, P;
+    load_ray(*p, ray, S, P);
+    return tof(crossing64d(*p, S, P, h, f, x));
+}
+
+// Entry point through boundary face (h, f) when its signs are certain but the
+// ray meets it at a grazing angle (as crossing64): weights w_a = side(b->c),
+// w_b = side(c->a), w_c = side(a->b) of the face triple in FP64.
+__device__ __noinline__ f3 entry64(const KParams *p, int64_t ray, int h, int f) {
+    d3 S, P;
+    load_ray(*p, ray, S, P);
+    const TetRec64 *r = p->m.rec64 + h;
+    int ia, ib, ic;
+    face_triple(f, ia, ib, ic);
+    const d3 a = rec64_vertex(r, ia), b = rec64_vertex(r, ib), c = rec64_vertex(r, ic);
+    const d3 d = sub(P, S);
+    const Filt64Vert Va = filt64_vert(S, d, a), Vb = filt64_vert(S, d, b);
+    double sab, sbc, sca;
+    filt64_side(Va, b, sab);
+    filt64_side(Vb, c, sbc);
+    filt64_side(filt64_vert(S, d, c), a, sca);
+    const double wa = fmax(0.0, sbc), wb = fmax(0.0, sca), wc = fmax(0.0, sab);
+    const double W = wa + wb + wc;
+    if (W == 0.0) return tof(a);
+    const double iw = 1.0 / W;
+    return tof(d3axpy(wc * iw, sub(c, a), d3axpy(wb * iw, sub(b, a), a)));
+}
+
 // Entry test of boundary face (h, f) in FP64 (+exact, symbolic).  known[j]:
 // certain signs of side(a->b), side(b->c), side(c->a) or 0.  Returns 1 if the
 // line enters the tet through the face, with the entry point in X.
@@ -448,6 +504,30 @@ __device__ __forceinline__ void defer_append(const KParams &p, bool want, int64_
     }
 }
 
+// Queues the FP64 correction of a grazing crossing (see XFix); false when the
+// chunk's fix list is full.  Called in divergent code: the lanes that arrive
+// together share one atomic on the list's counter.
+__device__ __forceinline__ bool xfix_append(const KParams &p, int64_t ray, int h, int hn,
+                                            const f3 &X, int fx) {
+    const unsigned long long cap = (unsigned long long)(p.q_cap / 2);
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(p.q_count + 1, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+    if (slot >= cap) return false;
+    XFix *e = queue_fixes(p.q, p.q_cap) + slot;
+    e->ray = ray | p.qtag;
+    e->h = h;
+    e->hn = hn;
+    e->x = X.x;
+    e->y = X.y;
+    e->z = X.z;
+    e->fx = fx;
+    return true;
+}
+
 // First segment-buffer slot of cone ray `ray` (MODE_SEG): its tile block's
 // offset, minus the chunk's base, plus the ray's offset inside the block.
 __device__ __forceinline__ int64_t seg_slot(const KParams &p, int64_t ray) {
@@ -466,7 +546,7 @@ __device__ __forceinline__ int64_t seg_slot(const KParams &p, int64_t ray) {
 template <int C, int MODE, bool ROBUST, int ENTRY = ENTRY_BVH>
 __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snodes, int nsm,
                                            int64_t ray, const bool valid, const QEntry *qe) {
-    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     Filt32Ray fr;
     f3 Xin = {0.f, 0.f, 0.f};
     float il = 0.f;  // 1 / |d|
@@ -502,8 +582,21 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 int hf = __float_as_int(A.w);
                 if (gab > 0 && gbc > 0 && gca > 0 &&
                     sab + sbc + sca >= (float)TP_WEIGHT_MARGIN * (bab + bbc + bca)) {
-                    float iw = __frcp_rn(sab + sbc + sca);
-                    Xin = f3axpy(sca * iw, sub(b, a), f3axpy(sab * iw, sub(c, a), a));
+                    const f3 N = crossf(sub(b, a), sub(c, a));
+                    if ((sab + sbc + sca) * il * (1.0f / TP_GRAZE_SIN) <
+                        fabsf(N.x) + fabsf(N.y) + fabsf(N.z)) {
+                        // grazing entry face: the entry point comes from the FP64
+                        // records, in the robust walk
+                        if (!ROBUST) {
+                            deferred = true;
+                            h = -1;
+                            return true;
+                        }
+                        Xin = entry64(&p, ray, hf >> 2, hf & 3);
+                    } else {
+                        float iw = __frcp_rn(sab + sbc + sca);
+                        Xin = f3axpy(sca * iw, sub(b, a), f3axpy(sab * iw, sub(c, a), a));
+                    }
                 } else if (!ROBUST) {
                     deferred = true;  // undecided entry face: finish the ray robustly
                     h = -1;           // (queued with fs = -1: resume from the entry search)
@@ -560,7 +653,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
     int64_t spos = 0;
     if (MODE == MODE_SEG && valid) spos = seg_slot(p, ray) + steps;
     flush_counters(p.m.counters, cnt);
-    cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 
     const TetRec32 *rec = p.m.rec32;
     const float *mu = reinterpret_cast<const float *>(p.in);
@@ -569,7 +662,7 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
 
     while (__any_sync(FULL_MASK, alive)) {
         bool did = alive;
-        const int hcur = h, fcur = f;
+        const int hcur = h;
         bool defer_now = false;
         float len = 0.f;
         if (alive) {
@@ -608,14 +701,34 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 f3 ey = x0 ? eb : (x1 ? ec : ea), ez = x0 ? ec : (x1 ? ea : eb);
                 float wy = x0 ? -sc : (x1 ? -sa : -sb), wz = x0 ? sb : (x1 ? sc : sa);
                 float bw = x0 ? bc + bb : (x1 ? ba + bc : bb + ba);
-                float W = dotf(fr.d, crossf(ey, ez));
-                // the ray nearly lies in the exit face: place the crossing exactly
+                const f3 N = crossf(ey, ez);
+                float W = dotf(fr.d, N);
+                // the crossing nearly coincides with a vertex or edge of the
+                // exit face (weights within the margin of their bounds):
+                // finish the ray robustly
                 fast = x < 0 || wy + wz >= (float)TP_WEIGHT_MARGIN * bw;
                 if (fast) {
                     // approximate reciprocal (2 ulp): W only scales the crossing
                     // offset, whose weights carry far larger certified errors
                     float iw = __fdividef(1.0f, W);
                     Xout = f3axpy(wz * iw, ez, f3axpy(wy * iw, ey, n));
+                    // grazing exit face: |W| / |d| = |N| sin(angle); with the 1-norm
+                    // of N this flags every sine below TP_GRAZE_SIN (and some up to
+                    // sqrt(3) times it)
+                    if (x >= 0 && fabsf(W) * il * (1.0f / TP_GRAZE_SIN) <
+                                      fabsf(N.x) + fabsf(N.y) + fabsf(N.z)) {
+                        ++cnt.graze;
+                        if (ROBUST || (MODE != MODE_FWD && MODE != MODE_BWD && MODE != MODE_BWD64)) {
+                            Xout = crossing64(&p, ray, h, f, x);
+                        } else {
+                            // keep the FP32 crossing and queue its FP64 correction; a ray
+                            // whose segment is clipped at t = 0 here, or that finds the
+                            // fix list full, is finished by the robust walk instead
+                            const int nx = __float_as_int(x == 0 ? va.w : (x == 1 ? vb.w : vc.w));
+                            defer_now = clip0 || !xfix_append(p, ray, h, nx < 0 ? -1 : nx >> 2, Xout,
+                                                              f | (x << 2));
+                        }
+                    }
                 }
             }
             if (!fast) {
@@ -696,10 +809,40 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
             }
             ++spos;
         }
-        if (MODE == MODE_BWD64 && did) {  // FP64 accumulation: no drift with many segments
-            double *acc64 = reinterpret_cast<double *>(p.out) + (int64_t)hcur * C;
+        if (MODE == MODE_BWD64) {  // FP64 accumulation: no drift with many segments
+            if (!ROBUST && p.scatter == TETPROJ_SCATTER_WARP) {
+                // lanes at the same tet add their contributions in FP64 first
+                // (in lane order), then one reduction per tet and channel
+                unsigned peers = __match_any_sync(FULL_MASK, did ? hcur : -1 - lane);
+                if (did) {
+                    double v[C];
 #pragma unroll
-            for (int cc = 0; cc < C; ++cc) red_add_global(acc64 + cc, (double)(len * yv[cc]));
+                    for (int cc = 0; cc < C; ++cc) v[cc] = (double)(len * yv[cc]);
+                    if (__popc(peers) > 1) {
+                        double t[C];
+#pragma unroll
+                        for (int cc = 0; cc < C; ++cc) t[cc] = 0.0;
+                        unsigned mm = peers;
+                        while (mm) {
+                            const int src = __ffs(mm) - 1;
+                            mm &= mm - 1;
+#pragma unroll
+                            for (int cc = 0; cc < C; ++cc) t[cc] += __shfl_sync(peers, v[cc], src);
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < C; ++cc) v[cc] = t[cc];
+                    }
+                    if (lane == __ffs(peers) - 1) {
+                        double *acc64 = reinterpret_cast<double *>(p.out) + (int64_t)hcur * C;
+#pragma unroll
+                        for (int cc = 0; cc < C; ++cc) red_add_global(acc64 + cc, v[cc]);
+                    }
+                }
+            } else if (did) {
+                double *acc64 = reinterpret_cast<double *>(p.out) + (int64_t)hcur * C;
+#pragma unroll
+                for (int cc = 0; cc < C; ++cc) red_add_global(acc64 + cc, (double)(len * yv[cc]));
+            }
         }
         if (MODE == MODE_BWD) {
             if (!ROBUST && p.scatter == TETPROJ_SCATTER_WARP) {
@@ -804,6 +947,79 @@ __global__ void __launch_bounds__(128, 4) k_resume32(const __grid_constant__ KPa
     }
 }
 
+// Correction of one queued grazing crossing (see XFix): the crossing placed
+// again from the FP64 records moves by delta along the ray, so the segment
+// that ends there (tet h) grows by delta and the one that starts there (tet
+// hn) shrinks by it.  Forward: proj += delta (mu_h - mu_hn); backward:
+// acc_h += delta y, acc_hn -= delta y.
+template <int C, int MODE>
+__device__ __forceinline__ void fix_apply(const KParams &p, const XFix &r) {
+    const int64_t ray = r.ray & ((int64_t(1) << 40) - 1);  // drop a batched launch's problem tag
+    d3 S, P;
+    load_ray(p, ray, S, P);
+    const d3 X = crossing64d(p, S, P, r.h, r.fx & 3, r.fx >> 2);
+    const d3 d = sub(P, S);
+    const double delta = ((X.x - (double)r.x) * d.x + (X.y - (double)r.y) * d.y +
+                          (X.z - (double)r.z) * d.z) / sqrt(dotd(d, d));
+    if (MODE == MODE_FWD) {
+        const float *mu = reinterpret_cast<const float *>(p.in);
+        float *o = reinterpret_cast<float *>(p.out) + ray * C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const double dm = (double)__ldg(mu + (int64_t)r.h * C + c) -
+                              (r.hn >= 0 ? (double)__ldg(mu + (int64_t)r.hn * C + c) : 0.0);
+            atomicAdd(o + c, (float)(delta * dm));
+        }
+    } else if (MODE == MODE_BWD) {
+        const float *y = reinterpret_cast<const float *>(p.in) + ray * C;
+        float *acc = reinterpret_cast<float *>(p.out);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float v = (float)(delta * (double)__ldg(y + c));
+            red_add_global(acc + (int64_t)r.h * C + c, v);
+            if (r.hn >= 0) red_add_global(acc + (int64_t)r.hn * C + c, -v);
+        }
+    } else if (MODE == MODE_BWD64) {
+        const float *y = reinterpret_cast<const float *>(p.in) + ray * C;
+        double *acc = reinterpret_cast<double *>(p.out);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const double v = delta * (double)__ldg(y + c);
+            red_add_global(acc + (int64_t)r.h * C + c, v);
+            if (r.hn >= 0) red_add_global(acc + (int64_t)r.hn * C + c, -v);
+        }
+    }
+}
+
+// The fixes a chunk's fast walk queued (after its resume kernel, which may
+// still write the forward results of deferred rays).
+template <int C, int MODE>
+__global__ void __launch_bounds__(128) k_fix32(const __grid_constant__ KParams p) {
+    const XFix *xf = queue_fixes(p.q, p.q_cap);
+    const unsigned long long n = min(p.q_count[1], (unsigned long long)(p.q_cap / 2));
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += stride)
+        fix_apply<C, MODE>(p, xf[k]);
+}
+
+// Modes whose fast walk queues crossing fixes (the others place grazing
+// crossings in FP64 in place).
+template <int MODE>
+constexpr bool queues_fixes() {
+    return MODE == MODE_FWD || MODE == MODE_BWD || MODE == MODE_BWD64;
+}
+
+template <int C, int MODE>
+static cudaError_t launch_fix(const KParams &p, unsigned grid, cudaStream_t stream) {
+    if constexpr (queues_fixes<MODE>()) {
+        k_fix32<C, MODE><<<grid, 128, 0, stream>>>(p);
+        note_launch();
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
 // ========================================================= plain FP64 walk
 
 // FP64 sign of side(n->k) for the plain path: FP64 filter, then exact/SoS.
@@ -822,7 +1038,7 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
     __syncthreads();
     const BvhNode *snodes = reinterpret_cast<const BvhNode *>(smem);
 
-    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int64_t ray = 0;
     const bool valid = thread_ray(p, ray);
     d3 S = {0, 0, 0}, d = {0, 0, 0}, dhat = {0, 0, 0}, Xin = {0, 0, 0};
@@ -884,7 +1100,7 @@ __global__ void __launch_bounds__(256) k_walk64(const __grid_constant__ KParams 
     }
 
     flush_counters(p.m.counters, cnt);
-    cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const double *mu = reinterpret_cast<const double *>(p.in);
     double *accbuf = reinterpret_cast<double *>(p.out);
     const int lane = threadIdx.x & 31;
@@ -1199,6 +1415,34 @@ __global__ void __launch_bounds__(128, 4)
     }
 }
 
+// The fixes one round of the batched walk queued; each names its problem in
+// the ray's tag bits.
+template <int C, int MODE>
+__global__ void __launch_bounds__(128) k_batch_fix32(const BatchProblem *__restrict__ probs,
+                                                     QEntry *q, const unsigned long long *q_count,
+                                                     int64_t q_cap) {
+    const XFix *xf = queue_fixes(q, q_cap);
+    const unsigned long long n = min(q_count[1], (unsigned long long)(q_cap / 2));
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += stride) {
+        const XFix r = xf[k];
+        fix_apply<C, MODE>(probs[(int)(r.ray >> TP_BATCH_TAG_SHIFT)].p, r);
+    }
+}
+
+template <int C, int MODE>
+static cudaError_t launch_batch_fix(const BatchProblem *probs, QEntry *q,
+                                    const unsigned long long *q_count, int64_t q_cap,
+                                    unsigned grid, cudaStream_t stream) {
+    if constexpr (queues_fixes<MODE>()) {
+        k_batch_fix32<C, MODE><<<grid, 128, 0, stream>>>(probs, q, q_count, q_cap);
+        note_launch();
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
 static size_t batch_smem(int smem_nodes) {
     return (size_t)(TP_BATCH_THREADS / 32) * (kBatchParamVec * 16 + (size_t)smem_nodes * sizeof(BvhNode));
 }
@@ -1275,7 +1519,7 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
             round_of(i, r0, r1);
             if (i >= 2) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
             if (e == cudaSuccess) e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
-            if (e == cudaSuccess) e = cudaMemsetAsync(cj, 0, sizeof(unsigned long long), stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(cj, 0, kQueueCountBytes, stream);
             if (e != cudaSuccess) break;
             k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
                 probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, qj, cj, wait);
@@ -1287,6 +1531,7 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
             k_batch_resume32<C, MODE><<<rgrid, 128, 0, ov->aux>>>(probs, qj, cj, q_cap);
             note_launch();
             e = cudaGetLastError();
+            if (e == cudaSuccess) e = launch_batch_fix<C, MODE>(probs, qj, cj, q_cap, rgrid, ov->aux);
             if (e == cudaSuccess) e = merge_all(ov->aux);
             if (e == cudaSuccess) e = cudaEventRecord(ov->ev_res[j], ov->aux);
             used |= 1 << j;
@@ -1299,7 +1544,7 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
         int64_t r0, r1;
         round_of(i, r0, r1);
         cudaError_t e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(q_count, 0, sizeof(unsigned long long), stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(q_count, 0, kQueueCountBytes, stream);
         if (e != cudaSuccess) return e;
         k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
             probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, q, q_count, wait);
@@ -1307,6 +1552,7 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
         k_batch_resume32<C, MODE><<<rgrid, 128, 0, stream>>>(probs, q, q_count, q_cap);
         note_launch();
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_batch_fix<C, MODE>(probs, q, q_count, q_cap, rgrid, stream);
         if (e == cudaSuccess) e = merge_all(stream);
         if (e != cudaSuccess) return e;
     }
@@ -1440,7 +1686,7 @@ __global__ void __launch_bounds__(128) k_walk_mt(const __grid_constant__ KParams
     const f3 d32 = {(float)(P.x - S.x), (float)(P.y - S.y), (float)(P.z - S.z)};
     const float smax = fmaxf(fmaxf(fabsf(S32.x), fabsf(S32.y)), fabsf(S32.z));
     const float margin = 16.f * 5.9604645e-8f * (smax + p.m.radius);
-    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    LocalCnt cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     T tbest = T(0);
     int hbest = -1, fbest = -1, ubest = 0, obest = 0;
     bvh_search(p.m, nullptr, 0, S32, safe_inv(d32), margin, cnt, [&](int q) -> bool {
@@ -1632,7 +1878,7 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
             pc.q_count = j ? ov->q2_count : p.q_count;
             const int64_t nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
             if (i >= 2) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
-            if (e == cudaSuccess) e = cudaMemsetAsync(pc.q_count, 0, sizeof(unsigned long long), stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(pc.q_count, 0, kQueueCountBytes, stream);
             if (e != cudaSuccess) break;
             k_walk32<C, MODE, ENTRY><<<(unsigned)nb, threads, smem, stream>>>(pc);
             note_launch();
@@ -1643,6 +1889,7 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
             k_resume32<C, MODE><<<rgrid, 128, smem, ov->aux>>>(pc);
             note_launch();
             e = cudaGetLastError();
+            if (e == cudaSuccess) e = launch_fix<C, MODE>(pc, rgrid, ov->aux);
             if (e == cudaSuccess && mg) e = launch_acc_merge(mg->acc32, mg->acc64, mg->n, ov->aux);
             if (e == cudaSuccess) e = cudaEventRecord(ov->ev_res[j], ov->aux);
             used |= 1 << j;
@@ -1654,13 +1901,14 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
     for (int64_t b0 = 0; b0 < nblocks; b0 += chunk) {
         int64_t nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
         p.block_offset = b0;
-        cudaError_t e = cudaMemsetAsync(p.q_count, 0, sizeof(unsigned long long), stream);
+        cudaError_t e = cudaMemsetAsync(p.q_count, 0, kQueueCountBytes, stream);
         if (e != cudaSuccess) return e;
         k_walk32<C, MODE, ENTRY><<<(unsigned)nb, threads, smem, stream>>>(p);
         note_launch();
         k_resume32<C, MODE><<<rgrid, 128, smem, stream>>>(p);
         note_launch();
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_fix<C, MODE>(p, rgrid, stream);
         if (e == cudaSuccess && mg) e = launch_acc_merge(mg->acc32, mg->acc64, mg->n, stream);
         if (e != cudaSuccess) return e;
     }
@@ -1694,13 +1942,15 @@ static cudaError_t launch_blocks_mode(const KParams &p0, int64_t b0, int64_t b1,
     if (b1 <= b0) return cudaSuccess;
     if ((b1 - b0) * threads > p.q_cap || b1 - b0 > 0x7fffffff) return cudaErrorInvalidValue;
     p.block_offset = b0;
-    cudaError_t e = cudaMemsetAsync(p.q_count, 0, sizeof(unsigned long long), stream);
+    cudaError_t e = cudaMemsetAsync(p.q_count, 0, kQueueCountBytes, stream);
     if (e != cudaSuccess) return e;
     k_walk32<C, MODE><<<(unsigned)(b1 - b0), threads, smem, stream>>>(p);
     note_launch();
     k_resume32<C, MODE><<<(unsigned)(4 * sm_count()), 128, smem, stream>>>(p);
     note_launch();
-    return cudaGetLastError();
+    cudaError_t e2 = cudaGetLastError();
+    if (e2 == cudaSuccess) e2 = launch_fix<C, MODE>(p, (unsigned)(4 * sm_count()), stream);
+    return e2;
 }
 
 cudaError_t launch_walk_blocks(const KParams &p, int channels, int mode, int64_t b0, int64_t b1,

@@ -30,6 +30,33 @@ struct __align__(16) QEntry {
 };
 static_assert(sizeof(QEntry) == 64, "QEntry must be 64 bytes");
 
+// A crossing the fast walk placed in FP32 although the ray meets the face at a
+// grazing angle (FP32 vertex rounding moves such a crossing by ~u|v|/sin along
+// the ray): the correction kernel places it again from the FP64 records and
+// moves the difference between the two segments that meet there (a ray's
+// integral is linear in each crossing's position along it).
+struct __align__(16) XFix {
+    int64_t ray;    // ray index (| qtag in batched launches)
+    int32_t h;      // tet the crossing leaves
+    int32_t hn;     // tet it enters, or -1 (the ray leaves the mesh)
+    float x, y, z;  // the FP32 crossing the walk used
+    int32_t fx;     // entry face of h | exit index << 2
+};
+static_assert(sizeof(XFix) == 32, "XFix must be 32 bytes");
+
+// A deferral queue's allocation also holds the crossing fixes of the same
+// launch chunk: q[0 .. cap) QEntry, then (cap / 2) XFix; its count words are
+// q_count[0] (deferred rays) and q_count[1] (fixes).  A walk that finds the
+// fix list full defers the ray instead (the resume walk places crossings in
+// FP64 itself).
+inline int64_t queue_bytes(int64_t cap) {
+    return cap * (int64_t)sizeof(QEntry) + (cap / 2) * (int64_t)sizeof(XFix);
+}
+constexpr size_t kQueueCountBytes = 2 * sizeof(unsigned long long);
+__host__ __device__ inline XFix *queue_fixes(QEntry *q, int64_t cap) {
+    return reinterpret_cast<XFix *>(q + cap);
+}
+
 struct KParams {
     MeshView m;
     // ray source: cone-beam tiles (src_kind 0) or explicit rays (1)

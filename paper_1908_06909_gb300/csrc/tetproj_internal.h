@@ -79,6 +79,7 @@ struct DevCounters {
     unsigned long long rays, hits, segments, fp64, exact, sos, bvh_nodes, bvh_faces, deferred;
     int error;
     int error_count;
+    unsigned long long grazing;  // crossings placed again from the FP64 records
 };
 
 struct MeshView {

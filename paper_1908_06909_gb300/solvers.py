@@ -75,24 +75,29 @@ def ossart(mesh, geo: Geometry, b, niter: int = 50, block: int = 20, lam: float 
 
 
 def cgls(mesh, geo: Geometry, b, niter: int = 20, x0=None, options=None, callback=None):
-    """CGLS for min |A x - b|; callback(k, x) after each iteration."""
+    """CGLS for min |A x - b|; callback(k, x) after each iteration.
+
+    Every scalar stays on the device (no host synchronisation inside the
+    loop, so the iterations queue back to back and can be captured in a CUDA
+    graph): a zero step length or direction, where the textbook loop would
+    stop, makes the remaining iterations leave x unchanged instead."""
     import torch
     x = torch.zeros(mesh.nt, dtype=b.dtype, device=b.device) if x0 is None else x0.clone()
     r = b - forward(mesh, geo, x, options=options)
     s = backward(mesh, geo, r, options=options)
     p = s.clone()
     gamma = torch.dot(s, s)
+    zero = torch.zeros((), dtype=b.dtype, device=b.device)
     for k in range(niter):
         q = forward(mesh, geo, p, options=options)
         qq = torch.dot(q.reshape(-1), q.reshape(-1))
-        if float(qq) == 0.0 or float(gamma) == 0.0:
-            break
-        alpha = gamma / qq
+        alpha = torch.where(qq > 0, gamma / torch.where(qq > 0, qq, 1), zero)
         x += alpha * p
         r -= alpha * q
         s = backward(mesh, geo, r, options=options)
         gamma_new = torch.dot(s, s)
-        p = s + (gamma_new / gamma) * p
+        beta = torch.where(gamma > 0, gamma_new / torch.where(gamma > 0, gamma, 1), zero)
+        p = s + beta * p
         gamma = gamma_new
         if callback is not None:
             callback(k, x)

@@ -123,3 +123,25 @@ def test_cgls_fp32_normal_residual_decreases(tp):
     assert all(norms[k + 1] < norms[k] * 1.5 for k in range(len(norms) - 1))
     assert norms[-1] < 0.05 * norms[0]
     assert float((x - xt).norm() / xt.norm()) < 0.25
+
+
+def test_cgls_no_host_sync(tp, small):
+    """CGLS keeps its scalars on the device: no torch operation in its loop
+    synchronises with the host (after a first call has allocated the mesh's
+    workspace), and the result equals the oracle's iterates as above."""
+    import torch
+    from paper_1908_06909_gb300 import solvers
+    verts, tets, geom, x_true, b = small
+    mesh = tp.Mesh(verts, tets)
+    geo = tp.Geometry.from_cone(geom)
+    bt = torch.tensor(b.reshape(geo.shape), dtype=torch.float64, device="cuda")
+    solvers.cgls(mesh, geo, bt, niter=1)
+    torch.cuda.synchronize()
+    torch.cuda.set_sync_debug_mode("error")
+    try:
+        x = solvers.cgls(mesh, geo, bt, niter=4)
+    finally:
+        torch.cuda.set_sync_debug_mode("default")
+    f, bk = OS.cone_operators(verts, tets, geom)
+    _, hist = OS.cgls(f, bk, b, np.zeros(tets.shape[0]), 4)
+    assert np.linalg.norm(x.cpu().numpy() - hist[3]) <= 1e-9 * np.linalg.norm(hist[3])
