@@ -79,6 +79,9 @@ struct tetproj_mesh {
     int64_t q_cap = 0;
     ResumeOverlap ov = {};
     bool ov_ready = false;
+    // candidate entry faces per pixel of a launch chunk's angles (cone rays)
+    int32_t *emap = nullptr;
+    int64_t emap_cap = 0;
     int64_t base_bytes = 0;
     SegPlan plan;
     SortWs sort;
@@ -234,6 +237,7 @@ static void mesh_free(tetproj_mesh *m) {
         for (int j = 0; j < 2; ++j) cudaFree(m->ws[i][j]);
     cudaFree(m->q);
     cudaFree(m->q_count);
+    cudaFree(m->emap);
     delete m;
 }
 
@@ -296,7 +300,7 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *m, tetproj_mesh_info *o
     o->nbvh_nodes = m->nnodes;
     o->nflipped = m->nflipped;
     int64_t b = m->base_bytes + queue_bytes(m->q_cap) * (m->ov_ready ? 2 : 1) +
-                (m->q_count ? (int64_t)kQueueCountBytes : 0) +
+                (m->q_count ? (int64_t)kQueueCountBytes : 0) + m->emap_cap * (int64_t)sizeof(int32_t) +
                 m->plan.bytes + m->sort.bytes + m->rstar_bytes;
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) b += m->ws_bytes[i][j];
@@ -582,8 +586,38 @@ static tetproj_status attach_queue(tetproj_mesh *m, KParams &p, const tetproj_op
     return TETPROJ_OK;
 }
 
+// The entry map of the fast walk (KParams::emap): for filtered cone-beam
+// calls with the BVH entry whose source circle lies outside the mesh's
+// bounding sphere, a buffer for the angles one launch chunk touches.  Only a
+// hint (the walk verifies every candidate), so it is left out under graph
+// capture when not yet allocated, or when it would exceed 256 MB.
+static tetproj_status attach_emap(tetproj_mesh *m, KParams &p, const tetproj_options &o,
+                                  const tetproj_geometry *geo, cudaStream_t s) {
+    p.emap_buf = nullptr;
+    p.emap_cap = 0;
+    if (o.precision != TETPROJ_FILTERED || p.entry != ENTRY_BVH || p.src_kind != 0 || !geo ||
+        !(geo->dso > 1.75 * (double)m->radius) || p.q_cap <= 0)
+        return TETPROJ_OK;
+    const int64_t pix = (int64_t)geo->nu * geo->nv;
+    const int64_t need = (p.q_cap / pix + 2) * pix;
+    if (need > (int64_t(1) << 26)) return TETPROJ_OK;
+    if (m->emap_cap < need) {
+        if (capturing(s)) return TETPROJ_OK;
+        cudaDeviceSynchronize();  // an earlier call may still read the old map
+        cudaFree(m->emap);
+        m->emap = nullptr;
+        m->emap_cap = 0;
+        TP_CUDA(cudaMalloc((void **)&m->emap, (size_t)need * sizeof(int32_t)));
+        m->emap_cap = need;
+    }
+    p.emap_buf = m->emap;
+    p.emap_cap = m->emap_cap;
+    return TETPROJ_OK;
+}
+
 static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
-                                  const void *mu, void *out, cudaStream_t s) {
+                                  const void *mu, void *out, cudaStream_t s,
+                                  const tetproj_geometry *geo = nullptr) {
     if (p.entry == ENTRY_RSTAR) {  // the paper's entry structure: filtered path, C = 1
         if (o.precision != TETPROJ_FILTERED || o.channels != 1) return TETPROJ_ERR_ARG;
         tetproj_status st = ensure_rstar(m, p);
@@ -591,6 +625,7 @@ static tetproj_status run_forward(tetproj_mesh *m, KParams &p, const tetproj_opt
     }
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
     if (st == TETPROJ_OK) st = attach_queue(m, p, o, s);
+    if (st == TETPROJ_OK) st = attach_emap(m, p, o, geo, s);
     if (st != TETPROJ_OK) return st;
     void *ws = m->ws[o.precision == TETPROJ_PLAIN_FP64][o.channels == 4];
     int f64 = o.precision == TETPROJ_PLAIN_FP64;
@@ -634,7 +669,8 @@ static int64_t dense_chunk_rays(int64_t nt) {
 }
 
 static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_options &o,
-                                   const void *y, void *mu_out, cudaStream_t s) {
+                                   const void *y, void *mu_out, cudaStream_t s,
+                                   const tetproj_geometry *geo = nullptr) {
     if (rstar_unsupported(o)) return TETPROJ_ERR_ARG;
     if ((o.flags & TETPROJ_FLAG_ACC64) && o.precision == TETPROJ_FILTERED &&
         o.scatter == TETPROJ_SCATTER_SORT)
@@ -643,6 +679,7 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
         // FP32 walk, FP64 accumulator (the plain path's workspace), one rounding at the end
         tetproj_status st = ensure_ws(m, TETPROJ_PLAIN_FP64, o.channels);
         if (st == TETPROJ_OK) st = attach_queue(m, p, o, s);
+        if (st == TETPROJ_OK) st = attach_emap(m, p, o, geo, s);
         if (st != TETPROJ_OK) return st;
         void *ws = m->ws[1][o.channels == 4];
         TP_CUDA(cudaMemsetAsync(ws, 0, (size_t)m->ws_bytes[1][o.channels == 4], s));
@@ -656,6 +693,7 @@ static tetproj_status run_backward(tetproj_mesh *m, KParams &p, const tetproj_op
     }
     tetproj_status st = ensure_ws(m, o.precision, o.channels);
     if (st == TETPROJ_OK) st = attach_queue(m, p, o, s);
+    if (st == TETPROJ_OK) st = attach_emap(m, p, o, geo, s);
     if (st != TETPROJ_OK) return st;
     void *ws = m->ws[o.precision == TETPROJ_PLAIN_FP64][o.channels == 4];
     int f64 = o.precision == TETPROJ_PLAIN_FP64;
@@ -826,7 +864,7 @@ tetproj_status tetproj_forward(const tetproj_mesh *mesh, const tetproj_geometry 
     tetproj_mesh *m = const_cast<tetproj_mesh *>(mesh);
     KParams p = base_params(m, o);
     set_cone(p, geo);
-    return run_forward(m, p, o, mu, proj, (cudaStream_t)stream);
+    return run_forward(m, p, o, mu, proj, (cudaStream_t)stream, geo);
 }
 
 tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry *geo,
@@ -845,7 +883,7 @@ tetproj_status tetproj_backward(const tetproj_mesh *mesh, const tetproj_geometry
             return TETPROJ_ERR_ARG;
         return run_backward_sort(m, geo, p, o, proj, mu_out, (cudaStream_t)stream);
     }
-    return run_backward(m, p, o, proj, mu_out, (cudaStream_t)stream);
+    return run_backward(m, p, o, proj, mu_out, (cudaStream_t)stream, geo);
 }
 
 tetproj_status tetproj_forward_rays(const tetproj_mesh *mesh, const double *src,

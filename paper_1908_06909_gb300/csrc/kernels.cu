@@ -612,10 +612,21 @@ __device__ __forceinline__ void walk32_ray(const KParams &p, const BvhNode *snod
                 alive = true;
                 return true;
             };
-            if (ENTRY == ENTRY_RSTAR)
+            if (ENTRY == ENTRY_RSTAR) {
                 rstar_search(p.m, S32, inv, margin, cnt, entry_test);
-            else
-                bvh_search(p.m, snodes, nsm, S32, inv, margin, cnt, entry_test);
+            } else {
+                // the face the entry map drew at this ray's pixel, if it is the one
+                bool found = false;
+                if (!ROBUST && p.emap) {
+                    const int64_t r = ray - p.emap_base;
+                    const int q = (r >= 0 && r < p.emap_len) ? __ldg(p.emap + r) : -1;
+                    if (q >= 0 && q < p.m.nb) {
+                        ++cnt.faces;
+                        found = entry_test(q);
+                    }
+                }
+                if (!found) bvh_search(p.m, snodes, nsm, S32, inv, margin, cnt, entry_test);
+            }
             if (alive) {
                 cnt.hits = 1;
                 // entry behind the source (source inside the mesh, or the mesh behind
@@ -1840,6 +1851,97 @@ __global__ void k_side(const double *S, const double *P, const double *p, const 
     stage[k] = (int8_t)st;
 }
 
+// ============================================================ entry map
+
+// Candidate entry faces for the cone rays of angles a0 .. a0 + gridDim.y - 1
+// (KParams::emap).  A convex mesh seen from a source outside it projects onto
+// the detector as the union of the projections of the boundary faces that
+// face the source, and a ray entering through a face passes through the
+// face's projection; so each such face writes its index to the pixels whose
+// centres its projection covers.  The projection is computed in FP64 and
+// grown by 1e-3 pixel; faces within 1e-6 of edge-on are drawn too.  Pixels on
+// shared edges get one of the faces.  Nothing here is trusted: the walk tests
+// the face with its exact entry test and searches the BVH when it fails.
+__global__ void __launch_bounds__(128) k_entry_raster(const MeshView m, const GeoView g, int a0,
+                                                      int32_t *emap) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ai = blockIdx.y;
+    if (q >= m.nb) return;
+    const AngleFrame *F = g.frames + a0 + ai;
+    const d3 S = mk(__ldg(&F->S[0]), __ldg(&F->S[1]), __ldg(&F->S[2]));
+    const d3 Cd = mk(__ldg(&F->C[0]), __ldg(&F->C[1]), __ldg(&F->C[2]));
+    const d3 U = mk(__ldg(&F->U[0]), __ldg(&F->U[1]), __ldg(&F->U[2]));
+    const d3 V = mk(__ldg(&F->V[0]), __ldg(&F->V[1]), __ldg(&F->V[2]));
+    const float4 *bf = reinterpret_cast<const float4 *>(m.bfaces + q);
+    const float4 A = __ldg(bf), B = __ldg(bf + 1), Cf = __ldg(bf + 2);
+    const d3 v[3] = {mk(A.x, A.y, A.z), mk(B.x, B.y, B.z), mk(Cf.x, Cf.y, Cf.z)};
+    // the mesh lies on the positive side of (b - a) x (c - a)
+    const d3 N = crossd(sub(v[1], v[0]), sub(v[2], v[0]));
+    const d3 sa = sub(S, v[0]);
+    if (dotd(N, sa) > 1e-6 * sqrt(dotd(N, N) * dotd(sa, sa))) return;
+    const d3 W = sub(Cd, S);
+    const double ww = dotd(W, W);
+    float px[3], py[3];
+    for (int k = 0; k < 3; ++k) {
+        const d3 D = sub(v[k], S);
+        const double dw = dotd(D, W);
+        if (!(dw > 0.0)) return;  // not in front of the source
+        const double t = ww / dw;
+        const d3 rel = mk(S.x + t * D.x - Cd.x, S.y + t * D.y - Cd.y, S.z + t * D.z - Cd.z);
+        px[k] = (float)(dotd(rel, U) / g.du + 0.5 * (double)(g.nu - 1));
+        py[k] = (float)(dotd(rel, V) / g.dv + 0.5 * (double)(g.nv - 1));
+    }
+    const float eps = 1e-3f;
+    const float ulo = fminf(fminf(px[0], px[1]), px[2]) - eps, uhi = fmaxf(fmaxf(px[0], px[1]), px[2]) + eps;
+    const float vlo = fminf(fminf(py[0], py[1]), py[2]) - eps, vhi = fmaxf(fmaxf(py[0], py[1]), py[2]) + eps;
+    if (uhi < 0.f || vhi < 0.f || ulo > (float)(g.nu - 1) || vlo > (float)(g.nv - 1)) return;
+    const int iu0 = max(0, (int)ceilf(ulo)), iu1 = min(g.nu - 1, (int)floorf(uhi));
+    const int iv0 = max(0, (int)ceilf(vlo)), iv1 = min(g.nv - 1, (int)floorf(vhi));
+    const float area = (px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]);
+    const float sg = area >= 0.f ? 1.f : -1.f;
+    float ex[3], ey[3], el[3];
+    for (int k = 0; k < 3; ++k) {
+        const int j = k == 2 ? 0 : k + 1;
+        ex[k] = px[j] - px[k];
+        ey[k] = py[j] - py[k];
+        el[k] = -eps * sqrtf(ex[k] * ex[k] + ey[k] * ey[k]);
+    }
+    int32_t *row0 = emap + (int64_t)ai * g.nv * g.nu;
+    for (int iv = iv0; iv <= iv1; ++iv)
+        for (int iu = iu0; iu <= iu1; ++iu) {
+            const float x = (float)iu, y = (float)iv;
+            bool in = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) in &= sg * (ex[k] * (y - py[k]) - ey[k] * (x - px[k])) >= el[k];
+            if (in) row0[(int64_t)iv * g.nu + iu] = (int32_t)q;
+        }
+}
+
+// Draws the entry map of the tile blocks [b0, b0 + nb) (cone rays) into
+// p.emap_buf and points p's map view at it.  Leaves p without a map when the
+// buffer is too small for the chunk's angles.
+static cudaError_t launch_entry_map(KParams &p, int64_t b0, int64_t nb, cudaStream_t stream) {
+    p.emap = nullptr;
+    if (!p.emap_buf || p.src_kind != 0 || nb <= 0) return cudaSuccess;
+    const int64_t per = (int64_t)p.tiles_u * p.tiles_v, pix = (int64_t)p.g.nu * p.g.nv;
+    const int64_t a_lo = b0 / per, a_hi = (b0 + nb - 1) / per;
+    const int64_t len = (a_hi - a_lo + 1) * pix;
+    if (len > p.emap_cap || a_hi - a_lo + 1 > 65535) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(p.emap_buf, 0xff, (size_t)len * sizeof(int32_t), stream);
+    if (e != cudaSuccess) return e;
+    if (p.m.nb > 0) {
+        dim3 grid((unsigned)((p.m.nb + 127) / 128), (unsigned)(a_hi - a_lo + 1));
+        k_entry_raster<<<grid, 128, 0, stream>>>(p.m, p.g, (int)a_lo, p.emap_buf);
+        note_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    p.emap = p.emap_buf;
+    p.emap_base = a_lo * pix;
+    p.emap_len = len;
+    return cudaSuccess;
+}
+
 // ================================================================ launchers
 
 template <int C, int MODE, int ENTRY = ENTRY_BVH>
@@ -1879,6 +1981,7 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
             const int64_t nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
             if (i >= 2) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
             if (e == cudaSuccess) e = cudaMemsetAsync(pc.q_count, 0, kQueueCountBytes, stream);
+            if (e == cudaSuccess && ENTRY == ENTRY_BVH) e = launch_entry_map(pc, b0, nb, stream);
             if (e != cudaSuccess) break;
             k_walk32<C, MODE, ENTRY><<<(unsigned)nb, threads, smem, stream>>>(pc);
             note_launch();
@@ -1902,6 +2005,7 @@ static cudaError_t launch_mode(const KParams &p0, int precision, int64_t nblocks
         int64_t nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
         p.block_offset = b0;
         cudaError_t e = cudaMemsetAsync(p.q_count, 0, kQueueCountBytes, stream);
+        if (e == cudaSuccess && ENTRY == ENTRY_BVH) e = launch_entry_map(p, b0, nb, stream);
         if (e != cudaSuccess) return e;
         k_walk32<C, MODE, ENTRY><<<(unsigned)nb, threads, smem, stream>>>(p);
         note_launch();

@@ -99,6 +99,16 @@ struct KParams {
     const int32_t *ray_off;
     int64_t seg_base, seg_cap;
     int32_t entry;  // ENTRY_BVH or ENTRY_RSTAR (fast walk, FWD C = 1 and ENTRY modes)
+    // Candidate entry faces of cone rays (fast walk, BVH entry): when emap_buf
+    // is set, each launch chunk first draws the boundary faces its angles'
+    // sources see from outside onto the detector (k_entry_raster), so that
+    // emap[ray - emap_base] (0 <= . < emap_len) is a boundary face whose
+    // projection covers the ray's pixel, or -1.  The walk tests that face with
+    // its exact entry test and searches the BVH only when it is not the one.
+    int32_t *emap_buf;   // emap_cap ints, or null (no map)
+    int64_t emap_cap;
+    const int32_t *emap;
+    int64_t emap_base, emap_len;
 };
 
 // One problem of a batched launch: its parameters (operands included) and a
