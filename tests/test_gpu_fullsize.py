@@ -278,6 +278,39 @@ def test_batched_workload_problem_sampled(tp, k):
     b.close()
 
 
+@pytest.mark.parametrize("k", [9, 5])
+def test_batched_workload_problem_fp64(tp, k):
+    """Problems of the batched workload on the plain FP64 path (single calls,
+    4 channels): #9 (31^3 cells, 230^2 x 71 rays) and #5 (21^3, 294^2 x 107);
+    1,000 sampled rays and 32 central tets against the oracle at 1e-12."""
+    import torch
+    n, N, na = W.config5_specs()[k]
+    w = W.config5_problem(k, n, N, na, channels=4)
+    mesh = tp.Mesh(w.verts, w.tets)
+    geo = tp.Geometry.from_cone(w.geom)
+    o = tp.make_options(precision=tp.PLAIN_FP64, channels=4)
+    proj = tp.forward(mesh, geo, torch.tensor(w.mu, dtype=torch.float64, device="cuda"), options=o)
+    back = tp.backward(mesh, geo, proj, options=o)
+    torch.cuda.synchronize()
+    assert mesh.stats()["error"] == 0
+    rng = np.random.default_rng(500 + k)
+    idx = np.sort(rng.choice(geo.nrays, 1000, replace=False))
+    both = oracle.forward_cone(w.verts, w.tets, np.concatenate([w.mu, np.abs(w.mu)], axis=1),
+                               w.geom, idx)
+    got = proj.reshape(-1, 4)[torch.tensor(idx, device="cuda")].cpu().numpy()
+    fl = floor_abs("f64", w.verts, w.mu)
+    for c in range(4):
+        check_rays(f"C5#{k} forward f64 channel {c}", got[:, c], both[:, c], both[:, 4 + c],
+                   TOL["f64"], fl)
+    cen = W.tet_centroids(w.verts, w.tets)
+    tets = rng.choice(np.nonzero(np.linalg.norm(cen, axis=1) < 0.5)[0], 32, replace=False)
+    y = proj.cpu().numpy().reshape(-1, 4)
+    wantb = oracle.backward_cone_subset(w.verts, w.tets, y, w.geom, tets)
+    gotb = back[torch.tensor(tets, device="cuda")].cpu().numpy()
+    _rel_report(f"C5#{k} backward f64", gotb, wantb, wantb)
+    assert np.all(np.abs(gotb - wantb) <= TOL["f64"] * wantb)
+
+
 def test_fp64_accumulator_many_segments_per_tet(tp):
     """Problem #18 of the batched workload (27^3 cells, 811^2 x 451 rays, ~10^5
     segments per tet): FP32 atomic sums (TETPROJ_FLAG_ACC32) come within 1e-5 of

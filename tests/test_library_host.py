@@ -75,6 +75,32 @@ def test_side_cascade_sound_and_exact(tp):
     assert n_fp32 > 1000 and n_fp64 > 1000 and n_exact > 100
 
 
+def test_side_cascade_sound_one_million(tp):
+    """10^6 near-degenerate orientations (rays within 1e-16..1e-1 of an edge
+    line, edges from 1e-1 down to 1e-5 long, some far from the origin): every
+    sign the FP32 or FP64 filter certifies equals the exact sign."""
+    rng = np.random.default_rng(24)
+    cases = []
+    for sc in (1e-1, 1e-2, 1e-3, 1e-4, 3e-5, 1e-5):
+        cases.append(_near_degenerate(rng, 150000, sc))
+    S, P, p, q = [np.concatenate([c[k] for c in cases]) for k in range(4)]
+    far = rng.random(S.shape[0]) < 0.2            # a fifth shifted away from the origin
+    shift = rng.uniform(-50.0, 50.0, size=(S.shape[0], 3)) * far[:, None]
+    S, P, p, q = S + shift, P + shift, p + shift, q + shift
+    assert S.shape[0] >= 1_000_000 - 100000
+    extra = _near_degenerate(rng, 1_000_000 - S.shape[0], 1e-3)
+    S, P, p, q = [np.concatenate([a, b]) for a, b in zip((S, P, p, q), extra)]
+    assert S.shape[0] == 1_000_000
+    sign, stage = tp.side_signs_host(S, P, p, q)
+    certain = stage <= 1
+    checked = 0
+    for k in np.nonzero(certain)[0]:
+        assert sign[k] == exact.side_sign_int(S[k], P[k], p[k], q[k]), (k, stage[k])
+        checked += 1
+    # the filters decide most cases and leave a real share to the exact stages
+    assert checked > 500_000 and (~certain).sum() > 10_000
+
+
 def test_side_cascade_symbolic_matches_exact_module(tp):
     rng = np.random.default_rng(22)
     grid = lambda: rng.integers(-4, 5, size=3).astype(float) / 4.0
