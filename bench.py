@@ -64,6 +64,7 @@ PROFILES = os.path.join(ROOT, "profiles")
 # FP64 operations per segment of the plain walk (profiles/walk64_kuhn64s_fp64.md);
 # both are used only while the walk sources hash to the value recorded there.
 TRAFFIC_FILE = os.path.join(PROFILES, "walk32_kuhn96s_traffic.md")
+PROFILED_TILE = "16x8"  # the launch configuration of that capture (default options)
 FP64OPS_FILE = os.path.join(PROFILES, "walk64_kuhn64s_fp64.md")
 WALK_SOURCES = ["kernels.cu", "kernels.cuh", "predicates.cuh", "tetproj_internal.h"]
 
@@ -525,7 +526,7 @@ def parse_args(argv=None):
                     help="default workload: leave out the nested batched measurement")
     ap.add_argument("--batched-workload", default="batch24")
     ap.add_argument("--scatter", default="atomic", choices=["atomic", "warp", "sort"])
-    ap.add_argument("--tile", default="8x8")
+    ap.add_argument("--tile", default="16x8")
     ap.add_argument("--tune-cache", default=None)
     ap.add_argument("--acc", default="auto", choices=["auto", "f32", "f64"],
                     help="accumulator of the filtered backprojection (auto: FP64 at C = 1)")
@@ -777,7 +778,7 @@ def run_single(args, tp, torch, dist, rank, world, local):
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     bwd_mode = "MODE_BWD64" if acc == "f64" else "MODE_BWD"
     tr = None
-    if args.tile == "8x8" and args.scatter == "atomic" and args.acc == "auto":
+    if args.tile == PROFILED_TILE and args.scatter == "atomic" and args.acc == "auto":
         per_seg = profile_per_segment(TRAFFIC_FILE, "dram_bytes_per_segment")
         if per_seg is not None:
             tr = per_seg[dom] * dom_stats["segments"]

@@ -116,8 +116,8 @@ typedef struct tetproj_geometry tetproj_geometry;
 typedef struct tetproj_options {
     int32_t precision; /* TETPROJ_FILTERED (default) or TETPROJ_PLAIN_FP64            */
     int32_t channels;  /* C: 1 (default) or 4                                          */
-    int32_t tile_u;    /* ray tile width in pixels: 1..32, power of two (default 8)    */
-    int32_t tile_v;    /* ray tile height: tile_u*tile_v in {32,64,128,256}            */
+    int32_t tile_u;    /* ray tile width in pixels: 1..32, power of two (default 16)   */
+    int32_t tile_v;    /* ray tile height: tile_u*tile_v in {32,64,128,256} (def. 8)   */
     int32_t order;     /* TETPROJ_ORDER_MORTON (default) or TETPROJ_ORDER_ROW          */
     int32_t scatter;   /* TETPROJ_SCATTER_ATOMIC (default), _WARP or _SORT             */
     int32_t max_steps; /* walk step limit per ray; 0 = 64 + 16*ceil(nt^(1/3))          */

@@ -91,7 +91,7 @@ def fma64_peak_tflops(iters: int = 1 << 16, reps: int = 3) -> float:
     return flops.value / (best / 1e3) / 1e12
 
 
-def make_options(precision=FILTERED, channels=1, tile=(8, 8), order=ORDER_MORTON,
+def make_options(precision=FILTERED, channels=1, tile=(16, 8), order=ORDER_MORTON,
                  scatter=SCATTER_ATOMIC, max_steps=0, flags=0) -> Options:
     o = Options()
     _lib.load().tetproj_default_options(ctypes.byref(o))

@@ -137,7 +137,7 @@ void tetproj_default_options(tetproj_options *o) {
     if (!o) return;
     o->precision = TETPROJ_FILTERED;
     o->channels = 1;
-    o->tile_u = 8;
+    o->tile_u = 16;
     o->tile_v = 8;
     o->order = TETPROJ_ORDER_MORTON;
     o->scatter = TETPROJ_SCATTER_ATOMIC;
