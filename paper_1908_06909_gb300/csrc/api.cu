@@ -1166,6 +1166,13 @@ struct tetproj_batch {
     std::vector<AccMerge> merges; // the dense problems' merges
     std::vector<int64_t> cuts;    // backprojection rounds (item boundaries; empty: uniform)
     BatchWait wait{kBatchWaitPolls, 0};  // bounded waits of the persistent kernel
+    // entry maps per round (forward: uniform rounds, backward: `cuts` or uniform)
+    int32_t *emap = nullptr;
+    EmapView *d_views[2] = {nullptr, nullptr};
+    std::vector<BatchEmapRound> em_rounds[2];
+    std::vector<BatchEmapJob> em_jobs[2];
+    BatchEmap em[2] = {};
+    bool em_ready = false;
 };
 
 static void batch_free(tetproj_batch *b) {
@@ -1180,7 +1187,77 @@ static void batch_free(tetproj_batch *b) {
     cudaFree(b->q_count);
     cudaFree(b->item_counter);
     if (b->ov_ready) overlap_release(b->ov);
+    cudaFree(b->emap);
+    cudaFree(b->d_views[0]);
+    cudaFree(b->d_views[1]);
     delete b;
+}
+
+// Entry maps of the batched launch (the single-problem walk's, per round):
+// for every round, the angles of each problem with items in it are drawn
+// into one buffer before the round's walk.  Problems whose source circle is
+// not outside their mesh's bounding sphere get no map.  Rounds are the
+// launch's: uniform for the forward, `cuts` (when set) for the backward.
+static cudaError_t batch_entry_maps(tetproj_batch *b, const tetproj_geometry *const *geos) {
+    const int n = b->n;
+    const int64_t total = b->item_begin.back();
+    const int64_t ri = batch_round_items(b->q_cap);
+    if (ri < 1) return cudaSuccess;
+    std::vector<int64_t> uni;
+    for (int64_t r = 0; r < total; r += ri) uni.push_back(r);
+    uni.push_back(total);
+    const std::vector<int64_t> *bounds[2] = {&uni, b->cuts.empty() ? &uni : &b->cuts};
+    std::vector<char> ok(n);
+    for (int k = 0; k < n; ++k)
+        ok[k] = b->base[k].entry == ENTRY_BVH && geos[k]->dso > 1.75 * (double)b->meshes[k]->radius;
+    int64_t maxlen = 0;
+    std::vector<std::vector<EmapView>> views(2);
+    for (int d = 0; d < 2; ++d) {
+        const std::vector<int64_t> &B = *bounds[d];
+        const int64_t nr = (int64_t)B.size() - 1;
+        views[d].assign((size_t)(nr * n), EmapView{nullptr, 0, 0});
+        for (int64_t i = 0; i < nr; ++i) {
+            BatchEmapRound R{(int32_t)b->em_jobs[d].size(), 0, 0};
+            for (int k = 0; k < n; ++k) {
+                const int64_t i0 = b->item_begin[k], i1 = b->item_begin[k + 1];
+                if (!ok[k] || i1 <= B[i] || i0 >= B[i + 1]) continue;
+                const KParams &P = b->base[k];
+                const int wpt_log = P.log_tu + P.log_tv - 5;
+                const int64_t per = (int64_t)P.tiles_u * P.tiles_v, nblk = (int64_t)P.g.na * per;
+                const int64_t lo = (B[i] > i0 ? B[i] : i0) - i0, hi = (B[i + 1] < i1 ? B[i + 1] : i1) - i0 - 1;
+                const int64_t b_lo = lo >> wpt_log;
+                int64_t b_hi = hi >> wpt_log;
+                if (b_lo >= nblk) continue;  // only the padding of the problem's last chunk
+                if (b_hi >= nblk) b_hi = nblk - 1;
+                const int64_t a_lo = b_lo / per, na = b_hi / per - a_lo + 1;
+                if (na > 65535) continue;
+                const int64_t pix = (int64_t)P.g.nu * P.g.nv;
+                b->em_jobs[d].push_back(BatchEmapJob{k, (int32_t)a_lo, (int32_t)na, R.len});
+                // the view's pointer is the offset for now
+                views[d][(size_t)(i * n + k)] = EmapView{reinterpret_cast<const int32_t *>(R.len),
+                                                         a_lo * pix, na * pix};
+                R.len += na * pix;
+                ++R.count;
+            }
+            b->em_rounds[d].push_back(R);
+            if (R.len > maxlen) maxlen = R.len;
+        }
+    }
+    if (maxlen == 0 || maxlen > (int64_t(1) << 27)) return cudaSuccess;  // no map (or > 512 MB)
+    cudaError_t e = cudaMalloc((void **)&b->emap, (size_t)maxlen * sizeof(int32_t));
+    for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
+        for (EmapView &v : views[d])
+            if (v.len > 0) v.emap = b->emap + reinterpret_cast<intptr_t>(v.emap);
+        e = cudaMalloc((void **)&b->d_views[d], sizeof(EmapView) * views[d].size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_views[d], views[d].data(), sizeof(EmapView) * views[d].size(),
+                           cudaMemcpyHostToDevice);
+        b->em[d] = BatchEmap{b->emap, b->d_views[d], b->em_rounds[d].data(), b->em_jobs[d].data(),
+                             b->base.data(), n};
+    }
+    if (e != cudaSuccess) return e;
+    b->em_ready = true;
+    return cudaSuccess;
 }
 
 extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes,
@@ -1310,6 +1387,8 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
     b->y.assign(n, nullptr);
     b->proj.assign(n, nullptr);
     b->mu_out.assign(n, nullptr);
+    e = batch_entry_maps(b, geos);
+    if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
     *out = b;
     return TETPROJ_OK;
 }
@@ -1352,7 +1431,7 @@ extern "C" tetproj_status tetproj_batch_forward(tetproj_batch *b, void *stream) 
     TP_CUDA(launch_batch(b->d_fwd, b->d_item_begin, b->n, b->item_begin.back(),
                          b->channels, MODE_FWD, b->grid_fwd, b->rgrid, b->q, b->q_count, b->q_cap, b->item_counter,
                          b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr, nullptr, 0, nullptr, 0,
-                         b->wait));
+                         b->wait, b->em_ready ? &b->em[0] : nullptr));
     return TETPROJ_OK;
 }
 
@@ -1371,7 +1450,7 @@ extern "C" tetproj_status tetproj_batch_backward(tetproj_batch *b, void *stream)
                          b->smem_nodes, s, b->ov_ready ? &b->ov : nullptr,
                          b->cuts.empty() ? nullptr : b->cuts.data(), (int)b->cuts.size(),
                          b->merges.empty() ? nullptr : b->merges.data(), (int)b->merges.size(),
-                         b->wait));
+                         b->wait, b->em_ready ? &b->em[1] : nullptr));
     for (int k = 0; k < b->n; ++k) {
         if (b->acc64 || b->acc32[k])
             TP_CUDA(launch_scatter_perm_d2f(b->meshes[k]->perm, b->meshes[k]->nt, b->channels,

@@ -1268,6 +1268,97 @@ static int sm_count() {
     return n;
 }
 
+// ============================================================ entry map
+
+// Candidate entry faces for the cone rays of angles a0 .. a0 + gridDim.y - 1
+// (KParams::emap).  A convex mesh seen from a source outside it projects onto
+// the detector as the union of the projections of the boundary faces that
+// face the source, and a ray entering through a face passes through the
+// face's projection; so each such face writes its index to the pixels whose
+// centres its projection covers.  The projection is computed in FP64 and
+// grown by 1e-3 pixel; faces within 1e-6 of edge-on are drawn too.  Pixels on
+// shared edges get one of the faces.  Nothing here is trusted: the walk tests
+// the face with its exact entry test and searches the BVH when it fails.
+__global__ void __launch_bounds__(128) k_entry_raster(const MeshView m, const GeoView g, int a0,
+                                                      int32_t *emap) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ai = blockIdx.y;
+    if (q >= m.nb) return;
+    const AngleFrame *F = g.frames + a0 + ai;
+    const d3 S = mk(__ldg(&F->S[0]), __ldg(&F->S[1]), __ldg(&F->S[2]));
+    const d3 Cd = mk(__ldg(&F->C[0]), __ldg(&F->C[1]), __ldg(&F->C[2]));
+    const d3 U = mk(__ldg(&F->U[0]), __ldg(&F->U[1]), __ldg(&F->U[2]));
+    const d3 V = mk(__ldg(&F->V[0]), __ldg(&F->V[1]), __ldg(&F->V[2]));
+    const float4 *bf = reinterpret_cast<const float4 *>(m.bfaces + q);
+    const float4 A = __ldg(bf), B = __ldg(bf + 1), Cf = __ldg(bf + 2);
+    const d3 v[3] = {mk(A.x, A.y, A.z), mk(B.x, B.y, B.z), mk(Cf.x, Cf.y, Cf.z)};
+    // the mesh lies on the positive side of (b - a) x (c - a)
+    const d3 N = crossd(sub(v[1], v[0]), sub(v[2], v[0]));
+    const d3 sa = sub(S, v[0]);
+    if (dotd(N, sa) > 1e-6 * sqrt(dotd(N, N) * dotd(sa, sa))) return;
+    const d3 W = sub(Cd, S);
+    const double ww = dotd(W, W);
+    float px[3], py[3];
+    for (int k = 0; k < 3; ++k) {
+        const d3 D = sub(v[k], S);
+        const double dw = dotd(D, W);
+        if (!(dw > 0.0)) return;  // not in front of the source
+        const double t = ww / dw;
+        const d3 rel = mk(S.x + t * D.x - Cd.x, S.y + t * D.y - Cd.y, S.z + t * D.z - Cd.z);
+        px[k] = (float)(dotd(rel, U) / g.du + 0.5 * (double)(g.nu - 1));
+        py[k] = (float)(dotd(rel, V) / g.dv + 0.5 * (double)(g.nv - 1));
+    }
+    const float eps = 1e-3f;
+    const float ulo = fminf(fminf(px[0], px[1]), px[2]) - eps, uhi = fmaxf(fmaxf(px[0], px[1]), px[2]) + eps;
+    const float vlo = fminf(fminf(py[0], py[1]), py[2]) - eps, vhi = fmaxf(fmaxf(py[0], py[1]), py[2]) + eps;
+    if (uhi < 0.f || vhi < 0.f || ulo > (float)(g.nu - 1) || vlo > (float)(g.nv - 1)) return;
+    const int iu0 = max(0, (int)ceilf(ulo)), iu1 = min(g.nu - 1, (int)floorf(uhi));
+    const int iv0 = max(0, (int)ceilf(vlo)), iv1 = min(g.nv - 1, (int)floorf(vhi));
+    const float area = (px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]);
+    const float sg = area >= 0.f ? 1.f : -1.f;
+    float ex[3], ey[3], el[3];
+    for (int k = 0; k < 3; ++k) {
+        const int j = k == 2 ? 0 : k + 1;
+        ex[k] = px[j] - px[k];
+        ey[k] = py[j] - py[k];
+        el[k] = -eps * sqrtf(ex[k] * ex[k] + ey[k] * ey[k]);
+    }
+    int32_t *row0 = emap + (int64_t)ai * g.nv * g.nu;
+    for (int iv = iv0; iv <= iv1; ++iv)
+        for (int iu = iu0; iu <= iu1; ++iu) {
+            const float x = (float)iu, y = (float)iv;
+            bool in = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) in &= sg * (ex[k] * (y - py[k]) - ey[k] * (x - px[k])) >= el[k];
+            if (in) row0[(int64_t)iv * g.nu + iu] = (int32_t)q;
+        }
+}
+
+// Draws the entry map of the tile blocks [b0, b0 + nb) (cone rays) into
+// p.emap_buf and points p's map view at it.  Leaves p without a map when the
+// buffer is too small for the chunk's angles.
+static cudaError_t launch_entry_map(KParams &p, int64_t b0, int64_t nb, cudaStream_t stream) {
+    p.emap = nullptr;
+    if (!p.emap_buf || p.src_kind != 0 || nb <= 0) return cudaSuccess;
+    const int64_t per = (int64_t)p.tiles_u * p.tiles_v, pix = (int64_t)p.g.nu * p.g.nv;
+    const int64_t a_lo = b0 / per, a_hi = (b0 + nb - 1) / per;
+    const int64_t len = (a_hi - a_lo + 1) * pix;
+    if (len > p.emap_cap || a_hi - a_lo + 1 > 65535) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(p.emap_buf, 0xff, (size_t)len * sizeof(int32_t), stream);
+    if (e != cudaSuccess) return e;
+    if (p.m.nb > 0) {
+        dim3 grid((unsigned)((p.m.nb + 127) / 128), (unsigned)(a_hi - a_lo + 1));
+        k_entry_raster<<<grid, 128, 0, stream>>>(p.m, p.g, (int)a_lo, p.emap_buf);
+        note_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    p.emap = p.emap_buf;
+    p.emap_base = a_lo * pix;
+    p.emap_len = len;
+    return cudaSuccess;
+}
+
 // ============================================================ batched walk
 //
 // Many meshes and geometries in one persistent launch.  The unit of work is a
@@ -1315,7 +1406,8 @@ template <int C, int MODE>
 __global__ void __launch_bounds__(TP_BATCH_THREADS, TP_BATCH_MIN_BLOCKS)
     k_batch32(const BatchProblem *__restrict__ probs, const int64_t *__restrict__ item_begin,
               int nprob, int64_t round_begin, int64_t round_end, unsigned *chunk_counter,
-              int nsm_max, QEntry *q, unsigned long long *q_count, BatchWait wait) {
+              int nsm_max, QEntry *q, unsigned long long *q_count, BatchWait wait,
+              const EmapView *__restrict__ views) {
     extern __shared__ float4 smem[];
     __shared__ unsigned s_ticket;
     __shared__ long long s_base[TP_BATCH_RING];
@@ -1389,6 +1481,11 @@ __global__ void __launch_bounds__(TP_BATCH_THREADS, TP_BATCH_MIN_BLOCKS)
                 sp->smem_nodes = nsm;
                 sp->q = q;  // this round's deferral queue (rounds may alternate queues)
                 sp->q_count = q_count;
+                // this round's entry map of the problem, if it has one
+                const EmapView ev = views ? views[k] : EmapView{nullptr, 0, 0};
+                sp->emap = ev.emap;
+                sp->emap_base = ev.base;
+                sp->emap_len = ev.len;
             }
             __syncwarp();
             cur = k;
@@ -1489,11 +1586,32 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
                                      int smem_nodes, cudaStream_t stream,
                                      const ResumeOverlap *ov, const int64_t *cuts,
                                      int ncuts, const AccMerge *merges, int nmerge,
-                                     BatchWait wait) {
+                                     BatchWait wait, const BatchEmap *em) {
     // rounds of warp items (32 rays each), at most q_cap rays: uniform, or
     // [cuts[i], cuts[i + 1]) when cuts are given
     if (nmerge > 0 && MODE != MODE_BWD) return cudaErrorInvalidValue;
-    const int64_t round_items = (q_cap / (32 * kBatchChunk)) * kBatchChunk;
+    const int64_t round_items = batch_round_items(q_cap);
+    // round i's entry maps (before its walk; the previous round's walk, the
+    // map's only reader, precedes it on the same stream)
+    auto draw_maps = [&](int64_t i, cudaStream_t st) -> cudaError_t {
+        if (!em) return cudaSuccess;
+        const BatchEmapRound &R = em->rounds[i];
+        if (R.len <= 0) return cudaSuccess;
+        cudaError_t e = cudaMemsetAsync(em->buf, 0xff, (size_t)R.len * sizeof(int32_t), st);
+        for (int j = R.first; j < R.first + R.count && e == cudaSuccess; ++j) {
+            const BatchEmapJob &J = em->jobs[j];
+            const KParams &P = em->probs[J.prob];
+            if (P.m.nb <= 0) continue;
+            dim3 g((unsigned)((P.m.nb + 127) / 128), (unsigned)J.na);
+            k_entry_raster<<<g, 128, 0, st>>>(P.m, P.g, J.a_lo, em->buf + J.off);
+            note_launch();
+            e = cudaGetLastError();
+        }
+        return e;
+    };
+    auto views_of = [&](int64_t i) -> const EmapView * {
+        return em ? em->views + i * em->nprob : nullptr;
+    };
     if (round_items < 1) return cudaErrorInvalidValue;
     const int64_t nrounds = cuts ? (int64_t)ncuts - 1 : (nitems + round_items - 1) / round_items;
     if (cuts) {
@@ -1531,9 +1649,10 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
             if (i >= 2) e = cudaStreamWaitEvent(stream, ov->ev_res[j], 0);
             if (e == cudaSuccess) e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(cj, 0, kQueueCountBytes, stream);
+            if (e == cudaSuccess) e = draw_maps(i, stream);
             if (e != cudaSuccess) break;
             k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
-                probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, qj, cj, wait);
+                probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, qj, cj, wait, views_of(i));
             note_launch();
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaEventRecord(ov->ev_fast[j], stream);
@@ -1556,9 +1675,10 @@ static cudaError_t launch_batch_mode(const BatchProblem *probs, const int64_t *i
         round_of(i, r0, r1);
         cudaError_t e = cudaMemsetAsync(item_counter, 0, sizeof(unsigned), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(q_count, 0, kQueueCountBytes, stream);
+        if (e == cudaSuccess) e = draw_maps(i, stream);
         if (e != cudaSuccess) return e;
         k_batch32<C, MODE><<<grid, TP_BATCH_THREADS, batch_smem(smem_nodes), stream>>>(
-            probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, q, q_count, wait);
+            probs, item_begin, nprob, r0, r1, item_counter, smem_nodes, q, q_count, wait, views_of(i));
         note_launch();
         k_batch_resume32<C, MODE><<<rgrid, 128, 0, stream>>>(probs, q, q_count, q_cap);
         note_launch();
@@ -1575,12 +1695,13 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
                          unsigned rgrid, QEntry *q, unsigned long long *q_count, int64_t q_cap,
                          unsigned *item_counter, int smem_nodes, cudaStream_t stream,
                          const ResumeOverlap *ov, const int64_t *cuts, int ncuts,
-                         const AccMerge *merges, int nmerge, BatchWait wait) {
+                         const AccMerge *merges, int nmerge, BatchWait wait,
+                         const BatchEmap *em) {
     if (nitems <= 0) return cudaSuccess;
     if (wait.limit < 1) return cudaErrorInvalidValue;
     if (grid < 1 || rgrid < 1) return cudaErrorInvalidValue;
 #define TP_BATCH_ARGS probs, item_begin, nprob, nitems, grid, rgrid, q, q_count, q_cap, \
-                      item_counter, smem_nodes, stream, ov, cuts, ncuts, merges, nmerge, wait
+                      item_counter, smem_nodes, stream, ov, cuts, ncuts, merges, nmerge, wait, em
     if (mode == MODE_FWD)
         return channels == 4 ? launch_batch_mode<4, MODE_FWD>(TP_BATCH_ARGS)
                              : launch_batch_mode<1, MODE_FWD>(TP_BATCH_ARGS);
@@ -1849,97 +1970,6 @@ __global__ void k_side(const double *S, const double *P, const double *p, const 
     int s = side_sign_cascade(ld(S, k), ld(P, k), ld(p, k), ld(q, k), &st);
     sign[k] = (int8_t)s;
     stage[k] = (int8_t)st;
-}
-
-// ============================================================ entry map
-
-// Candidate entry faces for the cone rays of angles a0 .. a0 + gridDim.y - 1
-// (KParams::emap).  A convex mesh seen from a source outside it projects onto
-// the detector as the union of the projections of the boundary faces that
-// face the source, and a ray entering through a face passes through the
-// face's projection; so each such face writes its index to the pixels whose
-// centres its projection covers.  The projection is computed in FP64 and
-// grown by 1e-3 pixel; faces within 1e-6 of edge-on are drawn too.  Pixels on
-// shared edges get one of the faces.  Nothing here is trusted: the walk tests
-// the face with its exact entry test and searches the BVH when it fails.
-__global__ void __launch_bounds__(128) k_entry_raster(const MeshView m, const GeoView g, int a0,
-                                                      int32_t *emap) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int ai = blockIdx.y;
-    if (q >= m.nb) return;
-    const AngleFrame *F = g.frames + a0 + ai;
-    const d3 S = mk(__ldg(&F->S[0]), __ldg(&F->S[1]), __ldg(&F->S[2]));
-    const d3 Cd = mk(__ldg(&F->C[0]), __ldg(&F->C[1]), __ldg(&F->C[2]));
-    const d3 U = mk(__ldg(&F->U[0]), __ldg(&F->U[1]), __ldg(&F->U[2]));
-    const d3 V = mk(__ldg(&F->V[0]), __ldg(&F->V[1]), __ldg(&F->V[2]));
-    const float4 *bf = reinterpret_cast<const float4 *>(m.bfaces + q);
-    const float4 A = __ldg(bf), B = __ldg(bf + 1), Cf = __ldg(bf + 2);
-    const d3 v[3] = {mk(A.x, A.y, A.z), mk(B.x, B.y, B.z), mk(Cf.x, Cf.y, Cf.z)};
-    // the mesh lies on the positive side of (b - a) x (c - a)
-    const d3 N = crossd(sub(v[1], v[0]), sub(v[2], v[0]));
-    const d3 sa = sub(S, v[0]);
-    if (dotd(N, sa) > 1e-6 * sqrt(dotd(N, N) * dotd(sa, sa))) return;
-    const d3 W = sub(Cd, S);
-    const double ww = dotd(W, W);
-    float px[3], py[3];
-    for (int k = 0; k < 3; ++k) {
-        const d3 D = sub(v[k], S);
-        const double dw = dotd(D, W);
-        if (!(dw > 0.0)) return;  // not in front of the source
-        const double t = ww / dw;
-        const d3 rel = mk(S.x + t * D.x - Cd.x, S.y + t * D.y - Cd.y, S.z + t * D.z - Cd.z);
-        px[k] = (float)(dotd(rel, U) / g.du + 0.5 * (double)(g.nu - 1));
-        py[k] = (float)(dotd(rel, V) / g.dv + 0.5 * (double)(g.nv - 1));
-    }
-    const float eps = 1e-3f;
-    const float ulo = fminf(fminf(px[0], px[1]), px[2]) - eps, uhi = fmaxf(fmaxf(px[0], px[1]), px[2]) + eps;
-    const float vlo = fminf(fminf(py[0], py[1]), py[2]) - eps, vhi = fmaxf(fmaxf(py[0], py[1]), py[2]) + eps;
-    if (uhi < 0.f || vhi < 0.f || ulo > (float)(g.nu - 1) || vlo > (float)(g.nv - 1)) return;
-    const int iu0 = max(0, (int)ceilf(ulo)), iu1 = min(g.nu - 1, (int)floorf(uhi));
-    const int iv0 = max(0, (int)ceilf(vlo)), iv1 = min(g.nv - 1, (int)floorf(vhi));
-    const float area = (px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]);
-    const float sg = area >= 0.f ? 1.f : -1.f;
-    float ex[3], ey[3], el[3];
-    for (int k = 0; k < 3; ++k) {
-        const int j = k == 2 ? 0 : k + 1;
-        ex[k] = px[j] - px[k];
-        ey[k] = py[j] - py[k];
-        el[k] = -eps * sqrtf(ex[k] * ex[k] + ey[k] * ey[k]);
-    }
-    int32_t *row0 = emap + (int64_t)ai * g.nv * g.nu;
-    for (int iv = iv0; iv <= iv1; ++iv)
-        for (int iu = iu0; iu <= iu1; ++iu) {
-            const float x = (float)iu, y = (float)iv;
-            bool in = true;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) in &= sg * (ex[k] * (y - py[k]) - ey[k] * (x - px[k])) >= el[k];
-            if (in) row0[(int64_t)iv * g.nu + iu] = (int32_t)q;
-        }
-}
-
-// Draws the entry map of the tile blocks [b0, b0 + nb) (cone rays) into
-// p.emap_buf and points p's map view at it.  Leaves p without a map when the
-// buffer is too small for the chunk's angles.
-static cudaError_t launch_entry_map(KParams &p, int64_t b0, int64_t nb, cudaStream_t stream) {
-    p.emap = nullptr;
-    if (!p.emap_buf || p.src_kind != 0 || nb <= 0) return cudaSuccess;
-    const int64_t per = (int64_t)p.tiles_u * p.tiles_v, pix = (int64_t)p.g.nu * p.g.nv;
-    const int64_t a_lo = b0 / per, a_hi = (b0 + nb - 1) / per;
-    const int64_t len = (a_hi - a_lo + 1) * pix;
-    if (len > p.emap_cap || a_hi - a_lo + 1 > 65535) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(p.emap_buf, 0xff, (size_t)len * sizeof(int32_t), stream);
-    if (e != cudaSuccess) return e;
-    if (p.m.nb > 0) {
-        dim3 grid((unsigned)((p.m.nb + 127) / 128), (unsigned)(a_hi - a_lo + 1));
-        k_entry_raster<<<grid, 128, 0, stream>>>(p.m, p.g, (int)a_lo, p.emap_buf);
-        note_launch();
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    p.emap = p.emap_buf;
-    p.emap_base = a_lo * pix;
-    p.emap_len = len;
-    return cudaSuccess;
 }
 
 // ================================================================ launchers

@@ -135,6 +135,36 @@ constexpr int kBatchChunk = 8;
 // operations (graph-capturable).
 struct ResumeOverlap;
 struct AccMerge;
+// Warp items per uniform round of the batched launch (rounds hold at most
+// q_cap rays and whole work chunks).
+inline int64_t batch_round_items(int64_t q_cap) {
+    return (q_cap / (32 * kBatchChunk)) * kBatchChunk;
+}
+// Entry map of one problem in one round of the batched launch (see
+// KParams::emap): emap[ray - base], 0 <= . < len, or emap == null.
+struct EmapView {
+    const int32_t *emap;
+    int64_t base, len;
+};
+// The rasters of one round: problem `prob`'s angles [a_lo, a_lo + na) drawn
+// into buf + off; rounds list their jobs [first, first + count) and the
+// length (ints) of the buffer they use.
+struct BatchEmapJob {
+    int32_t prob, a_lo, na;
+    int64_t off;
+};
+struct BatchEmapRound {
+    int32_t first, count;
+    int64_t len;
+};
+struct BatchEmap {
+    int32_t *buf;                  // device, shared by the rounds (one at a time)
+    const EmapView *views;         // device [nrounds][nprob]: the rounds' views
+    const BatchEmapRound *rounds;  // host [nrounds]
+    const BatchEmapJob *jobs;      // host
+    const KParams *probs;          // host [nprob]: mesh and geometry of each problem
+    int nprob;
+};
 // The bounded waits between the warps of a batched CTA: at most `limit` polls
 // each (kBatchWaitPolls by default), then TETPROJ_ERR_TIMEOUT and the warp
 // stops.  A non-zero `offset` makes every wait wait for a value no warp
@@ -149,7 +179,8 @@ cudaError_t launch_batch(const BatchProblem *probs, const int64_t *item_begin, i
                          QEntry *q, unsigned long long *q_count, int64_t q_cap,
                          unsigned *item_counter, int smem_nodes, cudaStream_t stream,
                          const ResumeOverlap *ov, const int64_t *cuts, int ncuts,
-                         const AccMerge *merges, int nmerge, BatchWait wait);
+                         const AccMerge *merges, int nmerge, BatchWait wait,
+                         const BatchEmap *emap = nullptr);
 // Persistent grid for the batched walk: resident CTAs per SM x SM count.
 cudaError_t batch_grid(int channels, int mode, int smem_nodes, unsigned &grid);
 int device_sm_count();
