@@ -1275,43 +1275,47 @@ static int sm_count() {
 // the detector as the union of the projections of the boundary faces that
 // face the source, and a ray entering through a face passes through the
 // face's projection; so each such face writes its index to the pixels whose
-// centres its projection covers.  The projection is computed in FP64 and
-// grown by 1e-3 pixel; faces within 1e-6 of edge-on are drawn too.  Pixels on
-// shared edges get one of the faces.  Nothing here is trusted: the walk tests
-// the face with its exact entry test and searches the BVH when it fails.
+// centres its projection covers.  The projection is computed in FP32 (FP64 is
+// 1/64 of the FP32 rate on GB300 and made this kernel cost more than the
+// searches it saves) and grown by 2e-3 pixel; faces within 1e-5 of edge-on
+// are drawn too.  Pixels on shared edges get one of the faces.  Nothing here
+// is trusted: the walk tests the face with its exact entry test and searches
+// the BVH when it fails, so rounding here only costs searches.
 __global__ void __launch_bounds__(128) k_entry_raster(const MeshView m, const GeoView g, int a0,
                                                       int32_t *emap) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int ai = blockIdx.y;
     if (q >= m.nb) return;
     const AngleFrame *F = g.frames + a0 + ai;
-    const d3 S = mk(__ldg(&F->S[0]), __ldg(&F->S[1]), __ldg(&F->S[2]));
-    const d3 Cd = mk(__ldg(&F->C[0]), __ldg(&F->C[1]), __ldg(&F->C[2]));
-    const d3 U = mk(__ldg(&F->U[0]), __ldg(&F->U[1]), __ldg(&F->U[2]));
-    const d3 V = mk(__ldg(&F->V[0]), __ldg(&F->V[1]), __ldg(&F->V[2]));
+    auto ld3 = [](const double *v) {
+        return mkf((float)__ldg(v), (float)__ldg(v + 1), (float)__ldg(v + 2));
+    };
+    const f3 S = ld3(F->S), Cd = ld3(F->C), U = ld3(F->U), V = ld3(F->V);
     const float4 *bf = reinterpret_cast<const float4 *>(m.bfaces + q);
     const float4 A = __ldg(bf), B = __ldg(bf + 1), Cf = __ldg(bf + 2);
-    const d3 v[3] = {mk(A.x, A.y, A.z), mk(B.x, B.y, B.z), mk(Cf.x, Cf.y, Cf.z)};
+    const f3 v[3] = {mkf(A.x, A.y, A.z), mkf(B.x, B.y, B.z), mkf(Cf.x, Cf.y, Cf.z)};
     // the mesh lies on the positive side of (b - a) x (c - a)
-    const d3 N = crossd(sub(v[1], v[0]), sub(v[2], v[0]));
-    const d3 sa = sub(S, v[0]);
-    if (dotd(N, sa) > 1e-6 * sqrt(dotd(N, N) * dotd(sa, sa))) return;
-    const d3 W = sub(Cd, S);
-    const double ww = dotd(W, W);
+    const f3 N = crossf(sub(v[1], v[0]), sub(v[2], v[0]));
+    const f3 sa = sub(S, v[0]);
+    if (dotf(N, sa) > 1e-5f * sqrtf(dotf(N, N) * dotf(sa, sa))) return;
+    const f3 W = sub(Cd, S);
+    const float ww = dotf(W, W);
+    const float idu = 1.0f / (float)g.du, idv = 1.0f / (float)g.dv;
+    const float hu = 0.5f * (float)(g.nu - 1), hv = 0.5f * (float)(g.nv - 1);
     float px[3], py[3];
     for (int k = 0; k < 3; ++k) {
-        const d3 D = sub(v[k], S);
-        const double dw = dotd(D, W);
-        if (!(dw > 0.0)) return;  // not in front of the source
-        const double t = ww / dw;
-        const d3 rel = mk(S.x + t * D.x - Cd.x, S.y + t * D.y - Cd.y, S.z + t * D.z - Cd.z);
-        px[k] = (float)(dotd(rel, U) / g.du + 0.5 * (double)(g.nu - 1));
-        py[k] = (float)(dotd(rel, V) / g.dv + 0.5 * (double)(g.nv - 1));
+        const f3 D = sub(v[k], S);
+        const float dw = dotf(D, W);
+        if (!(dw > 0.f)) return;  // not in front of the source
+        const float t = ww / dw;
+        const f3 rel = mkf(S.x + t * D.x - Cd.x, S.y + t * D.y - Cd.y, S.z + t * D.z - Cd.z);
+        px[k] = dotf(rel, U) * idu + hu;
+        py[k] = dotf(rel, V) * idv + hv;
     }
-    const float eps = 1e-3f;
+    const float eps = 2e-3f;
     const float ulo = fminf(fminf(px[0], px[1]), px[2]) - eps, uhi = fmaxf(fmaxf(px[0], px[1]), px[2]) + eps;
     const float vlo = fminf(fminf(py[0], py[1]), py[2]) - eps, vhi = fmaxf(fmaxf(py[0], py[1]), py[2]) + eps;
-    if (uhi < 0.f || vhi < 0.f || ulo > (float)(g.nu - 1) || vlo > (float)(g.nv - 1)) return;
+    if (!(uhi >= 0.f && vhi >= 0.f && ulo <= (float)(g.nu - 1) && vlo <= (float)(g.nv - 1))) return;
     const int iu0 = max(0, (int)ceilf(ulo)), iu1 = min(g.nu - 1, (int)floorf(uhi));
     const int iv0 = max(0, (int)ceilf(vlo)), iv1 = min(g.nv - 1, (int)floorf(vhi));
     const float area = (px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]);
@@ -1385,8 +1389,11 @@ static cudaError_t launch_entry_map(KParams &p, int64_t b0, int64_t nb, cudaStre
 #define TP_BATCH_THREADS 128
 #define TP_BATCH_RING 4
 
+// 7 resident CTAs per SM: at most 72 registers, no spills (8 CTAs cap it at 64 with
+// spills in the backprojection; batch of 24 config-5 problems, C = 4: 2,746
+// vs 2,835 ms per forward + backprojection)
 #ifndef TP_BATCH_MIN_BLOCKS
-#define TP_BATCH_MIN_BLOCKS 8
+#define TP_BATCH_MIN_BLOCKS 7
 #endif
 
 constexpr int kBatchParamVec = (int)((sizeof(KParams) + 15) / 16);
