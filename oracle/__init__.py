@@ -86,6 +86,17 @@ def lib():
         L.oracle_trace_rays.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64, _c_dp,
                                         _c_dp, ctypes.c_int64, ctypes.c_int64, _c_ip, _c_dp,
                                         _c_dp, _c_lp, _c_dp, _c_ip, ctypes.c_int]
+        L.oracle_walker_create.argtypes = [_c_dp, ctypes.c_int64, _c_ip, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int)]
+        L.oracle_walker_create.restype = ctypes.c_void_p
+        L.oracle_walker_destroy.argtypes = [ctypes.c_void_p]
+        L.oracle_walker_destroy.restype = None
+        L.oracle_walk.argtypes = [ctypes.c_void_p, _c_dp, _c_dp, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_double, ctypes.c_double, _c_dp, ctypes.c_int64,
+                                  _c_lp, _c_dp, _c_dp, ctypes.c_int64, _c_dp, _c_dp, _c_lp,
+                                  ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
+        L.oracle_walk.restype = ctypes.c_int
         for f in ("oracle_forward_rays", "oracle_forward_rays_range", "oracle_forward_cone", "oracle_backward_rays",
                   "oracle_backward_cone", "oracle_backward_cone_subset", "oracle_trace_rays"):
             getattr(L, f).restype = ctypes.c_int
@@ -320,6 +331,93 @@ def backward_cone_subset(verts, tets, y, geom, tet_idx, threads=None):
                                              threads or default_threads()),
            "oracle_backward_cone_subset")
     return out[:, 0] if C == 1 else out
+
+
+class Walker:
+    """Rows of A found by walking face adjacency (the oracle walker of
+    ``oracle.c``): the same a_ij as the brute-force clipper, each computed by
+    the same clipping code, but only for the tets a ray passes through.  Rays
+    with a near-tie anywhere on their walk (two candidate entries or exits
+    within 1e-9 in t, a visit shorter than that, a face plane containing the
+    ray) get the brute-force row instead.  The adjacency is the oracle's own,
+    built from the vertex ids.  Meant for convex meshes with sources outside;
+    any other ray still gets a brute-force row."""
+
+    def __init__(self, verts, tets):
+        self._v, vp = _d(verts)
+        self._t, tp = _i(tets)
+        st = ctypes.c_int(0)
+        h = lib().oracle_walker_create(vp, self._v.shape[0], tp, self._t.shape[0], ctypes.byref(st))
+        if not h:
+            raise RuntimeError(f"oracle_walker_create failed with code {st.value}")
+        self._h = ctypes.c_void_p(h)
+        self.nt = self._t.shape[0]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.oracle_walker_destroy(h)
+            self._h = None
+
+    def _run(self, mu, y, geom, ray_idx, S, P, threads):
+        if S is not None:
+            s, sp = _d(S)
+            p, pp = _d(P)
+            n = s.shape[0]
+            ip, angp, g = None, None, (0.0, 0.0, 0, 0, 0.0, 0.0)
+            na = 0
+        else:
+            sp = pp = None
+            ray_idx, ip = _l(np.arange(geom.nrays) if ray_idx is None else ray_idx)
+            n = ray_idx.size
+            ang, angp = _d(geom.angles)
+            g = (geom.dso, geom.dsd, geom.nu, geom.nv, geom.du, geom.dv)
+            na = geom.nangles
+        mp = yp = None
+        C = 1
+        if mu is not None:
+            mu2, C = _channels(mu, self.nt)
+            m, mp = _d(mu2)
+        if y is not None:
+            y2, C = _channels(y, n)
+            yy, yp = _d(y2)
+        fwd = np.empty((n, C)) if mu is not None else None
+        bwd = np.empty((self.nt, C)) if y is not None else None
+        cnt = np.empty(self.nt, dtype=np.int64) if y is not None else None
+        status = np.empty(n, dtype=np.int8)
+        _check(lib().oracle_walk(self._h, mp, yp, C, *g, angp, na, ip, sp, pp, n,
+                                 None if fwd is None else fwd.ctypes.data_as(_c_dp),
+                                 None if bwd is None else bwd.ctypes.data_as(_c_dp),
+                                 None if cnt is None else cnt.ctypes.data_as(_c_lp),
+                                 status.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                 threads or default_threads()), "oracle_walk")
+        self.last_count = cnt
+        return fwd, bwd, status
+
+    def forward_cone(self, mu, geom, ray_idx=None, threads=None):
+        """(b [n](,C), status [n]) for the selected cone rays (Eq. 2);
+        status 0 walked, 1 brute force, 2 brute force, ray in a face plane."""
+        fwd, _, st = self._run(mu, None, geom, ray_idx, None, None, threads)
+        return (fwd[:, 0] if np.asarray(mu).ndim == 1 else fwd), st
+
+    def backward_cone(self, y, geom, ray_idx, threads=None):
+        """(x [nt](,C), status): x_i = sum_k a_i,ray_idx[k] y[k] (Eq. 3 over
+        the selected cone rays only).  ``last_count`` then holds, per tet, how
+        many of these rays cross it."""
+        _, bwd, st = self._run(None, y, geom, ray_idx, None, None, threads)
+        return (bwd[:, 0] if np.asarray(y).ndim == 1 else bwd), st
+
+    def rows_cone(self, mu, y, geom, ray_idx, threads=None):
+        """Both at once (each row walked once): (b [n, C], x [nt, C], status)."""
+        return self._run(mu, y, geom, ray_idx, None, None, threads)
+
+    def forward_rays(self, mu, S, P, threads=None):
+        fwd, _, st = self._run(mu, None, None, None, S, P, threads)
+        return (fwd[:, 0] if np.asarray(mu).ndim == 1 else fwd), st
+
+    def backward_rays(self, y, S, P, threads=None):
+        _, bwd, st = self._run(None, y, None, None, S, P, threads)
+        return (bwd[:, 0] if np.asarray(y).ndim == 1 else bwd), st
 
 
 def mt_forward_rays(verts, tets, mu, S, P, precision="f64", max_steps=100000):

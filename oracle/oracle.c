@@ -541,3 +541,384 @@ int oracle_trace_rays(const double *verts, int64_t nv, const int32_t *tets, int6
     free(jobs);
     return rc;
 }
+
+/* ---------------------------------------------------------------- walker */
+/*
+ * The oracle walker: the same a_ij (each from tet_clip, the brute-force
+ * clipper's own arithmetic), but only the tets a ray passes through are
+ * clipped, found by walking face adjacency.  The adjacency is built here from
+ * the tets' vertex ids (faces matched by their sorted vertex triples), not
+ * taken from the CUDA path.
+ *
+ *   entry  among the tets with a boundary face whose bounding box the
+ *          half-line meets, the one with the smallest clipped lo (hi > lo);
+ *          the face that sets lo must be a boundary face;
+ *   step   the exit face is the face (n.d > 0) whose plane sets hi; the next
+ *          tet is its neighbour; the walk ends at a boundary face.
+ *
+ * A ray whose walk meets a near-tie -- two entry candidates, or two exit
+ * planes, within WALK_TOL in t, a visit shorter than WALK_TOL, a tet whose lo
+ * is not the previous hi, a face plane containing the ray, or more steps than
+ * tets -- is not walked: its row of A is computed by the brute-force clipper
+ * over all tets instead (status 1; status 2 if the ray lies in a face plane,
+ * where the closed-tet measure counts both sides of the plane).  Both give
+ * the plain definition; the walk is only the faster way to the same tets.
+ */
+#define WALK_TOL 1e-9
+
+typedef struct {
+    const double *verts;
+    const int32_t *tets;
+    int64_t nt, nb;
+    int32_t *adj;   /* [nt][4]: tet across the face opposite vertex k, or -1 */
+    int32_t *btet;  /* tets with at least one boundary face */
+    double *bbox;   /* [nb][6]: their boxes, min xyz then max xyz */
+} walker;
+
+typedef struct { int32_t b, c, code; } face_rec; /* code = tet * 4 + k */
+
+void oracle_walker_destroy(void *h) {
+    walker *w = (walker *)h;
+    if (!w) return;
+    free(w->adj);
+    free(w->btet);
+    free(w->bbox);
+    free(w);
+}
+
+static void sort3(int32_t *a, int32_t *b, int32_t *c) {
+    int32_t t;
+    if (*a > *b) { t = *a; *a = *b; *b = t; }
+    if (*b > *c) { t = *b; *b = *c; *c = t; }
+    if (*a > *b) { t = *a; *a = *b; *b = t; }
+}
+
+/* status: 0 ok, -1 out of memory, -3 a face shared by more than two tets,
+ * -4 a vertex id out of range. */
+void *oracle_walker_create(const double *verts, int64_t nv, const int32_t *tets, int64_t nt,
+                           int *status) {
+    *status = -1;
+    walker *w = (walker *)calloc(1, sizeof(walker));
+    int64_t nf = 4 * nt;
+    int64_t *start = (int64_t *)calloc((size_t)nv + 1, sizeof(int64_t));
+    face_rec *rec = (face_rec *)malloc(sizeof(face_rec) * (size_t)(nf > 0 ? nf : 1));
+    if (!w || !start || !rec) { free(start); free(rec); oracle_walker_destroy(w); return NULL; }
+    w->verts = verts; w->tets = tets; w->nt = nt;
+    w->adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nf > 0 ? nf : 1));
+    if (!w->adj) { free(start); free(rec); oracle_walker_destroy(w); return NULL; }
+    for (int64_t q = 0; q < nf; ++q) {
+        int32_t v = tets[q];
+        if (v < 0 || v >= nv) { *status = -4; free(start); free(rec); oracle_walker_destroy(w); return NULL; }
+        w->adj[q] = -1;
+    }
+    /* bucket the faces by their smallest vertex id (counting sort), then sort
+     * each bucket by the other two ids */
+    for (int64_t i = 0; i < nt; ++i)
+        for (int k = 0; k < 4; ++k) {
+            int32_t a = tets[4 * i + ((k + 1) & 3)], b = tets[4 * i + ((k + 2) & 3)],
+                    c = tets[4 * i + ((k + 3) & 3)];
+            sort3(&a, &b, &c);
+            start[a + 1]++;
+        }
+    for (int64_t v = 0; v < nv; ++v) start[v + 1] += start[v];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nv > 0 ? nv : 1));
+    if (!fill) { free(start); free(rec); oracle_walker_destroy(w); return NULL; }
+    memcpy(fill, start, sizeof(int64_t) * (size_t)nv);
+    for (int64_t i = 0; i < nt; ++i)
+        for (int k = 0; k < 4; ++k) {
+            int32_t a = tets[4 * i + ((k + 1) & 3)], b = tets[4 * i + ((k + 2) & 3)],
+                    c = tets[4 * i + ((k + 3) & 3)];
+            sort3(&a, &b, &c);
+            face_rec r = {b, c, (int32_t)(4 * i + k)};
+            rec[fill[a]++] = r;
+        }
+    free(fill);
+    *status = 0;
+    for (int64_t v = 0; v < nv && *status == 0; ++v) {
+        face_rec *f = rec + start[v];
+        int64_t n = start[v + 1] - start[v];
+        for (int64_t x = 1; x < n; ++x) {  /* insertion sort: buckets are small */
+            face_rec r = f[x];
+            int64_t y = x - 1;
+            while (y >= 0 && (f[y].b > r.b || (f[y].b == r.b && f[y].c > r.c))) { f[y + 1] = f[y]; --y; }
+            f[y + 1] = r;
+        }
+        for (int64_t x = 0; x < n;) {
+            int64_t e = x + 1;
+            while (e < n && f[e].b == f[x].b && f[e].c == f[x].c) ++e;
+            if (e - x > 2) { *status = -3; break; }
+            if (e - x == 2) {
+                w->adj[f[x].code] = f[x + 1].code >> 2;
+                w->adj[f[x + 1].code] = f[x].code >> 2;
+            }
+            x = e;
+        }
+    }
+    free(start);
+    free(rec);
+    if (*status) { oracle_walker_destroy(w); return NULL; }
+    int64_t nb = 0;
+    for (int64_t i = 0; i < nt; ++i)
+        if (w->adj[4 * i] < 0 || w->adj[4 * i + 1] < 0 || w->adj[4 * i + 2] < 0 || w->adj[4 * i + 3] < 0) ++nb;
+    w->nb = nb;
+    w->btet = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
+    w->bbox = (double *)malloc(sizeof(double) * 6 * (size_t)(nb > 0 ? nb : 1));
+    if (!w->btet || !w->bbox) { *status = -1; oracle_walker_destroy(w); return NULL; }
+    nb = 0;
+    for (int64_t i = 0; i < nt; ++i) {
+        if (!(w->adj[4 * i] < 0 || w->adj[4 * i + 1] < 0 || w->adj[4 * i + 2] < 0 || w->adj[4 * i + 3] < 0))
+            continue;
+        double *bx = w->bbox + 6 * nb;
+        for (int q = 0; q < 3; ++q) { bx[q] = INFINITY; bx[3 + q] = -INFINITY; }
+        for (int k = 0; k < 4; ++k) {
+            const double *p = verts + 3 * (int64_t)tets[4 * i + k];
+            for (int q = 0; q < 3; ++q) {
+                if (p[q] < bx[q]) bx[q] = p[q];
+                if (p[q] > bx[3 + q]) bx[3 + q] = p[q];
+            }
+        }
+        w->btet[nb++] = (int32_t)i;
+    }
+    return w;
+}
+
+/* Outward face planes of tet v along the ray (the orientation rule of
+ * tet_clip_range): den[k] = n_k.d and, for den[k] != 0, tf[k] = the t at which
+ * the ray meets face k's plane. */
+static void tet_face_params(const double v[4][3], const double S[3], const double d[3],
+                            double tf[4], double den[4]) {
+    for (int k = 0; k < 4; ++k) {
+        const double *q0 = v[(k + 1) & 3], *q1 = v[(k + 2) & 3], *q2 = v[(k + 3) & 3];
+        double e1[3], e2[3], n[3], x[3], qs[3];
+        sub3(q1, q0, e1);
+        sub3(q2, q0, e2);
+        cross3(e1, e2, n);
+        sub3(v[k], q0, x);
+        if (dot3(n, x) > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+        sub3(q0, S, qs);
+        den[k] = dot3(n, d);
+        tf[k] = den[k] != 0.0 ? dot3(n, qs) / den[k] : 0.0;
+    }
+}
+
+typedef struct { int32_t tet; double a; } wseg;
+typedef struct { wseg *s; int64_t n, cap; } wbuf;
+
+static int wpush(wbuf *b, int32_t tet, double a) {
+    if (b->n == b->cap) {
+        int64_t cap = b->cap ? 2 * b->cap : 256;
+        wseg *s = (wseg *)realloc(b->s, sizeof(wseg) * (size_t)cap);
+        if (!s) return -1;
+        b->s = s;
+        b->cap = cap;
+    }
+    b->s[b->n].tet = tet;
+    b->s[b->n].a = a;
+    ++b->n;
+    return 0;
+}
+
+/* Row j of A by brute force over all tets; 2 if some face plane contains the ray. */
+static int walk_brute(const walker *w, const double S[3], const double d[3], double len, wbuf *out) {
+    int planar_any = 0;
+    out->n = 0;
+    for (int64_t i = 0; i < w->nt; ++i) {
+        double v[4][3], lo, hi;
+        int planar;
+        load_tet(w->verts, w->tets, i, v);
+        if (!tet_clip(v, S, d, NULL, &lo, &hi, &planar)) continue;
+        if (planar) planar_any = 1;
+        if (hi > lo && wpush(out, (int32_t)i, (hi - lo) * len)) return -1;
+    }
+    return planar_any ? 2 : 1;
+}
+
+/* Does the half-line S + t d, t >= 0, meet the box (grown by pad)? */
+static int ray_meets_box(const double *bx, const double S[3], const double d[3], double pad) {
+    double t0 = 0.0, t1 = INFINITY;
+    for (int q = 0; q < 3; ++q) {
+        double lo = bx[q] - pad, hi = bx[3 + q] + pad;
+        if (d[q] == 0.0) {
+            if (S[q] < lo || S[q] > hi) return 0;
+            continue;
+        }
+        double a = (lo - S[q]) / d[q], b = (hi - S[q]) / d[q];
+        if (a > b) { double t = a; a = b; b = t; }
+        if (a > t0) t0 = a;
+        if (b < t1) t1 = b;
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+/* Row j of A (the tets with a_ij > 0 and their a_ij) by the walk: 0; or, for a
+ * ray the walk does not take (see above), by brute force: 1 or 2. -1: no memory. */
+static int walk_row(const walker *w, const double S[3], const double P[3], wbuf *out) {
+    double d[3];
+    sub3(P, S, d);
+    const double len = sqrt(dot3(d, d));
+    const double pad = 1e-9 * (1.0 + fabs(S[0]) + fabs(S[1]) + fabs(S[2]) + len);
+    out->n = 0;
+    int32_t cur = -1;
+    double lo = INFINITY, hi = 0.0, second = INFINITY;
+    for (int64_t q = 0; q < w->nb; ++q) {
+        if (!ray_meets_box(w->bbox + 6 * q, S, d, pad)) continue;
+        double v[4][3], l, h;
+        int planar;
+        load_tet(w->verts, w->tets, w->btet[q], v);
+        if (!tet_clip(v, S, d, NULL, &l, &h, &planar)) return walk_brute(w, S, d, len, out);
+        if (planar) return walk_brute(w, S, d, len, out);
+        if (!(h > l)) continue;
+        if (l < lo) { second = lo; lo = l; hi = h; cur = w->btet[q]; }
+        else if (l < second) second = l;
+    }
+    if (cur < 0) return 0;  /* the half-line misses the mesh (or only touches it) */
+    if (second - lo <= WALK_TOL) return walk_brute(w, S, d, len, out);
+    {
+        /* the entry must be through a boundary face: the face plane that sets lo */
+        double v[4][3], tf[4], den[4];
+        load_tet(w->verts, w->tets, cur, v);
+        tet_face_params(v, S, d, tf, den);
+        int nset = 0, bnd = 0;
+        for (int k = 0; k < 4; ++k)
+            if (den[k] < 0.0 && fabs(tf[k] - lo) <= WALK_TOL) { ++nset; bnd = w->adj[4 * (int64_t)cur + k] < 0; }
+        if (nset != 1 || !bnd) return walk_brute(w, S, d, len, out);
+    }
+    for (int64_t steps = 0; steps < w->nt; ++steps) {
+        if (hi - lo <= WALK_TOL) return walk_brute(w, S, d, len, out);
+        if (wpush(out, cur, (hi - lo) * len)) return -1;
+        double v[4][3], tf[4], den[4];
+        load_tet(w->verts, w->tets, cur, v);
+        tet_face_params(v, S, d, tf, den);
+        int g = -1;
+        for (int k = 0; k < 4; ++k)
+            if (den[k] > 0.0 && (g < 0 || tf[k] < tf[g])) g = k;
+        if (g < 0 || fabs(tf[g] - hi) > WALK_TOL) return walk_brute(w, S, d, len, out);
+        for (int k = 0; k < 4; ++k)
+            if (k != g && den[k] > 0.0 && tf[k] - tf[g] <= WALK_TOL) return walk_brute(w, S, d, len, out);
+        const int32_t nxt = w->adj[4 * (int64_t)cur + g];
+        if (nxt < 0) return 0;
+        int planar;
+        load_tet(w->verts, w->tets, nxt, v);
+        if (!tet_clip(v, S, d, NULL, &lo, &hi, &planar) || planar || fabs(lo - tf[g]) > WALK_TOL)
+            return walk_brute(w, S, d, len, out);
+        cur = nxt;
+    }
+    return walk_brute(w, S, d, len, out);
+}
+
+typedef struct {
+    const walker *w;
+    const cone_geom *geom;
+    const int64_t *ray_idx;
+    const double *S, *P;
+    const double *mu, *y;
+    int C;
+    int64_t begin, end;
+    double *out;    /* forward: [n][C] */
+    int8_t *status; /* [n] */
+    wbuf rows;      /* backward: this thread's rows, concatenated */
+    int64_t *row_end; /* [end - begin]: end of each ray's row in rows */
+    int rc;
+} wjob;
+
+static void *walk_worker(void *arg) {
+    wjob *jb = (wjob *)arg;
+    wbuf row = {NULL, 0, 0};
+    for (int64_t k = jb->begin; k < jb->end; ++k) {
+        double S[3], P[3];
+        if (jb->geom) {
+            cone_ray(jb->geom, jb->ray_idx ? jb->ray_idx[k] : k, S, P);
+        } else {
+            memcpy(S, jb->S + 3 * k, sizeof(S));
+            memcpy(P, jb->P + 3 * k, sizeof(P));
+        }
+        int st = walk_row(jb->w, S, P, &row);
+        if (st < 0) { jb->rc = -1; break; }
+        jb->status[k] = (int8_t)st;
+        if (jb->mu) {
+            nsum acc[16];
+            for (int c = 0; c < jb->C; ++c) acc[c].s = acc[c].c = 0.0;
+            for (int64_t q = 0; q < row.n; ++q)
+                for (int c = 0; c < jb->C; ++c)
+                    nadd(&acc[c], row.s[q].a * jb->mu[(int64_t)row.s[q].tet * jb->C + c]);
+            for (int c = 0; c < jb->C; ++c) jb->out[k * jb->C + c] = nval(&acc[c]);
+        }
+        if (jb->y) {
+            for (int64_t q = 0; q < row.n; ++q)
+                if (wpush(&jb->rows, row.s[q].tet, row.s[q].a)) { jb->rc = -1; break; }
+            jb->row_end[k - jb->begin] = jb->rows.n;
+        }
+        if (jb->rc) break;
+    }
+    free(row.s);
+    return NULL;
+}
+
+/*
+ * Rows of A for n rays by the walker: cone rays ray_idx[0..n) of the geometry
+ * (geom_* given, S = P = NULL), or explicit rays S, P [n][3].
+ *   mu != NULL: out_fwd[k][c] = sum_i a_ik mu[i][c]        (Eq. 2)
+ *   y  != NULL: out_bwd[i][c] = sum_k a_ik y[k][c]          (Eq. 3 over these
+ *               rays only; y is indexed by k, not by the cone ray index), and,
+ *               if out_count != NULL, out_count[i] = #{k : a_ik > 0}
+ * status[k]: 0 walked, 1 brute force, 2 brute force and a face plane contains
+ * the ray (closed-tet measure: the integral counts both sides).  Backward sums
+ * are added in ray order after the threads finish (deterministic).
+ * Returns 0, -1 (no memory) or -2 (C outside 1..16).
+ */
+int oracle_walk(void *h, const double *mu, const double *y, int C, double dso, double dsd,
+                int64_t nu, int64_t nv, double du, double dv, const double *angles, int64_t na,
+                const int64_t *ray_idx, const double *S, const double *P, int64_t n,
+                double *out_fwd, double *out_bwd, int64_t *out_count, int8_t *status,
+                int nthreads) {
+    const walker *w = (const walker *)h;
+    if (C < 1 || C > 16) return -2;
+    cone_geom g = {dso, dsd, du, dv, nu, nv, na, angles};
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n && n > 0) nthreads = (int)n;
+    wjob *jobs = (wjob *)calloc((size_t)nthreads, sizeof(wjob));
+    if (!jobs) return -1;
+    int rc = 0;
+    for (int i = 0; i < nthreads; ++i) {
+        wjob *j = &jobs[i];
+        j->w = w; j->geom = S ? NULL : &g; j->ray_idx = ray_idx; j->S = S; j->P = P;
+        j->mu = mu; j->y = y; j->C = C; j->out = out_fwd; j->status = status;
+        split(n, nthreads, i, &j->begin, &j->end);
+        if (y) {
+            j->row_end = (int64_t *)malloc(sizeof(int64_t) * (size_t)(j->end - j->begin + 1));
+            if (!j->row_end) rc = -1;
+        }
+    }
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    if (!th) rc = -1;
+    if (!rc) {
+        for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, walk_worker, &jobs[i]);
+        for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+        for (int i = 0; i < nthreads; ++i) if (jobs[i].rc) rc = jobs[i].rc;
+    }
+    if (!rc && y) {
+        int64_t m = w->nt * C;
+        nsum *acc = (nsum *)calloc((size_t)(m > 0 ? m : 1), sizeof(nsum));
+        if (!acc) rc = -1;
+        for (int i = 0; i < nthreads && !rc; ++i) {
+            wjob *j = &jobs[i];
+            int64_t q = 0;
+            for (int64_t k = j->begin; k < j->end; ++k)
+                for (; q < j->row_end[k - j->begin]; ++q)
+                    for (int c = 0; c < C; ++c)
+                        nadd(&acc[(int64_t)j->rows.s[q].tet * C + c], j->rows.s[q].a * y[k * C + c]);
+        }
+        if (!rc) for (int64_t q = 0; q < m; ++q) out_bwd[q] = nval(&acc[q]);
+        free(acc);
+        if (!rc && out_count) {
+            memset(out_count, 0, sizeof(int64_t) * (size_t)w->nt);
+            for (int i = 0; i < nthreads; ++i)
+                for (int64_t q = 0; q < jobs[i].rows.n; ++q) out_count[jobs[i].rows.s[q].tet]++;
+        }
+    }
+    for (int i = 0; i < nthreads; ++i) { free(jobs[i].rows.s); free(jobs[i].row_end); }
+    free(th);
+    free(jobs);
+    return rc;
+}

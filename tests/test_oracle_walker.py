@@ -1,0 +1,133 @@
+"""Pins of the oracle walker (oracle.Walker) -- CPU only.
+
+The walker finds the tets a ray crosses by walking face adjacency that it
+builds itself, and clips each with the brute-force clipper's own code, so it
+must give the brute-force rows of A exactly (summation order aside).  Pinned
+here against things outside the walker: the brute-force clipper (every tet
+tested against every ray), the closed-form chord of the cube (mu = 1), the
+per-ray tet counts of the brute-force trace, and mesh errors it must reject.
+It is also checked that the walk itself is what produces the values (most
+rays walked, not handed to the brute-force fallback).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+def cube_chord(S, P):
+    """|{t >= 0 : S + t (P - S) in [-1, 1]^3}| * |P - S| (slab method)."""
+    d = P - S
+    t0 = np.zeros(S.shape[0])
+    t1 = np.full(S.shape[0], np.inf)
+    for k in range(3):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            a = (-1.0 - S[:, k]) / d[:, k]
+            b = (1.0 - S[:, k]) / d[:, k]
+        lo = np.where(d[:, k] == 0, np.where(np.abs(S[:, k]) <= 1, -np.inf, np.inf), np.minimum(a, b))
+        hi = np.where(d[:, k] == 0, np.where(np.abs(S[:, k]) <= 1, np.inf, -np.inf), np.maximum(a, b))
+        t0 = np.maximum(t0, lo)
+        t1 = np.minimum(t1, hi)
+    return np.maximum(0.0, t1 - t0) * np.linalg.norm(d, axis=1)
+
+
+def small_meshes():
+    c2 = W.config2(n_cells=8, det=24, pitch=0.25, nangles=12)
+    c3 = W.config3(n_cells=8, det=24, pitch=0.25, nangles=12, n_adversarial=0)
+    c5 = W.config5_problem(3, 6, 20, 10)
+    return {"jittered": c2, "cubic": c3, "c5like": c5}
+
+
+@pytest.fixture(scope="module")
+def meshes():
+    return small_meshes()
+
+
+def test_config1_all_rays_equal_brute_force():
+    w = W.config1()
+    wk = oracle.Walker(w.verts, w.tets)
+    got, st = wk.forward_cone(w.mu, w.geom)
+    want = oracle.forward_cone(w.verts, w.tets, w.mu, w.geom)
+    scale = oracle.forward_cone(w.verts, w.tets, np.abs(w.mu), w.geom)
+    assert np.all(np.abs(got - want) <= 1e-14 * scale)
+    # the unjittered grid has many rays through edges: those take the fallback
+    assert (st == 0).mean() > 0.9
+    # rays reported in a face plane are planar by the brute-force trace too
+    S, P = oracle.cone_rays(w.geom)
+    planar = oracle.trace_rays(w.verts, w.tets, S, P, max_visits=2)[5]
+    assert np.all(planar[st == 2])
+
+
+@pytest.mark.parametrize("name", ["jittered", "cubic", "c5like"])
+def test_forward_and_backward_equal_brute_force(meshes, name):
+    w = meshes[name]
+    wk = oracle.Walker(w.verts, w.tets)
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(w.geom.nrays, 2000, replace=False))
+    mu = np.asarray(w.mu)
+    got, st = wk.forward_cone(mu, w.geom, idx)
+    want = oracle.forward_cone(w.verts, w.tets, mu, w.geom, idx)
+    scale = oracle.forward_cone(w.verts, w.tets, np.abs(mu), w.geom, idx)
+    assert np.all(np.abs(got - want) <= 1e-14 * scale + 1e-300)
+    assert (st == 0).mean() > 0.9, np.bincount(st)
+    C = 1 if mu.ndim == 1 else mu.shape[1]
+    y = rng.uniform(-1.0, 1.0, size=(idx.size, C)).squeeze()
+    x, _ = wk.backward_cone(y, w.geom, idx)
+    S, P = oracle.cone_rays(w.geom, idx)
+    xb = oracle.backward_rays(w.verts, w.tets, y, S, P)
+    xs = oracle.backward_rays(w.verts, w.tets, np.abs(y), S, P)
+    assert np.all(np.abs(x - xb) <= 1e-14 * xs + 1e-300)
+    # per-tet crossing counts = the brute-force trace's rows
+    tr_tet, _, _, tr_count = oracle.trace_rays(w.verts, w.tets, S, P, max_visits=512)[:4]
+    assert tr_count.max() <= 512
+    cnt = np.zeros(w.tets.shape[0], np.int64)
+    for k in range(idx.size):
+        np.add.at(cnt, tr_tet[k, :tr_count[k]], 1)
+    assert np.array_equal(wk.last_count, cnt)
+
+
+def test_explicit_rays_and_cube_chord(meshes):
+    w = meshes["jittered"]
+    wk = oracle.Walker(w.verts, w.tets)
+    S, P = W.random_rays_through_box(3000, np.random.default_rng(11))
+    ones = np.ones(w.tets.shape[0])
+    chord, st = wk.forward_rays(ones, S, P)
+    # Sum_i a_ij = the chord of the cube (jitter moves interior vertices only)
+    ref = cube_chord(S, P)
+    assert np.all(np.abs(chord - ref) <= 1e-12 * np.maximum(ref, 1.0))
+    assert (ref > 0).sum() > 1000 and (st[ref > 0] == 0).mean() > 0.95
+    mu = np.asarray(w.mu)
+    got, _ = wk.forward_rays(mu, S, P)
+    want = oracle.forward_rays(w.verts, w.tets, mu, S, P)
+    assert np.all(np.abs(got - want) <= 1e-14 * oracle.forward_rays(w.verts, w.tets, np.abs(mu), S, P) + 1e-300)
+
+
+def test_walk_is_what_produces_the_rows(meshes):
+    """The same mesh with its vertex ids and tet order permuted (so the
+    adjacency the walker builds, its face buckets and its boundary list all
+    change) gives the same values."""
+    w = meshes["jittered"]
+    rng = np.random.default_rng(3)
+    perm_v = rng.permutation(w.verts.shape[0])
+    inv = np.empty_like(perm_v)
+    inv[perm_v] = np.arange(perm_v.size)
+    perm_t = rng.permutation(w.tets.shape[0])
+    verts2 = w.verts[perm_v]
+    tets2 = inv[w.tets[perm_t]]
+    mu2 = np.asarray(w.mu)[perm_t]
+    idx = np.arange(0, w.geom.nrays, 5)
+    a, _ = oracle.Walker(w.verts, w.tets).forward_cone(w.mu, w.geom, idx)
+    b, _ = oracle.Walker(verts2, tets2).forward_cone(mu2, w.geom, idx)
+    assert np.all(np.abs(a - b) <= 1e-13 * np.maximum(np.abs(a), 1e-3))
+
+
+def test_rejects_bad_meshes():
+    verts, tets = W.kuhn_cube(2)
+    bad = np.concatenate([tets, tets[:1]])  # a tet twice: its faces are shared three times
+    with pytest.raises(RuntimeError, match="-3"):
+        oracle.Walker(verts, bad)
+    bad = tets.copy()
+    bad[0, 0] = verts.shape[0]
+    with pytest.raises(RuntimeError, match="-4"):
+        oracle.Walker(verts, bad)
