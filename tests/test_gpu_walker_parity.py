@@ -1,0 +1,199 @@
+"""Parity on 10^5 sampled rays per configuration (GPU) against the oracle
+walker (oracle.Walker: the brute-force clipper's a_ij, found by walking the
+oracle's own adjacency; pinned in test_oracle_walker).
+
+* Config 2 (the bench workload) and config 4, both precisions: the forward
+  projection at 10^5 seeded rays, and the backprojection of a y that is
+  non-zero on those rays only, compared at every tet they cross.
+* Config 5, all 24 problems through one batched launch (C = 4, filtered
+  FP32): 10^5 rays per problem, forward and backprojection as above; and
+  problems #9 and #5 on the plain FP64 path.
+
+Rays the walker finds inside a face plane (status 2: the closed-tet measure
+counts both sides there, the method follows one) are left out and counted;
+their references are the exact ones of test_gpu_parity / test_gpu_fullsize.
+
+Tolerances.  Per ray as in test_gpu_parity (max(tau sum a|mu|, 32 u R
+max|mu|)).  Per tet: tau sum_j a_ij |y_j| + n_i 32 u R max|y|, n_i the number
+of sampled rays crossing tet i: a crossing point is placed to a few u R, so
+each crossing's chord carries that much absolute error, and unlike a ray's
+sum, a tet's sum over rays does not cancel it.  How many tets only the
+second term admits is printed and bounded.  Tets that no sampled ray crosses
+must come out below 64 * 32 u R max|y| (a ray can graze a tet the oracle
+gives zero length).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+from test_gpu_parity import TOL, UNIT, check_rays, floor_abs
+
+pytestmark = pytest.mark.gpu
+
+NSAMPLE = 100_000
+
+
+@pytest.fixture(scope="module")
+def tp():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1908_06909_gb300 as tp
+    return tp
+
+
+def _dt(prec):
+    import torch
+    return torch.float32 if prec == "f32" else torch.float64
+
+
+def sample(nrays, seed, n=NSAMPLE):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(nrays, min(n, nrays), replace=False)), rng
+
+
+def check_tets(name, got, want, scale, cnt, prec, R, ymax, max_floor_frac=1.0):
+    """Per-tet parity (module doc) over all tets; prints the errors."""
+    got = np.asarray(got, np.float64).reshape(cnt.size, -1)
+    want = np.asarray(want, np.float64).reshape(cnt.size, -1)
+    scale = np.asarray(scale, np.float64).reshape(cnt.size, -1)
+    q = 32.0 * UNIT[prec] * R * ymax
+    hit = cnt > 0
+    err = np.abs(got - want)
+    rel = TOL[prec] * scale
+    bound = rel + (cnt * q)[:, None]
+    n_floor = int(np.sum(np.any(err[hit] > rel[hit], axis=1)))
+    r = err[hit] / np.maximum(scale[hit], 1e-300)
+    stray = float(np.abs(got[~hit]).max()) if (~hit).any() else 0.0
+    print(f"{name}: {int(hit.sum())} tets crossed, max rel {r.max():.3e} median rel "
+          f"{np.median(r):.3e} max abs {err[hit].max():.3e}; admitted only by the crossing "
+          f"term: {n_floor}; largest value at an uncrossed tet {stray:.3e}")
+    bad = np.nonzero(~np.all(err <= bound, axis=1) & hit)[0]
+    assert bad.size == 0, (name, bad[:5], err[bad[:5]], bound[bad[:5]])
+    assert stray <= 64 * q, (name, stray, 64 * q)
+    assert n_floor <= max(3, max_floor_frac * hit.sum()), (name, n_floor)
+
+
+def scatter_sample(geo_shape, C, idx, vals, dt):
+    """A full-size y (geo_shape, or geo_shape + (C,)) on the device, zero but
+    at the sampled rays."""
+    import torch
+    y = torch.zeros(int(np.prod(geo_shape)), C, dtype=dt, device="cuda")
+    y[torch.tensor(idx, device="cuda")] = torch.tensor(vals.reshape(-1, C), dtype=dt, device="cuda")
+    return y.view(*geo_shape, C) if C > 1 else y.view(*geo_shape)
+
+
+class Single:
+    """One mesh, its walker and a 10^5-ray sample with the oracle's rows:
+    forward of (mu, |mu|) and backprojection of y >= 0 on the sample."""
+
+    def __init__(self, tp, w, seed):
+        self.w = w
+        self.mesh = tp.Mesh(w.verts, w.tets)
+        self.geo = tp.Geometry.from_cone(w.geom)
+        self.idx, rng = sample(self.geo.nrays, seed)
+        mu = np.asarray(w.mu, np.float64)
+        self.C = 1 if mu.ndim == 1 else mu.shape[1]
+        # FP32-representable y in [0.5, 1.5]
+        self.yv = rng.uniform(0.5, 1.5, size=(self.idx.size, self.C)).astype(np.float32).astype(np.float64)
+        wk = oracle.Walker(w.verts, w.tets)
+        m2 = np.concatenate([mu.reshape(-1, self.C), np.abs(mu).reshape(-1, self.C)], axis=1)
+        y2 = np.concatenate([self.yv, self.yv], axis=1)
+        fwd, bwd, self.status = wk.rows_cone(m2, y2, w.geom, self.idx)
+        self.want, self.scale = fwd[:, :self.C], fwd[:, self.C:]
+        self.wantb = bwd[:, :self.C]
+        self.cnt = wk.last_count
+        self.planar = np.nonzero(self.status == 2)[0]
+        print(f"{w.name}: walker status counts {np.bincount(self.status, minlength=3)}")
+
+    def run(self, tp, prec, options=None):
+        import torch
+        dt = _dt(prec)
+        mu = torch.tensor(np.asarray(self.w.mu), dtype=dt, device="cuda")
+        self.mesh.stats_reset()
+        proj = tp.forward(self.mesh, self.geo, mu, options=options)
+        y = scatter_sample(self.geo.shape, self.C, self.idx, self.yv, dt)
+        back = tp.backward(self.mesh, self.geo, y, options=options)
+        torch.cuda.synchronize()
+        assert self.mesh.stats()["error"] == 0
+        got = proj.reshape(-1, self.C)[torch.tensor(self.idx, device="cuda")].double().cpu().numpy()
+        return got, back.double().cpu().numpy()
+
+    def check(self, tp, prec, options=None):
+        got, back = self.run(tp, prec, options)
+        w = self.w
+        R = float(np.abs(w.verts).max())
+        fl = floor_abs(prec, w.verts, np.asarray(w.mu))
+        for c in range(self.C):
+            check_rays(f"{w.name} forward {prec} channel {c} (10^5 rays, {self.planar.size} in-plane "
+                       f"left out)", got[:, c], self.want[:, c], self.scale[:, c], TOL[prec], fl,
+                       skip=self.planar)
+        check_tets(f"{w.name} backward {prec}", back, self.wantb, self.wantb, self.cnt, prec, R,
+                   float(self.yv.max()))
+
+
+@pytest.fixture(scope="module")
+def c2(tp):
+    return Single(tp, W.config2(), 61)
+
+
+@pytest.fixture(scope="module")
+def c4(tp):
+    return Single(tp, W.config4(), 62)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_config2_walker_sampled(tp, c2, prec):
+    c2.check(tp, prec)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_config4_walker_sampled(tp, c4, prec):
+    c4.check(tp, prec)
+
+
+@pytest.mark.parametrize("k", [9, 5])
+def test_config5_plain_fp64_walker_sampled(tp, k):
+    n, N, na = W.config5_specs()[k]
+    s = Single(tp, W.config5_problem(k, n, N, na, channels=4), 700 + k)
+    s.check(tp, "f64", tp.make_options(precision=tp.PLAIN_FP64, channels=4))
+
+
+def test_config5_all_problems_batched_walker_sampled(tp):
+    """All 24 problems in one batched launch (the bench's batched workload at
+    full size, default tiles), 10^5 rays per problem."""
+    import torch
+    specs = W.config5_specs()
+    ws = [W.config5_problem(k, n, N, na, channels=4) for k, (n, N, na) in enumerate(specs)]
+    meshes = [tp.Mesh(w.verts, w.tets) for w in ws]
+    geos = [tp.Geometry.from_cone(w.geom) for w in ws]
+    b = tp.Batch(meshes, geos, channels=4)
+    samples = []
+    for k, w in enumerate(ws):
+        idx, rng = sample(geos[k].nrays, 800 + k)
+        yv = rng.uniform(0.5, 1.5, size=(idx.size, 4)).astype(np.float32).astype(np.float64)
+        samples.append((idx, yv))
+        b.mu[k].copy_(torch.tensor(w.mu, dtype=torch.float32))
+        b.y[k].copy_(scatter_sample(geos[k].shape, 4, idx, yv, torch.float32).reshape(b.y[k].shape))
+    b.forward()
+    b.backward()
+    torch.cuda.synchronize()
+    for k, w in enumerate(ws):
+        assert meshes[k].stats()["error"] == 0, k
+        idx, yv = samples[k]
+        wk = oracle.Walker(w.verts, w.tets)
+        mu = np.asarray(w.mu, np.float64)  # U[0, 1]: sum a|mu| is the value itself
+        fwd, bwd, st = wk.rows_cone(mu, yv, w.geom, idx)
+        cnt = wk.last_count
+        planar = np.nonzero(st == 2)[0]
+        got = b.proj[k].reshape(-1, 4)[torch.tensor(idx, device="cuda")].double().cpu().numpy()
+        fl = floor_abs("f32", w.verts, mu)
+        for c in range(4):
+            check_rays(f"C5#{k} batched forward f32 channel {c} ({planar.size} in-plane left out)",
+                       got[:, c], fwd[:, c], fwd[:, c], TOL["f32"], fl, skip=planar)
+        back = b.mu_out[k].double().cpu().numpy()
+        check_tets(f"C5#{k} batched backward f32", back, bwd, bwd, cnt, "f32",
+                   float(np.abs(w.verts).max()), float(yv.max()))
+        del wk
+    b.close()
