@@ -552,7 +552,8 @@ int oracle_trace_rays(const double *verts, int64_t nv, const int32_t *tets, int6
  *
  *   entry  among the tets with a boundary face whose bounding box the
  *          half-line meets, the one with the smallest clipped lo (hi > lo);
- *          the face that sets lo must be a boundary face;
+ *          the face that sets lo must be a boundary face (a ray that meets
+ *          the mesh's box but crosses no such tet is not walked);
  *   step   the exit face is the face (n.d > 0) whose plane sets hi; the next
  *          tet is its neighbour; the walk ends at a boundary face.
  *
@@ -573,6 +574,7 @@ typedef struct {
     int32_t *adj;   /* [nt][4]: tet across the face opposite vertex k, or -1 */
     int32_t *btet;  /* tets with at least one boundary face */
     double *bbox;   /* [nb][6]: their boxes, min xyz then max xyz */
+    double box[6];  /* the mesh's box */
 } walker;
 
 typedef struct { int32_t b, c, code; } face_rec; /* code = tet * 4 + k */
@@ -664,6 +666,12 @@ void *oracle_walker_create(const double *verts, int64_t nv, const int32_t *tets,
     w->btet = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
     w->bbox = (double *)malloc(sizeof(double) * 6 * (size_t)(nb > 0 ? nb : 1));
     if (!w->btet || !w->bbox) { *status = -1; oracle_walker_destroy(w); return NULL; }
+    for (int q = 0; q < 3; ++q) { w->box[q] = INFINITY; w->box[3 + q] = -INFINITY; }
+    for (int64_t v = 0; v < nv; ++v)
+        for (int q = 0; q < 3; ++q) {
+            if (verts[3 * v + q] < w->box[q]) w->box[q] = verts[3 * v + q];
+            if (verts[3 * v + q] > w->box[3 + q]) w->box[3 + q] = verts[3 * v + q];
+        }
     nb = 0;
     for (int64_t i = 0; i < nt; ++i) {
         if (!(w->adj[4 * i] < 0 || w->adj[4 * i + 1] < 0 || w->adj[4 * i + 2] < 0 || w->adj[4 * i + 3] < 0))
@@ -772,7 +780,13 @@ static int walk_row(const walker *w, const double S[3], const double P[3], wbuf 
         if (l < lo) { second = lo; lo = l; hi = h; cur = w->btet[q]; }
         else if (l < second) second = l;
     }
-    if (cur < 0) return 0;  /* the half-line misses the mesh (or only touches it) */
+    if (cur < 0) {
+        /* no tet with a boundary face is crossed: the half-line misses the
+         * mesh, or enters it through a boundary edge or vertex into a tet
+         * that touches the boundary only there */
+        if (!ray_meets_box(w->box, S, d, pad)) return 0;
+        return walk_brute(w, S, d, len, out);
+    }
     if (second - lo <= WALK_TOL) return walk_brute(w, S, d, len, out);
     {
         /* the entry must be through a boundary face: the face plane that sets lo */

@@ -131,3 +131,48 @@ def test_rejects_bad_meshes():
     bad[0, 0] = verts.shape[0]
     with pytest.raises(RuntimeError, match="-4"):
         oracle.Walker(verts, bad)
+
+
+def test_entries_through_boundary_edges_and_vertices():
+    """Rays that enter the mesh exactly through a boundary edge or vertex can
+    cross no tet with a boundary face first (the tet they enter may touch the
+    boundary only there); the walker must still give the brute-force row, not
+    a miss.  Entry points on the x = 1 face: grid vertices, points of grid
+    lines, midpoints of the face diagonals; sources at random directions
+    outside that face (so no ray lies in a face plane)."""
+    verts, tets = W.kuhn_cube(4)
+    verts = W.jitter_interior(verts, tets, 4, W.rng_for(9, 1))
+    rng = np.random.default_rng(2)
+    mu = rng.uniform(0.5, 1.5, tets.shape[0])
+    g = np.linspace(-1.0, 1.0, 5)[1:-1]
+    E = [(1.0, a, b) for a in g for b in g]
+    E += [(1.0, a, z) for a in g for z in rng.uniform(-0.9, 0.9, 3)]
+    E += [(1.0, z, a) for a in g for z in rng.uniform(-0.9, 0.9, 3)]
+    E += [(1.0, a + 0.25, b + 0.25) for a in g for b in g]
+    E = np.array(E)
+    u = rng.normal(size=E.shape)
+    u[:, 0] = np.abs(u[:, 0]) + 0.5
+    S = E + 3.0 * u / np.linalg.norm(u, axis=1, keepdims=True)
+    P = E + (E - S)
+    wk = oracle.Walker(verts, tets)
+    got, st = wk.forward_rays(mu, S, P)
+    want = oracle.forward_rays(verts, tets, mu, S, P)
+    assert np.all(np.abs(got - want) <= 1e-14 * np.abs(want) + 1e-300)
+    assert np.all(want > 0)
+    assert np.all(st < 2) and np.any(st == 1)
+
+
+def test_ray_entering_and_leaving_through_boundary_edges():
+    """Problem #5 of the batched workload (jittered Kuhn 21^3), cone ray 35,374
+    (angle 0, source (4, 0, 0)): it enters the cube exactly on the boundary
+    grid line y = -3/7 of the face x = 1 and leaves on y = -5/7 of x = -1, and
+    every tet it crosses with positive length touches the boundary at most in
+    an edge.  No tet with a boundary face is crossed, yet the ray is not a
+    miss: the brute-force row (sum 0.986 on channel 0)."""
+    n, N, na = W.config5_specs()[5]
+    w = W.config5_problem(5, n, N, na, channels=4)
+    idx = np.array([35372, 35373, 35374, 35375, 35376])
+    got, st = oracle.Walker(w.verts, w.tets).forward_cone(w.mu, w.geom, idx)
+    want = oracle.forward_cone(w.verts, w.tets, w.mu, w.geom, idx)
+    assert np.all(np.abs(got - want) <= 1e-14 * np.abs(want) + 1e-300)
+    assert want[2, 0] > 0.9 and st[2] == 1
