@@ -95,6 +95,7 @@ def lib():
                                   ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_double, ctypes.c_double, _c_dp, ctypes.c_int64,
                                   _c_lp, _c_dp, _c_dp, ctypes.c_int64, _c_dp, _c_dp, _c_lp,
+                                  ctypes.c_double, _c_dp, _c_dp,
                                   ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
         L.oracle_walk.restype = ctypes.c_int
         for f in ("oracle_forward_rays", "oracle_forward_rays_range", "oracle_forward_cone", "oracle_backward_rays",
@@ -359,7 +360,7 @@ class Walker:
             _lib.oracle_walker_destroy(h)
             self._h = None
 
-    def _run(self, mu, y, geom, ray_idx, S, P, threads):
+    def _run(self, mu, y, geom, ray_idx, S, P, threads, cap=64.0):
         if S is not None:
             s, sp = _d(S)
             p, pp = _d(P)
@@ -384,14 +385,15 @@ class Walker:
         fwd = np.empty((n, C)) if mu is not None else None
         bwd = np.empty((self.nt, C)) if y is not None else None
         cnt = np.empty(self.nt, dtype=np.int64) if y is not None else None
+        kf = np.empty((n, C, 2)) if mu is not None else None
+        kb = np.empty((self.nt, C, 2)) if y is not None else None
         status = np.empty(n, dtype=np.int8)
-        _check(lib().oracle_walk(self._h, mp, yp, C, *g, angp, na, ip, sp, pp, n,
-                                 None if fwd is None else fwd.ctypes.data_as(_c_dp),
-                                 None if bwd is None else bwd.ctypes.data_as(_c_dp),
-                                 None if cnt is None else cnt.ctypes.data_as(_c_lp),
+        ptr = lambda a, t=_c_dp: None if a is None else a.ctypes.data_as(t)
+        _check(lib().oracle_walk(self._h, mp, yp, C, *g, angp, na, ip, sp, pp, n, ptr(fwd),
+                                 ptr(bwd), ptr(cnt, _c_lp), float(cap), ptr(kf), ptr(kb),
                                  status.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
                                  threads or default_threads()), "oracle_walk")
-        self.last_count = cnt
+        self.last_count, self.last_kf, self.last_kb = cnt, kf, kb
         return fwd, bwd, status
 
     def forward_cone(self, mu, geom, ray_idx=None, threads=None):
@@ -407,9 +409,15 @@ class Walker:
         _, bwd, st = self._run(None, y, geom, ray_idx, None, None, threads)
         return (bwd[:, 0] if np.asarray(y).ndim == 1 else bwd), st
 
-    def rows_cone(self, mu, y, geom, ray_idx, threads=None):
-        """Both at once (each row walked once): (b [n, C], x [nt, C], status)."""
-        return self._run(mu, y, geom, ray_idx, None, None, threads)
+    def rows_cone(self, mu, y, geom, ray_idx, threads=None, cap=64.0):
+        """Both at once (each row walked once): (b [n, C], x [nt, C], status).
+        Also sets the crossings' conditioning (``oracle_walk`` in oracle.c):
+        ``last_kf`` [n, C, 2] per ray, sum of |mu jump| w / sin over its
+        crossings, and ``last_kb`` [nt, C, 2] per tet, sum over the rays
+        crossing it of |y| (w_in / sin_in + w_out / sin_out); [..., 0] with
+        1 / sin capped at ``cap``, [..., 1] uncapped; w = distance from the
+        source + mesh radius."""
+        return self._run(mu, y, geom, ray_idx, None, None, threads, cap)
 
     def forward_rays(self, mu, S, P, threads=None):
         fwd, _, st = self._run(mu, None, None, None, S, P, threads)

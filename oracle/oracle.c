@@ -575,6 +575,7 @@ typedef struct {
     int32_t *btet;  /* tets with at least one boundary face */
     double *bbox;   /* [nb][6]: their boxes, min xyz then max xyz */
     double box[6];  /* the mesh's box */
+    double radius;  /* the largest |coordinate| */
 } walker;
 
 typedef struct { int32_t b, c, code; } face_rec; /* code = tet * 4 + k */
@@ -671,6 +672,7 @@ void *oracle_walker_create(const double *verts, int64_t nv, const int32_t *tets,
         for (int q = 0; q < 3; ++q) {
             if (verts[3 * v + q] < w->box[q]) w->box[q] = verts[3 * v + q];
             if (verts[3 * v + q] > w->box[3 + q]) w->box[3 + q] = verts[3 * v + q];
+            if (fabs(verts[3 * v + q]) > w->radius) w->radius = fabs(verts[3 * v + q]);
         }
     nb = 0;
     for (int64_t i = 0; i < nt; ++i) {
@@ -691,10 +693,11 @@ void *oracle_walker_create(const double *verts, int64_t nv, const int32_t *tets,
 }
 
 /* Outward face planes of tet v along the ray (the orientation rule of
- * tet_clip_range): den[k] = n_k.d and, for den[k] != 0, tf[k] = the t at which
- * the ray meets face k's plane. */
+ * tet_clip_range): den[k] = n_k.d, for den[k] != 0 tf[k] = the t at which the
+ * ray meets face k's plane, and sn[k] = |n_k.d| / (|n_k| |d|), the sine of
+ * the angle between the ray and that plane. */
 static void tet_face_params(const double v[4][3], const double S[3], const double d[3],
-                            double tf[4], double den[4]) {
+                            double tf[4], double den[4], double sn[4]) {
     for (int k = 0; k < 4; ++k) {
         const double *q0 = v[(k + 1) & 3], *q1 = v[(k + 2) & 3], *q2 = v[(k + 3) & 3];
         double e1[3], e2[3], n[3], x[3], qs[3];
@@ -706,23 +709,41 @@ static void tet_face_params(const double v[4][3], const double S[3], const doubl
         sub3(q0, S, qs);
         den[k] = dot3(n, d);
         tf[k] = den[k] != 0.0 ? dot3(n, qs) / den[k] : 0.0;
+        sn[k] = fabs(den[k]) / (sqrt(dot3(n, n)) * sqrt(dot3(d, d)));
     }
 }
 
-typedef struct { int32_t tet; double a; } wseg;
+/* One entry of a row: tet, a_ij, its clipped interval, and for the crossings
+ * where the ray enters (i) and leaves (o) it: the inverse sine of the angle
+ * with the face plane (g) and the distance from the source plus the mesh
+ * radius (w); gi = 0 when the interval starts at the source (t = 0). */
+typedef struct { int32_t tet; double a, lo, hi, gi, go, wi, wo; } wseg;
 typedef struct { wseg *s; int64_t n, cap; } wbuf;
 
-static int wpush(wbuf *b, int32_t tet, double a) {
-    if (b->n == b->cap) {
-        int64_t cap = b->cap ? 2 * b->cap : 256;
-        wseg *s = (wseg *)realloc(b->s, sizeof(wseg) * (size_t)cap);
-        if (!s) return -1;
-        b->s = s;
-        b->cap = cap;
-    }
-    b->s[b->n].tet = tet;
-    b->s[b->n].a = a;
-    ++b->n;
+static int wgrow(wbuf *b) {
+    if (b->n < b->cap) return 0;
+    int64_t cap = b->cap ? 2 * b->cap : 256;
+    wseg *s = (wseg *)realloc(b->s, sizeof(wseg) * (size_t)cap);
+    if (!s) return -1;
+    b->s = s;
+    b->cap = cap;
+    return 0;
+}
+
+static int wappend(wbuf *b, const wseg *e) {
+    if (wgrow(b)) return -1;
+    b->s[b->n++] = *e;
+    return 0;
+}
+
+static int wpush(wbuf *b, int32_t tet, double a, double lo, double hi) {
+    if (wgrow(b)) return -1;
+    wseg *e = b->s + b->n++;
+    memset(e, 0, sizeof(*e));
+    e->tet = tet;
+    e->a = a;
+    e->lo = lo;
+    e->hi = hi;
     return 0;
 }
 
@@ -736,7 +757,7 @@ static int walk_brute(const walker *w, const double S[3], const double d[3], dou
         load_tet(w->verts, w->tets, i, v);
         if (!tet_clip(v, S, d, NULL, &lo, &hi, &planar)) continue;
         if (planar) planar_any = 1;
-        if (hi > lo && wpush(out, (int32_t)i, (hi - lo) * len)) return -1;
+        if (hi > lo && wpush(out, (int32_t)i, (hi - lo) * len, lo, hi)) return -1;
     }
     return planar_any ? 2 : 1;
 }
@@ -790,9 +811,9 @@ static int walk_row(const walker *w, const double S[3], const double P[3], wbuf 
     if (second - lo <= WALK_TOL) return walk_brute(w, S, d, len, out);
     {
         /* the entry must be through a boundary face: the face plane that sets lo */
-        double v[4][3], tf[4], den[4];
+        double v[4][3], tf[4], den[4], sn[4];
         load_tet(w->verts, w->tets, cur, v);
-        tet_face_params(v, S, d, tf, den);
+        tet_face_params(v, S, d, tf, den, sn);
         int nset = 0, bnd = 0;
         for (int k = 0; k < 4; ++k)
             if (den[k] < 0.0 && fabs(tf[k] - lo) <= WALK_TOL) { ++nset; bnd = w->adj[4 * (int64_t)cur + k] < 0; }
@@ -800,10 +821,10 @@ static int walk_row(const walker *w, const double S[3], const double P[3], wbuf 
     }
     for (int64_t steps = 0; steps < w->nt; ++steps) {
         if (hi - lo <= WALK_TOL) return walk_brute(w, S, d, len, out);
-        if (wpush(out, cur, (hi - lo) * len)) return -1;
-        double v[4][3], tf[4], den[4];
+        if (wpush(out, cur, (hi - lo) * len, lo, hi)) return -1;
+        double v[4][3], tf[4], den[4], sn[4];
         load_tet(w->verts, w->tets, cur, v);
-        tet_face_params(v, S, d, tf, den);
+        tet_face_params(v, S, d, tf, den, sn);
         int g = -1;
         for (int k = 0; k < 4; ++k)
             if (den[k] > 0.0 && (g < 0 || tf[k] < tf[g])) g = k;
@@ -821,6 +842,32 @@ static int walk_row(const walker *w, const double S[3], const double P[3], wbuf 
     return walk_brute(w, S, d, len, out);
 }
 
+/* Crossing data of a row (see wseg), in order along the ray. */
+static int seg_lo_cmp(const void *x, const void *y) {
+    const wseg *a = (const wseg *)x, *b = (const wseg *)y;
+    return (a->lo > b->lo) - (a->lo < b->lo);
+}
+
+static void row_cond(const walker *w, const double S[3], const double d[3], double len, wbuf *row,
+                     int sorted) {
+    if (!sorted) qsort(row->s, (size_t)row->n, sizeof(wseg), seg_lo_cmp);
+    for (int64_t q = 0; q < row->n; ++q) {
+        wseg *e = row->s + q;
+        double v[4][3], tf[4], den[4], sn[4];
+        load_tet(w->verts, w->tets, e->tet, v);
+        tet_face_params(v, S, d, tf, den, sn);
+        int ki = -1, ko = -1;
+        for (int k = 0; k < 4; ++k) {
+            if (den[k] < 0.0 && (ki < 0 || tf[k] > tf[ki])) ki = k;
+            if (den[k] > 0.0 && (ko < 0 || tf[k] < tf[ko])) ko = k;
+        }
+        e->gi = (e->lo > 0.0 && ki >= 0) ? 1.0 / fmax(sn[ki], 1e-300) : 0.0;
+        e->go = ko >= 0 ? 1.0 / fmax(sn[ko], 1e-300) : 0.0;
+        e->wi = e->lo * len + w->radius;
+        e->wo = e->hi * len + w->radius;
+    }
+}
+
 typedef struct {
     const walker *w;
     const cone_geom *geom;
@@ -828,8 +875,10 @@ typedef struct {
     const double *S, *P;
     const double *mu, *y;
     int C;
+    double cap;
     int64_t begin, end;
     double *out;    /* forward: [n][C] */
+    double *kf;     /* forward conditioning: [n][C][2] */
     int8_t *status; /* [n] */
     wbuf rows;      /* backward: this thread's rows, concatenated */
     int64_t *row_end; /* [end - begin]: end of each ray's row in rows */
@@ -840,7 +889,7 @@ static void *walk_worker(void *arg) {
     wjob *jb = (wjob *)arg;
     wbuf row = {NULL, 0, 0};
     for (int64_t k = jb->begin; k < jb->end; ++k) {
-        double S[3], P[3];
+        double S[3], P[3], d[3];
         if (jb->geom) {
             cone_ray(jb->geom, jb->ray_idx ? jb->ray_idx[k] : k, S, P);
         } else {
@@ -850,17 +899,42 @@ static void *walk_worker(void *arg) {
         int st = walk_row(jb->w, S, P, &row);
         if (st < 0) { jb->rc = -1; break; }
         jb->status[k] = (int8_t)st;
+        sub3(P, S, d);
+        row_cond(jb->w, S, d, sqrt(dot3(d, d)), &row, st == 0);
+        const int C = jb->C;
         if (jb->mu) {
             nsum acc[16];
-            for (int c = 0; c < jb->C; ++c) acc[c].s = acc[c].c = 0.0;
+            for (int c = 0; c < C; ++c) acc[c].s = acc[c].c = 0.0;
             for (int64_t q = 0; q < row.n; ++q)
-                for (int c = 0; c < jb->C; ++c)
-                    nadd(&acc[c], row.s[q].a * jb->mu[(int64_t)row.s[q].tet * jb->C + c]);
-            for (int c = 0; c < jb->C; ++c) jb->out[k * jb->C + c] = nval(&acc[c]);
+                for (int c = 0; c < C; ++c)
+                    nadd(&acc[c], row.s[q].a * jb->mu[(int64_t)row.s[q].tet * C + c]);
+            for (int c = 0; c < C; ++c) jb->out[k * C + c] = nval(&acc[c]);
+        }
+        if (jb->mu && jb->kf) {
+            /* sum over the crossings of |mu before - mu after| (w / sin), with
+             * 1 / sin capped at cap ([0]) and not ([1]); mu = 0 outside */
+            for (int c = 0; c < C; ++c) {
+                double s0 = 0.0, s1 = 0.0, prev = 0.0, g = 0.0, wd = 0.0;
+                for (int64_t q = 0; q <= row.n; ++q) {
+                    double cur = q < row.n ? jb->mu[(int64_t)row.s[q].tet * C + c] : 0.0;
+                    if (q == 0) { g = row.n ? row.s[0].gi : 0.0; wd = row.n ? row.s[0].wi : 0.0; }
+                    else if (q == row.n) { g = row.s[q - 1].go; wd = row.s[q - 1].wo; }
+                    else {
+                        g = fmax(row.s[q - 1].go, row.s[q].gi);
+                        wd = fmax(row.s[q - 1].wo, row.s[q].wi);
+                    }
+                    double jump = fabs(prev - cur) * wd;
+                    s0 += jump * fmin(g, jb->cap);
+                    s1 += jump * g;
+                    prev = cur;
+                }
+                jb->kf[(k * C + c) * 2] = s0;
+                jb->kf[(k * C + c) * 2 + 1] = s1;
+            }
         }
         if (jb->y) {
-            for (int64_t q = 0; q < row.n; ++q)
-                if (wpush(&jb->rows, row.s[q].tet, row.s[q].a)) { jb->rc = -1; break; }
+            for (int64_t q = 0; q < row.n && !jb->rc; ++q)
+                if (wappend(&jb->rows, &row.s[q])) jb->rc = -1;
             jb->row_end[k - jb->begin] = jb->rows.n;
         }
         if (jb->rc) break;
@@ -876,6 +950,14 @@ static void *walk_worker(void *arg) {
  *   y  != NULL: out_bwd[i][c] = sum_k a_ik y[k][c]          (Eq. 3 over these
  *               rays only; y is indexed by k, not by the cone ray index), and,
  *               if out_count != NULL, out_count[i] = #{k : a_ik > 0}
+ * Conditioning of the crossings (for error bounds: under rounding a crossing
+ * moves along the ray by ~u (its distance from the source + the mesh radius)
+ * / sin of the angle between ray and face plane), with 1 / sin capped at
+ * `cap` in [..][0] and uncapped in [..][1]:
+ *   out_kf [n][C][2] (with mu): sum over a ray's crossings of
+ *       |mu before - mu after| w / sin, mu = 0 outside the mesh;
+ *   out_kb [nt][C][2] (with y): sum over the rays crossing tet i of
+ *       |y[k][c]| (w_in / sin_in + w_out / sin_out).
  * status[k]: 0 walked, 1 brute force, 2 brute force and a face plane contains
  * the ray (closed-tet measure: the integral counts both sides).  Backward sums
  * are added in ray order after the threads finish (deterministic).
@@ -884,8 +966,8 @@ static void *walk_worker(void *arg) {
 int oracle_walk(void *h, const double *mu, const double *y, int C, double dso, double dsd,
                 int64_t nu, int64_t nv, double du, double dv, const double *angles, int64_t na,
                 const int64_t *ray_idx, const double *S, const double *P, int64_t n,
-                double *out_fwd, double *out_bwd, int64_t *out_count, int8_t *status,
-                int nthreads) {
+                double *out_fwd, double *out_bwd, int64_t *out_count, double cap,
+                double *out_kf, double *out_kb, int8_t *status, int nthreads) {
     const walker *w = (const walker *)h;
     if (C < 1 || C > 16) return -2;
     cone_geom g = {dso, dsd, du, dv, nu, nv, na, angles};
@@ -897,7 +979,8 @@ int oracle_walk(void *h, const double *mu, const double *y, int C, double dso, d
     for (int i = 0; i < nthreads; ++i) {
         wjob *j = &jobs[i];
         j->w = w; j->geom = S ? NULL : &g; j->ray_idx = ray_idx; j->S = S; j->P = P;
-        j->mu = mu; j->y = y; j->C = C; j->out = out_fwd; j->status = status;
+        j->mu = mu; j->y = y; j->C = C; j->cap = cap; j->out = out_fwd; j->kf = out_kf;
+        j->status = status;
         split(n, nthreads, i, &j->begin, &j->end);
         if (y) {
             j->row_end = (int64_t *)malloc(sizeof(int64_t) * (size_t)(j->end - j->begin + 1));
@@ -929,6 +1012,24 @@ int oracle_walk(void *h, const double *mu, const double *y, int C, double dso, d
             memset(out_count, 0, sizeof(int64_t) * (size_t)w->nt);
             for (int i = 0; i < nthreads; ++i)
                 for (int64_t q = 0; q < jobs[i].rows.n; ++q) out_count[jobs[i].rows.s[q].tet]++;
+        }
+        if (!rc && out_kb) {
+            memset(out_kb, 0, sizeof(double) * (size_t)(2 * m));
+            for (int i = 0; i < nthreads; ++i) {
+                wjob *j = &jobs[i];
+                int64_t q = 0;
+                for (int64_t k = j->begin; k < j->end; ++k)
+                    for (; q < j->row_end[k - j->begin]; ++q) {
+                        const wseg *e = j->rows.s + q;
+                        double c0 = e->wi * fmin(e->gi, cap) + e->wo * fmin(e->go, cap);
+                        double c1 = e->wi * e->gi + e->wo * e->go;
+                        for (int c = 0; c < C; ++c) {
+                            double ay = fabs(y[k * C + c]);
+                            out_kb[((int64_t)e->tet * C + c) * 2] += ay * c0;
+                            out_kb[((int64_t)e->tet * C + c) * 2 + 1] += ay * c1;
+                        }
+                    }
+            }
         }
     }
     for (int i = 0; i < nthreads; ++i) { free(jobs[i].rows.s); free(jobs[i].row_end); }

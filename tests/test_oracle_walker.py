@@ -176,3 +176,61 @@ def test_ray_entering_and_leaving_through_boundary_edges():
     want = oracle.forward_cone(w.verts, w.tets, w.mu, w.geom, idx)
     assert np.all(np.abs(got - want) <= 1e-14 * np.abs(want) + 1e-300)
     assert want[2, 0] > 0.9 and st[2] == 1
+
+
+def test_crossing_conditioning_by_hand():
+    """The conditioning sums the parity tests scale their floors by, on the
+    corner tet (0,0,0), (1,0,0), (0,1,0), (0,0,1) and the ray from (-2, .1, .2)
+    along +x (d = (4, 0, 0)): it enters through x = 0 at t = 1/2 (distance 2
+    from the source, sin 1) and leaves through x + y + z = 1 at x = 0.7,
+    t = 0.675 (distance 2.7, sin 1/sqrt 3); mesh radius 1.  Per ray
+    K = |mu| (2 + 1) / 1 + |mu| (2.7 + 1) sqrt 3; per tet the same with |y|;
+    with 1 / sin capped at 1 the second term loses its sqrt 3."""
+    verts = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    tets = np.array([[0, 1, 2, 3]])
+    S = np.array([[-2.0, 0.1, 0.2]])
+    P = S + np.array([[4.0, 0, 0]])
+    wk = oracle.Walker(verts, tets)
+    for cap, g_out in ((64.0, np.sqrt(3.0)), (1.0, 1.0)):
+        fwd, bwd, st = wk._run(np.array([-1.5]), np.array([2.0]), None, None, S, P, 1, cap)
+        assert st[0] == 0 and abs(fwd[0, 0] - (-1.5 * 0.7)) < 1e-15
+        want = 3.0 + 3.7 * g_out
+        assert abs(wk.last_kf[0, 0, 0] - 1.5 * want) < 1e-13
+        assert abs(wk.last_kf[0, 0, 1] - 1.5 * (3.0 + 3.7 * np.sqrt(3.0))) < 1e-13
+        assert abs(wk.last_kb[0, 0, 0] - 2.0 * want) < 1e-13
+        assert abs(bwd[0, 0] - 2.0 * 0.7) < 1e-15
+
+
+def test_crossing_conditioning_constant_mu(meshes):
+    """mu = 1 on a jittered mesh: mu jumps only where the ray enters and leaves
+    the cube, so K = (L_in + R) / sin_in + (L_out + R) / sin_out with the
+    cube's axis faces (sin = |d_k| / |d| for the face normal to axis k),
+    L the distance from the source, R = 1."""
+    w = meshes["jittered"]
+    wk = oracle.Walker(w.verts, w.tets)
+    S, P = W.random_rays_through_box(2000, np.random.default_rng(12))
+    d = P - S
+    dn = np.linalg.norm(d, axis=1)
+    chord = cube_chord(S, P)
+    ok = chord > 1e-3
+    _, _, st = wk._run(np.ones(w.tets.shape[0]), None, None, None, S[ok], P[ok], None, 64.0)
+    K = wk.last_kf[:, 0, 1]
+    t_in = np.full(S.shape[0], -np.inf)
+    t_out = np.full(S.shape[0], np.inf)
+    ax_in = np.zeros(S.shape[0], int)
+    ax_out = np.zeros(S.shape[0], int)
+    for k in range(3):
+        with np.errstate(divide="ignore"):
+            a = (-1.0 - S[:, k]) / d[:, k]
+            b = (1.0 - S[:, k]) / d[:, k]
+        lo, hi = np.minimum(a, b), np.maximum(a, b)
+        ax_in = np.where(lo > t_in, k, ax_in)
+        t_in = np.maximum(t_in, lo)
+        ax_out = np.where(hi < t_out, k, ax_out)
+        t_out = np.minimum(t_out, hi)
+    r = np.arange(S.shape[0])
+    want = ((t_in * dn + 1.0) * dn / np.abs(d[r, ax_in]) +
+            (t_out * dn + 1.0) * dn / np.abs(d[r, ax_out]))[ok]
+    keep = st == 0
+    assert keep.mean() > 0.95
+    assert np.all(np.abs(K[keep] - want[keep]) <= 1e-9 * want[keep])
