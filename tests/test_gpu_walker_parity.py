@@ -10,8 +10,9 @@ oracle's own adjacency; pinned in test_oracle_walker).
   problems #9 and #5 on the plain FP64 path.
 
 Rays the walker finds inside a face plane (status 2: the closed-tet measure
-counts both sides there, the method follows one) are left out and counted;
-their references are the exact ones of test_gpu_parity / test_gpu_fullsize.
+counts both sides there, the method follows one) are left out of the forward
+checks and get y = 0 in the backprojections; their references are the exact
+ones of test_gpu_parity / test_gpu_fullsize.
 
 Tolerances, from the arithmetic.  Rounding moves a crossing point along the
 ray by about u (L + R) / sin(alpha): L its distance from the source, R the
@@ -103,6 +104,16 @@ def check_uncrossed(name, got, cnt, prec, R, ymax):
     assert stray <= 64 * q, (name, stray, 64 * q)
 
 
+def planar_free_y(wk, geom, idx, rng, C):
+    """y for the sampled rays: U[0.5, 1.5] (FP32-representable), but 0 on
+    rays that lie inside a face plane (walker status 2), whose split between
+    the tets on either side of the plane is not unique."""
+    _, st = wk.forward_cone(np.zeros((wk.nt, C)), geom, idx)
+    y = rng.uniform(0.5, 1.5, size=(idx.size, C)).astype(np.float32).astype(np.float64)
+    y[st == 2] = 0.0
+    return y
+
+
 def scatter_sample(geo_shape, C, idx, vals, dt):
     """A full-size y (geo_shape, or geo_shape + (C,)) on the device, zero but
     at the sampled rays."""
@@ -123,9 +134,9 @@ class Single:
         self.idx, rng = sample(self.geo.nrays, seed)
         mu = np.asarray(w.mu, np.float64)
         self.C = 1 if mu.ndim == 1 else mu.shape[1]
-        # FP32-representable y in [0.5, 1.5]
-        self.yv = rng.uniform(0.5, 1.5, size=(self.idx.size, self.C)).astype(np.float32).astype(np.float64)
         wk = oracle.Walker(w.verts, w.tets)
+        # FP32-representable y in [0.5, 1.5], 0 on rays inside a face plane
+        self.yv = planar_free_y(wk, w.geom, self.idx, rng, self.C)
         m2 = np.concatenate([mu.reshape(-1, self.C), np.abs(mu).reshape(-1, self.C)], axis=1)
         y2 = np.concatenate([self.yv, self.yv], axis=1)
         fwd, bwd, self.status = wk.rows_cone(m2, y2, w.geom, self.idx)
@@ -200,7 +211,7 @@ def test_config5_all_problems_batched_walker_sampled(tp):
     samples = []
     for k, w in enumerate(ws):
         idx, rng = sample(geos[k].nrays, 800 + k)
-        yv = rng.uniform(0.5, 1.5, size=(idx.size, 4)).astype(np.float32).astype(np.float64)
+        yv = planar_free_y(oracle.Walker(w.verts, w.tets), w.geom, idx, rng, 4)
         samples.append((idx, yv))
         b.mu[k].copy_(torch.tensor(w.mu, dtype=torch.float32))
         b.y[k].copy_(scatter_sample(geos[k].shape, 4, idx, yv, torch.float32).reshape(b.y[k].shape))
