@@ -98,6 +98,10 @@ def lib():
                                   ctypes.c_double, _c_dp, _c_dp,
                                   ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
         L.oracle_walk.restype = ctypes.c_int
+        L.oracle_walk_trace.argtypes = [ctypes.c_void_p, _c_dp, _c_dp, ctypes.c_int64,
+                                        ctypes.c_int64, _c_ip, _c_dp, _c_dp, _c_lp,
+                                        ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
+        L.oracle_walk_trace.restype = ctypes.c_int
         for f in ("oracle_forward_rays", "oracle_forward_rays_range", "oracle_forward_cone", "oracle_backward_rays",
                   "oracle_backward_cone", "oracle_backward_cone_subset", "oracle_trace_rays"):
             getattr(L, f).restype = ctypes.c_int
@@ -418,6 +422,29 @@ class Walker:
         1 / sin capped at ``cap``, [..., 1] uncapped; w = distance from the
         source + mesh radius."""
         return self._run(mu, y, geom, ray_idx, None, None, threads, cap)
+
+    def trace_rays(self, S, P, max_visits=512, threads=None):
+        """Visit sequences of explicit rays: (tet [n, max_visits] int32, a_ij
+        [n, max_visits], count [n], status [n]); tets in walk order (rays not
+        walked: the brute-force row sorted by entry parameter).  Sets
+        ``last_cond`` [n, max_visits, 2]: each visit's (L + R) / sin summed
+        over its two crossings (1 / sin capped at 64, uncapped), the scale of
+        its chord's rounding error (see ``rows_cone``)."""
+        s, sp = _d(S)
+        p, pp = _d(P)
+        n = s.shape[0]
+        tet = np.full((n, max_visits), -1, dtype=np.int32)
+        ln = np.zeros((n, max_visits))
+        cnt = np.empty(n, dtype=np.int64)
+        st = np.empty(n, dtype=np.int8)
+        cond = np.zeros((n, max_visits, 2))
+        self.last_cond = cond
+        _check(lib().oracle_walk_trace(self._h, sp, pp, n, max_visits, tet.ctypes.data_as(_c_ip),
+                                       ln.ctypes.data_as(_c_dp), cond.ctypes.data_as(_c_dp),
+                                       cnt.ctypes.data_as(_c_lp),
+                                       st.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                       threads or default_threads()), "oracle_walk_trace")
+        return tet, ln, cnt, st
 
     def forward_rays(self, mu, S, P, threads=None):
         fwd, _, st = self._run(mu, None, None, None, S, P, threads)

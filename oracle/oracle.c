@@ -1037,3 +1037,74 @@ int oracle_walk(void *h, const double *mu, const double *y, int C, double dso, d
     free(jobs);
     return rc;
 }
+
+typedef struct {
+    const walker *w;
+    const double *S, *P;
+    int64_t begin, end, max_visits;
+    int32_t *tet;   /* [n][max_visits] */
+    double *len;    /* [n][max_visits] */
+    double *cond;   /* [n][max_visits][2] or NULL */
+    int64_t *count; /* [n] */
+    int8_t *status; /* [n] */
+    int rc;
+} tjob;
+
+static void *trace_walk_worker(void *arg) {
+    tjob *jb = (tjob *)arg;
+    wbuf row = {NULL, 0, 0};
+    for (int64_t k = jb->begin; k < jb->end; ++k) {
+        double S[3], P[3];
+        memcpy(S, jb->S + 3 * k, sizeof(S));
+        memcpy(P, jb->P + 3 * k, sizeof(P));
+        int st = walk_row(jb->w, S, P, &row);
+        if (st < 0) { jb->rc = -1; break; }
+        jb->status[k] = (int8_t)st;
+        double d[3];
+        sub3(P, S, d);
+        row_cond(jb->w, S, d, sqrt(dot3(d, d)), &row, st == 0);
+        jb->count[k] = row.n;
+        for (int64_t q = 0; q < row.n && q < jb->max_visits; ++q) {
+            const wseg *e = row.s + q;
+            jb->tet[k * jb->max_visits + q] = e->tet;
+            jb->len[k * jb->max_visits + q] = e->a;
+            if (jb->cond) {
+                jb->cond[(k * jb->max_visits + q) * 2] = e->wi * fmin(e->gi, 64.0) + e->wo * fmin(e->go, 64.0);
+                jb->cond[(k * jb->max_visits + q) * 2 + 1] = e->wi * e->gi + e->wo * e->go;
+            }
+        }
+    }
+    free(row.s);
+    return NULL;
+}
+
+/* Row j of A as the sequence of tets the ray visits (walk order; for rays not
+ * walked, status 1 or 2, the brute-force row sorted by entry parameter) with
+ * each a_ij, for explicit rays S, P [n][3].  out_count[k] is the full count
+ * (visits past max_visits are dropped).  out_cond (or NULL) [n][max_visits][2]:
+ * each visit's w_in / sin_in + w_out / sin_out (see oracle_walk), with 1 / sin
+ * capped at 64 and uncapped.  Returns 0 or -1 (no memory). */
+int oracle_walk_trace(void *h, const double *S, const double *P, int64_t n, int64_t max_visits,
+                      int32_t *out_tet, double *out_len, double *out_cond, int64_t *out_count,
+                      int8_t *status, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n && n > 0) nthreads = (int)n;
+    tjob *jobs = (tjob *)calloc((size_t)nthreads, sizeof(tjob));
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    int rc = (!jobs || !th) ? -1 : 0;
+    if (!rc) {
+        for (int i = 0; i < nthreads; ++i) {
+            tjob *j = &jobs[i];
+            j->w = (const walker *)h; j->S = S; j->P = P; j->max_visits = max_visits;
+            j->tet = out_tet; j->len = out_len; j->cond = out_cond; j->count = out_count;
+            j->status = status;
+            split(n, nthreads, i, &j->begin, &j->end);
+            pthread_create(&th[i], NULL, trace_walk_worker, j);
+        }
+        for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+        for (int i = 0; i < nthreads; ++i) if (jobs[i].rc) rc = jobs[i].rc;
+    }
+    free(th);
+    free(jobs);
+    return rc;
+}

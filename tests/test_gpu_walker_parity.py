@@ -237,3 +237,55 @@ def test_config5_all_problems_batched_walker_sampled(tp):
                         float(np.abs(w.verts).max()), float(yv.max()))
         del wk
     b.close()
+
+
+def _visit_workload(name):
+    if name == "C2":
+        return W.config2()
+    if name == "C3":
+        return W.config3(n_adversarial=0)
+    if name == "C4":
+        return W.config4()
+    k = int(name[3:])  # "C5#k"
+    n, N, na = W.config5_specs()[k]
+    return W.config5_problem(k, n, N, na, channels=4)
+
+
+@pytest.mark.parametrize("name", ["C2", "C3", "C4", "C5#12", "C5#0"])
+def test_visit_sequences_full_size(tp, name):
+    """Identical tet-visit sequences on 10^4 sampled rays of each full-size
+    configuration (the walker's non-degenerate rays: no two candidate
+    crossings within 1e-9), in both precisions, with each visit's chord within
+    32 e K of the oracle's (K the visit's two crossings' (L + R) / sin)."""
+    import torch
+    w = _visit_workload(name)
+    mesh = tp.Mesh(w.verts, w.tets)
+    idx, _ = sample(w.geom.nrays, 900 + len(name), n=10_000)
+    S, P = oracle.cone_rays(w.geom, idx)
+    wk = oracle.Walker(w.verts, w.tets)
+    mv = 1024
+    tet, ln, cnt, st = wk.trace_rays(S, P, max_visits=mv)
+    cond = wk.last_cond
+    sel = np.nonzero((st == 0) & (cnt > 0) & (cnt <= mv))[0]
+    assert sel.size > 0.5 * np.count_nonzero(cnt)
+    src = torch.tensor(S[sel], device="cuda")
+    dst = torch.tensor(P[sel], device="cuda")
+    for prec in ("f32", "f64"):
+        gt, gl, gc = tp.trace_rays(mesh, src, dst, max_visits=mv,
+                                   precision=tp.FILTERED if prec == "f32" else tp.PLAIN_FP64)
+        torch.cuda.synchronize()
+        gt, gl, gc = gt.cpu().numpy(), gl.cpu().numpy(), gc.cpu().numpy()
+        assert np.array_equal(gc, cnt[sel]), (name, prec)
+        worst = 0.0
+        nvis = 0
+        for r, k in enumerate(sel):
+            n = cnt[k]
+            assert np.array_equal(gt[r, :n], tet[k, :n]), (name, prec, k)
+            err = np.abs(gl[r, :n] - ln[k, :n])
+            bound = cond_term(prec, cond[k, :n])
+            assert np.all(err <= np.maximum(bound, 1e-300)), (name, prec, k, (err / bound).max())
+            worst = max(worst, float((err / bound).max()))
+            nvis += n
+        print(f"{name} visit sequences {prec}: {sel.size} rays, {nvis} visits identical; "
+              f"largest chord error / 32 e K {worst:.3f}")
+    assert mesh.stats()["error"] == 0

@@ -199,6 +199,9 @@ def test_crossing_conditioning_by_hand():
         assert abs(wk.last_kf[0, 0, 1] - 1.5 * (3.0 + 3.7 * np.sqrt(3.0))) < 1e-13
         assert abs(wk.last_kb[0, 0, 0] - 2.0 * want) < 1e-13
         assert abs(bwd[0, 0] - 2.0 * 0.7) < 1e-15
+    tet, ln, cnt, st = wk.trace_rays(S, P, max_visits=4)
+    assert cnt[0] == 1 and tet[0, 0] == 0 and abs(ln[0, 0] - 0.7) < 1e-15
+    assert abs(wk.last_cond[0, 0, 1] - (3.0 + 3.7 * np.sqrt(3.0))) < 1e-13
 
 
 def test_crossing_conditioning_constant_mu(meshes):
@@ -234,3 +237,22 @@ def test_crossing_conditioning_constant_mu(meshes):
     keep = st == 0
     assert keep.mean() > 0.95
     assert np.all(np.abs(K[keep] - want[keep]) <= 1e-9 * want[keep])
+
+
+@pytest.mark.parametrize("name", ["jittered", "cubic"])
+def test_trace_equals_brute_force_trace(meshes, name):
+    """Visit sequences: the walker's order and a_ij equal the brute-force
+    trace (all tets clipped, sorted by entry parameter) on walked rays."""
+    w = meshes[name]
+    idx = np.sort(np.random.default_rng(8).choice(w.geom.nrays, 1500, replace=False))
+    S, P = oracle.cone_rays(w.geom, idx)
+    tet, ln, cnt, st = oracle.Walker(w.verts, w.tets).trace_rays(S, P, max_visits=256)
+    bt, blo, bhi, bcnt = oracle.trace_rays(w.verts, w.tets, S, P, max_visits=256)[:4]
+    assert np.array_equal(cnt, bcnt)
+    dl = np.linalg.norm(P - S, axis=1)
+    walked = np.nonzero(st == 0)[0]
+    assert walked.size > 0.9 * idx.size
+    for k in walked:
+        n = cnt[k]
+        assert np.array_equal(tet[k, :n], bt[k, :n]), k
+        assert np.array_equal(ln[k, :n], (bhi[k, :n] - blo[k, :n]) * dl[k])
