@@ -289,3 +289,36 @@ def test_visit_sequences_full_size(tp, name):
         print(f"{name} visit sequences {prec}: {sel.size} rays, {nvis} visits identical; "
               f"largest chord error / 32 e K {worst:.3f}")
     assert mesh.stats()["error"] == 0
+
+
+def test_config3_adversarial_rays_walker_sampled(tp):
+    """10^4 of config 3's adversarial rays (aimed exactly at vertices, edge
+    midpoints and face points of the cubic-mapped mesh; 3,334 / 3,333 / 3,333
+    per kind), both precisions, against the oracle (their walks meet ties, so
+    most rows come from the clipper through the walker's fallback); rays
+    inside a face plane are left out (exact references in test_gpu_fullsize)."""
+    import torch
+    w = W.config3()
+    mesh = tp.Mesh(w.verts, w.tets)
+    AS, AT, kind = w.extra["adv_src"], w.extra["adv_target"], w.extra["adv_kind"]
+    rng = np.random.default_rng(950)
+    sel = np.concatenate([rng.choice(np.nonzero(kind == k)[0], 3334 - (k > 0), replace=False)
+                          for k in range(3)])
+    S, P = AS[sel], AT[sel]
+    wk = oracle.Walker(w.verts, w.tets)
+    mu = np.asarray(w.mu)  # U[0, 1]: sum a|mu| is the value itself
+    want, _, st = wk._run(mu, None, None, None, S, P, None)
+    want = want[:, 0]
+    K = wk.last_kf
+    planar = st == 2
+    print(f"C3 adversarial: walker status counts {np.bincount(st, minlength=3)}")
+    src = torch.tensor(S, device="cuda")
+    dst = torch.tensor(P, device="cuda")
+    for prec in ("f32", "f64"):
+        o = tp.make_options(precision=tp.FILTERED if prec == "f32" else tp.PLAIN_FP64)
+        got = tp.forward_rays(mesh, src, dst, torch.tensor(mu, dtype=_dt(prec), device="cuda"),
+                              options=o)
+        torch.cuda.synchronize()
+        check_cond(f"C3 adversarial forward {prec} ({int(planar.sum())} in-plane left out)",
+                   got.double().cpu().numpy(), want, want, K, prec, skip=planar)
+    assert mesh.stats()["error"] == 0
