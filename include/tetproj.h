@@ -177,7 +177,7 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *mesh, tetproj_mesh_info
  * the first compute call: operand/accumulator buffers and the deferral queue,
  * for the filtered path also the FP64 accumulator its backprojection uses by
  * default at C = 1 (and at C = 4 when nt * 4 <= 2^20).  Calls of more than
- * 2^23 rays add a second queue and a stream on first use to overlap their
+ * 2^24 rays add a second queue and a stream on first use to overlap their
  * chunks; under CUDA-graph capture they run without them rather than
  * allocate.  Synchronous. */
 tetproj_status tetproj_mesh_reserve(tetproj_mesh *mesh, int32_t precision, int32_t channels);
@@ -298,7 +298,7 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
  * it.  Backprojections add into FP64 accumulators at C = 1 (with each problem's
  * atomic or warp-aggregated scatter) and into FP32 ones at C = 4, two-level
  * for dense problems (as TETPROJ_FLAG_ACC32 describes; merged after every
- * round).  Rays are processed in rounds of at most 2^23 rays; backprojection
+ * round).  Rays are processed in rounds of at most 2^25 rays; backprojection
  * rounds are cut further inside dense problems (at most max(2^18,
  * 8192 nt / s) of their rays per round, as above).
  * Errors: TETPROJ_ERR_ARG (null handle, n < 1, bad channels or tiles),

@@ -88,7 +88,13 @@ struct tetproj_mesh {
 };
 
 // Largest deferral queue (entries of 64 B); launches over more rays are chunked.
-static const int64_t kQueueMax = int64_t(1) << 23;
+// Single-problem calls: 2^24 rays per chunk (queue and fix list 1.25 GB; two
+// of them when a call has several chunks); on the 94M-ray jittered 96^3 step
+// 1% faster than 2^23 (272.7 vs 275.5 ms), 2^22 was 2% slower.  A batch holds
+// one queue pair for all its problems and runs rounds of 2^25 rays (2.5 GB
+// each): on 24 config-5 problems 2,606 ms per step against 2,722 at 2^23.
+static const int64_t kQueueMax = int64_t(1) << 24;
+static const int64_t kBatchQueueMax = int64_t(1) << 25;
 
 static std::atomic<uint64_t> g_geometry_uid{1};
 
@@ -1318,7 +1324,7 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
         if (e != cudaSuccess) { batch_free(b); return cuda_status(e); }
     }
     if (b->item_begin.back() >= (int64_t(1) << 40)) { batch_free(b); return TETPROJ_ERR_TOO_LARGE; }
-    int64_t need = total_rays < kQueueMax ? total_rays : kQueueMax;
+    int64_t need = total_rays < kBatchQueueMax ? total_rays : kBatchQueueMax;
     need = ((need + 4095) / 4096) * 4096;
     cudaError_t e = cudaMalloc((void **)&b->q, (size_t)queue_bytes(need));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->q_count, kQueueCountBytes);
@@ -1330,7 +1336,7 @@ extern "C" tetproj_status tetproj_batch_create(const tetproj_mesh *const *meshes
         e = cudaMemcpy(b->d_item_begin, b->item_begin.data(), sizeof(int64_t) * (n + 1),
                        cudaMemcpyHostToDevice);
     // several rounds: round r's resume overlaps round r + 1's walk
-    if (e == cudaSuccess && total_rays > kQueueMax) {
+    if (e == cudaSuccess && total_rays > kBatchQueueMax) {
         e = overlap_create(b->ov, need);
         b->ov_ready = e == cudaSuccess;
     }

@@ -165,17 +165,17 @@ def test_batch_graph_capture_replay(tp, probs):
 
 
 def test_batch_several_rounds_and_shared_mesh(tp):
-    """One problem of 512 x 512 x 34 rays (> 2^23, two rounds of the deferral
-    queue) and a second problem on the same mesh, one channel."""
+    """One problem of 512 x 512 x 136 rays (> 2^25, two rounds of the batch's
+    deferral queue) and a second problem on the same mesh, one channel."""
     import torch
     n = 6
     verts, tets = W.kuhn_cube(n)
     verts = W.jitter_interior(verts, tets, n, W.rng_for(4, 900))
     mu = W.rng_for(4, 901).uniform(0, 1, tets.shape[0])
     mesh = tp.Mesh(verts, tets)
-    g_big = W.ConeBeam(4.0, 8.0, 512, 512, 6.4 / 512, 6.4 / 512, W.uniform_angles(34))
+    g_big = W.ConeBeam(4.0, 8.0, 512, 512, 6.4 / 512, 6.4 / 512, W.uniform_angles(136))
     g_small = W.ConeBeam(4.0, 8.0, 24, 20, 0.3, 0.3, W.uniform_angles(5))
-    assert g_big.nrays > 2 ** 23
+    assert g_big.nrays > 2 ** 25
     geos = [tp.Geometry.from_cone(g_big), tp.Geometry.from_cone(g_small)]
     tiles = [(16, 8, tp.ORDER_MORTON, tp.SCATTER_ATOMIC), (8, 16, tp.ORDER_ROW, tp.SCATTER_WARP)]
     mesh.stats_reset()
@@ -209,7 +209,7 @@ def test_batch_several_rounds_and_shared_mesh(tp):
 
 def test_batch_dense_two_level_accumulation(tp):
     """A dense 4-channel problem (1296 tets, 512 x 512 x 34 rays: ~10^5
-    segments per tet, two rounds of the queue) through the batched launch and
+    segments per tet; backprojection rounds cut inside the dense problem) through the batched launch and
     a single call: both backprojections use two-level accumulation (FP32
     reductions merged into FP64 after every round / chunk) and meet the FP32
     target on sampled tets against the oracle's FP64 sums."""

@@ -441,7 +441,7 @@ def test_backward_fp64_accumulator_c1(tp, c1, C):
 
 
 def test_single_calls_graph_capture_after_reserve(tp):
-    """A forward projection and a backprojection of a two-chunk scan (> 2^23
+    """A forward projection and a backprojection of a two-chunk scan (> 2^24
     rays) captured in one CUDA graph on a mesh that only had
     tetproj_mesh_reserve: nothing is allocated under capture (the chunks run
     without the overlap stream), and the replay equals eager calls."""
@@ -452,8 +452,8 @@ def test_single_calls_graph_capture_after_reserve(tp):
     mu_np = W.rng_for(4, 901).uniform(0, 1, tets.shape[0])
     mesh = tp.Mesh(verts, tets)
     mesh.reserve(tp.FILTERED, 1)
-    g = W.ConeBeam(4.0, 8.0, 512, 512, 6.4 / 512, 6.4 / 512, W.uniform_angles(34))
-    assert g.nrays > 2 ** 23
+    g = W.ConeBeam(4.0, 8.0, 512, 512, 6.4 / 512, 6.4 / 512, W.uniform_angles(68))
+    assert g.nrays > 2 ** 24
     geo = tp.Geometry.from_cone(g)
     mu = torch.tensor(mu_np, dtype=torch.float32, device="cuda")
     proj = torch.empty(geo.shape, dtype=torch.float32, device="cuda")

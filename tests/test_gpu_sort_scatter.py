@@ -75,13 +75,13 @@ def test_sort_is_bit_reproducible_and_plan_reused(tp, c1):
 
 
 def test_sort_several_chunks(tp):
-    """512 x 512 x 34 rays (> 2^23: two chunks) through a jittered Kuhn 6^3 mesh."""
+    """512 x 512 x 68 rays (> 2^24: two chunks) through a jittered Kuhn 6^3 mesh."""
     import torch
     n = 6
     verts, tets = W.kuhn_cube(n)
     verts = W.jitter_interior(verts, tets, n, W.rng_for(4, 900))
     mesh = tp.Mesh(verts, tets)
-    g = W.ConeBeam(4.0, 8.0, 512, 512, 6.4 / 512, 6.4 / 512, W.uniform_angles(34))
+    g = W.ConeBeam(4.0, 8.0, 512, 512, 6.4 / 512, 6.4 / 512, W.uniform_angles(68))
     geo = tp.Geometry.from_cone(g)
     gen = torch.Generator(device="cuda").manual_seed(11)
     y = torch.rand(geo.shape + (4,), device="cuda", generator=gen)
