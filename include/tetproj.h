@@ -176,9 +176,10 @@ tetproj_status tetproj_mesh_get_info(const tetproj_mesh *mesh, tetproj_mesh_info
 /* Allocates the mesh's workspace for (precision, channels) now instead of on
  * the first compute call: operand/accumulator buffers and the deferral queue,
  * for the filtered path also the FP64 accumulator its backprojection uses by
- * default at C = 1 (and at C = 4 when nt * 4 <= 2^20).  Calls of more than
- * 2^24 rays add a second queue and a stream on first use to overlap their
- * chunks; under CUDA-graph capture they run without them rather than
+ * default at C = 1 (and at C = 4 when nt * 4 <= 2^20).  The queue holds one
+ * launch chunk, min(rays, 2^24), at 80 B per ray (1.25 GB at 2^24).  Calls of
+ * more than 2^24 rays add a second queue and a stream on first use to overlap
+ * their chunks; under CUDA-graph capture they run without them rather than
  * allocate.  Synchronous. */
 tetproj_status tetproj_mesh_reserve(tetproj_mesh *mesh, int32_t precision, int32_t channels);
 
@@ -293,8 +294,10 @@ tetproj_status tetproj_trace_rays(const tetproj_mesh *mesh, const double *src, c
  *          for the defaults; each as in the options struct (powers of two,
  *          32..256 rays per tile); problems may use different tiles;
  *   channels: C = 1 or 4 for every problem.
- * The batch owns per-problem workspace and one deferral queue (allocated
- * here); it keeps pointers into the meshes and geometries, which must outlive
+ * The batch owns per-problem workspace and one deferral queue of
+ * min(total rays, 2^25) entries at 80 B (2.5 GB at 2^25; a second one when
+ * there are several rounds), allocated here; it keeps pointers into the
+ * meshes and geometries, which must outlive
  * it.  Backprojections add into FP64 accumulators at C = 1 (with each problem's
  * atomic or warp-aggregated scatter) and into FP32 ones at C = 4, two-level
  * for dense problems (as TETPROJ_FLAG_ACC32 describes; merged after every
