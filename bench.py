@@ -22,8 +22,9 @@ batch24 / batch6s (the batched workload alone), c5pK (problem K of the
 batched workload alone, one channel), kuhn24 / kuhn64 / kuhn64s / kuhn96s
 (smaller copies for profiling).
 
---impl reference times the CPU oracle (brute-force FP64 clipping) on a bounded
-sample of the same rays, on the host cores.
+--impl reference times the CPU oracle on a bounded sample of the same rays, on
+the host cores: the oracle walker by default (FP64 clipping of the tets each
+ray crosses), the brute-force clipper with --cpu-oracle clipper.
 """
 from __future__ import annotations
 
@@ -201,21 +202,43 @@ def l2_note(nt, nrays, C):
             f"projections {proj / 1e6:.0f} MB)")
 
 
-def cpu_baseline(w, nsample, threads=None):
+CPU_SAMPLE = {"walker": 20000, "clipper": 256}
+
+
+def cpu_baseline(w, nsample, threads=None, kind="walker"):
     """The oracle as it stands, on `nsample` rays spread over the workload:
     forward (b_j for the sampled rays) and backward (A^T y restricted to
-    those rays); returns fwd+back ray pairs per second."""
+    those rays); returns fwd+back ray pairs per second.  kind "walker": the
+    oracle walker (each a_ij from the clipper, only for the tets the ray
+    crosses, found over the oracle's own adjacency; rays with near-ties over
+    all tets), its adjacency built outside the timed region; "clipper": the
+    brute-force clipper (every ray against every tet)."""
     import oracle
     rng = np.random.default_rng(12345)
     idx = np.sort(rng.choice(w.geom.nrays, nsample, replace=False))
-    S, P = oracle.cone_rays(w.geom, idx)
     y = rng.uniform(size=nsample)
     threads = threads or oracle.default_threads()
-    t0 = time.perf_counter()
-    oracle.forward_rays(w.verts, w.tets, w.mu, S, P, threads=threads)
-    oracle.backward_rays(w.verts, w.tets, y, S, P, threads=threads)
-    dt = time.perf_counter() - t0
+    mu = np.asarray(w.mu)
+    if kind == "walker":
+        wk = oracle.Walker(w.verts, w.tets)
+        t0 = time.perf_counter()
+        wk.forward_cone(mu, w.geom, idx, threads=threads)
+        wk.backward_cone(y, w.geom, idx, threads=threads)
+        dt = time.perf_counter() - t0
+    else:
+        S, P = oracle.cone_rays(w.geom, idx)
+        t0 = time.perf_counter()
+        oracle.forward_rays(w.verts, w.tets, mu, S, P, threads=threads)
+        oracle.backward_rays(w.verts, w.tets, y, S, P, threads=threads)
+        dt = time.perf_counter() - t0
     return nsample / dt, threads, dt, idx.size
+
+
+def cpu_sample_text(kind, n, nrays):
+    if kind == "walker":
+        return (f"{n} of {nrays} rays per step (fwd + back), oracle walker: FP64 clipping of the "
+                f"tets each ray crosses, found over the oracle's own adjacency")
+    return f"{n} of {nrays} rays per step (fwd + back), brute-force FP64 clipping over all tets"
 
 
 def run_reference(args, rank, world):
@@ -224,12 +247,13 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     w = build_workload(args)
-    n = args.cpu_sample
+    kind = args.cpu_oracle
+    n = args.cpu_sample or CPU_SAMPLE[kind]
     for _ in range(args.warmup):
-        cpu_baseline(w, max(8, n // 16))
+        cpu_baseline(w, max(8, n // 16), kind=kind)
     times = []
     for _ in range(args.steps):
-        v, cores, dt, ns = cpu_baseline(w, n)
+        v, cores, dt, ns = cpu_baseline(w, n, kind=kind)
         times.append(dt)
     value = n / float(np.mean(times))
     line = {
@@ -240,7 +264,7 @@ def run_reference(args, rank, world):
         "config": {"workload": w.name, "nt": int(w.tets.shape[0]),
                    "rays_per_step": n, "note": "bounded ray sample of the same workload"},
         "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{n} of {w.geom.nrays} rays per step (fwd + back), brute-force FP64 clipping over all tets"},
+                         "sample": cpu_sample_text(kind, n, w.geom.nrays)},
         "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -452,20 +476,30 @@ def run_batch(args, tp, torch, dist, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         oracle.build()
-        per = max(1, args.cpu_sample // len(ws))
-        t0 = time.perf_counter()
+        kind = args.cpu_oracle
+        per = max(1, (args.cpu_sample or CPU_SAMPLE[kind]) // len(ws))
+        dt = 0.0
         n_cpu = 0
         for w in ws:
             rng = np.random.default_rng(777)
             idx = np.sort(rng.choice(w.geom.nrays, per, replace=False))
-            S, P = oracle.cone_rays(w.geom, idx)
-            oracle.forward_rays(w.verts, w.tets, w.mu, S, P)
-            oracle.backward_rays(w.verts, w.tets, rng.uniform(size=(per, C)), S, P)
+            yv = rng.uniform(size=(per, C))
+            if kind == "walker":
+                wk = oracle.Walker(w.verts, w.tets)  # adjacency built outside the timing
+                t0 = time.perf_counter()
+                wk.forward_cone(w.mu, w.geom, idx)
+                wk.backward_cone(yv, w.geom, idx)
+            else:
+                S, P = oracle.cone_rays(w.geom, idx)
+                t0 = time.perf_counter()
+                oracle.forward_rays(w.verts, w.tets, w.mu, S, P)
+                oracle.backward_rays(w.verts, w.tets, yv, S, P)
+            dt += time.perf_counter() - t0
             n_cpu += per
-        dt = time.perf_counter() - t0
+        how = ("oracle walker" if kind == "walker" else "brute-force FP64 clipping")
         cpu = {"value": n_cpu / dt, "unit": "rays/s", "cores": oracle.default_threads(),
                "kind": "oracle", "sample": f"{per} rays of each of {len(ws)} problems (fwd + back, "
-                                           f"4 channels), brute-force FP64 clipping, {dt:.1f} s"}
+                                           f"4 channels), {how}, {dt:.1f} s"}
     line = None
     if rank == 0:
         line = {
@@ -520,7 +554,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kuhn96")
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--cpu-sample", type=int, default=256)
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="rays of the CPU oracle sample (0: 20000 for the walker, 256 for the clipper)")
+    ap.add_argument("--cpu-oracle", default="walker", choices=["walker", "clipper"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="default workload: leave out the nested batched measurement")
@@ -798,9 +834,10 @@ def run_single(args, tp, torch, dist, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         oracle.build()
-        v, cores, dt, ns = cpu_baseline(w, args.cpu_sample)
+        kind = args.cpu_oracle
+        v, cores, dt, ns = cpu_baseline(w, args.cpu_sample or CPU_SAMPLE[kind], kind=kind)
         cpu = {"value": v, "unit": "rays/s", "cores": cores, "kind": "oracle",
-               "sample": f"{ns} of {nrays} rays (fwd + back), brute-force FP64 clipping, {dt:.1f} s"}
+               "sample": cpu_sample_text(kind, ns, nrays).replace(" per step", "") + f", {dt:.1f} s"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,

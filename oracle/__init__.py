@@ -364,7 +364,7 @@ class Walker:
             _lib.oracle_walker_destroy(h)
             self._h = None
 
-    def _run(self, mu, y, geom, ray_idx, S, P, threads, cap=64.0):
+    def _run(self, mu, y, geom, ray_idx, S, P, threads, cap=64.0, cond=True):
         if S is not None:
             s, sp = _d(S)
             p, pp = _d(P)
@@ -389,8 +389,8 @@ class Walker:
         fwd = np.empty((n, C)) if mu is not None else None
         bwd = np.empty((self.nt, C)) if y is not None else None
         cnt = np.empty(self.nt, dtype=np.int64) if y is not None else None
-        kf = np.empty((n, C, 2)) if mu is not None else None
-        kb = np.empty((self.nt, C, 2)) if y is not None else None
+        kf = np.empty((n, C, 2)) if (cond and mu is not None) else None
+        kb = np.empty((self.nt, C, 2)) if (cond and y is not None) else None
         status = np.empty(n, dtype=np.int8)
         ptr = lambda a, t=_c_dp: None if a is None else a.ctypes.data_as(t)
         _check(lib().oracle_walk(self._h, mp, yp, C, *g, angp, na, ip, sp, pp, n, ptr(fwd),
@@ -403,14 +403,14 @@ class Walker:
     def forward_cone(self, mu, geom, ray_idx=None, threads=None):
         """(b [n](,C), status [n]) for the selected cone rays (Eq. 2);
         status 0 walked, 1 brute force, 2 brute force, ray in a face plane."""
-        fwd, _, st = self._run(mu, None, geom, ray_idx, None, None, threads)
+        fwd, _, st = self._run(mu, None, geom, ray_idx, None, None, threads, cond=False)
         return (fwd[:, 0] if np.asarray(mu).ndim == 1 else fwd), st
 
     def backward_cone(self, y, geom, ray_idx, threads=None):
         """(x [nt](,C), status): x_i = sum_k a_i,ray_idx[k] y[k] (Eq. 3 over
         the selected cone rays only).  ``last_count`` then holds, per tet, how
         many of these rays cross it."""
-        _, bwd, st = self._run(None, y, geom, ray_idx, None, None, threads)
+        _, bwd, st = self._run(None, y, geom, ray_idx, None, None, threads, cond=False)
         return (bwd[:, 0] if np.asarray(y).ndim == 1 else bwd), st
 
     def rows_cone(self, mu, y, geom, ray_idx, threads=None, cap=64.0):
@@ -447,11 +447,11 @@ class Walker:
         return tet, ln, cnt, st
 
     def forward_rays(self, mu, S, P, threads=None):
-        fwd, _, st = self._run(mu, None, None, None, S, P, threads)
+        fwd, _, st = self._run(mu, None, None, None, S, P, threads, cond=False)
         return (fwd[:, 0] if np.asarray(mu).ndim == 1 else fwd), st
 
     def backward_rays(self, y, S, P, threads=None):
-        _, bwd, st = self._run(None, y, None, None, S, P, threads)
+        _, bwd, st = self._run(None, y, None, None, S, P, threads, cond=False)
         return (bwd[:, 0] if np.asarray(y).ndim == 1 else bwd), st
 
 

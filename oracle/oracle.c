@@ -576,6 +576,7 @@ typedef struct {
     double *bbox;   /* [nb][6]: their boxes, min xyz then max xyz */
     double box[6];  /* the mesh's box */
     double radius;  /* the largest |coordinate| */
+    double *tbox;   /* [nt][6]: every tet's box, for the brute-force rows */
 } walker;
 
 typedef struct { int32_t b, c, code; } face_rec; /* code = tet * 4 + k */
@@ -586,6 +587,7 @@ void oracle_walker_destroy(void *h) {
     free(w->adj);
     free(w->btet);
     free(w->bbox);
+    free(w->tbox);
     free(w);
 }
 
@@ -664,6 +666,19 @@ void *oracle_walker_create(const double *verts, int64_t nv, const int32_t *tets,
     for (int64_t i = 0; i < nt; ++i)
         if (w->adj[4 * i] < 0 || w->adj[4 * i + 1] < 0 || w->adj[4 * i + 2] < 0 || w->adj[4 * i + 3] < 0) ++nb;
     w->nb = nb;
+    w->tbox = (double *)malloc(sizeof(double) * 6 * (size_t)(nt > 0 ? nt : 1));
+    if (!w->tbox) { *status = -1; oracle_walker_destroy(w); return NULL; }
+    for (int64_t i = 0; i < nt; ++i) {
+        double *bx = w->tbox + 6 * i;
+        for (int q = 0; q < 3; ++q) { bx[q] = INFINITY; bx[3 + q] = -INFINITY; }
+        for (int k = 0; k < 4; ++k) {
+            const double *p = verts + 3 * (int64_t)tets[4 * i + k];
+            for (int q = 0; q < 3; ++q) {
+                if (p[q] < bx[q]) bx[q] = p[q];
+                if (p[q] > bx[3 + q]) bx[3 + q] = p[q];
+            }
+        }
+    }
     w->btet = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
     w->bbox = (double *)malloc(sizeof(double) * 6 * (size_t)(nb > 0 ? nb : 1));
     if (!w->btet || !w->bbox) { *status = -1; oracle_walker_destroy(w); return NULL; }
@@ -747,11 +762,18 @@ static int wpush(wbuf *b, int32_t tet, double a, double lo, double hi) {
     return 0;
 }
 
-/* Row j of A by brute force over all tets; 2 if some face plane contains the ray. */
+static int ray_meets_box(const double *bx, const double S[3], const double d[3], double pad);
+
+/* Row j of A by brute force over the tets whose boxes (grown by pad) the
+ * half-line meets -- a tet it crosses, or touches, lies in its box, so this
+ * is every tet with a_ij > 0; 2 if a face plane of one of them contains the
+ * ray (the closed-tet measure then counts both sides of that plane). */
 static int walk_brute(const walker *w, const double S[3], const double d[3], double len, wbuf *out) {
     int planar_any = 0;
+    const double pad = 1e-9 * (1.0 + fabs(S[0]) + fabs(S[1]) + fabs(S[2]) + len);
     out->n = 0;
     for (int64_t i = 0; i < w->nt; ++i) {
+        if (!ray_meets_box(w->tbox + 6 * i, S, d, pad)) continue;
         double v[4][3], lo, hi;
         int planar;
         load_tet(w->verts, w->tets, i, v);
@@ -876,6 +898,7 @@ typedef struct {
     const double *mu, *y;
     int C;
     double cap;
+    int want_cond;  /* fill the rows' crossing data (for out_kf / out_kb) */
     int64_t begin, end;
     double *out;    /* forward: [n][C] */
     double *kf;     /* forward conditioning: [n][C][2] */
@@ -900,7 +923,7 @@ static void *walk_worker(void *arg) {
         if (st < 0) { jb->rc = -1; break; }
         jb->status[k] = (int8_t)st;
         sub3(P, S, d);
-        row_cond(jb->w, S, d, sqrt(dot3(d, d)), &row, st == 0);
+        if (jb->want_cond) row_cond(jb->w, S, d, sqrt(dot3(d, d)), &row, st == 0);
         const int C = jb->C;
         if (jb->mu) {
             nsum acc[16];
@@ -980,6 +1003,7 @@ int oracle_walk(void *h, const double *mu, const double *y, int C, double dso, d
         wjob *j = &jobs[i];
         j->w = w; j->geom = S ? NULL : &g; j->ray_idx = ray_idx; j->S = S; j->P = P;
         j->mu = mu; j->y = y; j->C = C; j->cap = cap; j->out = out_fwd; j->kf = out_kf;
+        j->want_cond = out_kf != NULL || out_kb != NULL;
         j->status = status;
         split(n, nthreads, i, &j->begin, &j->end);
         if (y) {
