@@ -1316,8 +1316,10 @@ __global__ void __launch_bounds__(128) k_entry_raster(const MeshView m, const Ge
     const float ulo = fminf(fminf(px[0], px[1]), px[2]) - eps, uhi = fmaxf(fmaxf(px[0], px[1]), px[2]) + eps;
     const float vlo = fminf(fminf(py[0], py[1]), py[2]) - eps, vhi = fmaxf(fmaxf(py[0], py[1]), py[2]) + eps;
     if (!(uhi >= 0.f && vhi >= 0.f && ulo <= (float)(g.nu - 1) && vlo <= (float)(g.nv - 1))) return;
-    const int iu0 = max(0, (int)ceilf(ulo)), iu1 = min(g.nu - 1, (int)floorf(uhi));
-    const int iv0 = max(0, (int)ceilf(vlo)), iv1 = min(g.nv - 1, (int)floorf(vhi));
+    // clamped to the detector before the conversion (a vertex near the
+    // source's plane projects arbitrarily far)
+    const int iu0 = (int)ceilf(fmaxf(ulo, 0.f)), iu1 = (int)floorf(fminf(uhi, (float)(g.nu - 1)));
+    const int iv0 = (int)ceilf(fmaxf(vlo, 0.f)), iv1 = (int)floorf(fminf(vhi, (float)(g.nv - 1)));
     const float area = (px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]);
     const float sg = area >= 0.f ? 1.f : -1.f;
     float ex[3], ey[3], el[3];
