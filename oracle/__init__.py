@@ -6,9 +6,12 @@ product library never loads it, and it shares no code with the CUDA path.
 
 ``oracle.c`` evaluates the paper's plain definition (Eq. 1-3): every chord
 a_ij = |half-line j  intersected with closed tet i| is computed by brute-force
-clipping of every ray against every tet, in FP64.  ``exact.py`` holds exact
-rational predicates (orientation, the symbolic tie-break) used to pin the
-predicate cascade of the CUDA path.
+clipping of every ray against every tet, in FP64.  Its walker (``Walker``)
+gives the same a_ij, each from the same clipping code, for the tets a ray
+passes through, found over adjacency the oracle builds itself (rays with
+near-ties get the brute-force row), so that large samples are affordable.
+``exact.py`` holds exact rational predicates (orientation, the symbolic
+tie-break) used to pin the predicate cascade of the CUDA path.
 """
 from __future__ import annotations
 
@@ -445,6 +448,10 @@ class Walker:
                                        st.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
                                        threads or default_threads()), "oracle_walk_trace")
         return tet, ln, cnt, st
+
+    def rows_rays(self, mu, y, S, P, threads=None, cap=64.0):
+        """``rows_cone`` for explicit rays S, P [n, 3]."""
+        return self._run(mu, y, None, None, S, P, threads, cap)
 
     def forward_rays(self, mu, S, P, threads=None):
         fwd, _, st = self._run(mu, None, None, None, S, P, threads, cond=False)

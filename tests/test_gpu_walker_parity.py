@@ -307,7 +307,7 @@ def test_config3_adversarial_rays_walker_sampled(tp):
     S, P = AS[sel], AT[sel]
     wk = oracle.Walker(w.verts, w.tets)
     mu = np.asarray(w.mu)  # U[0, 1]: sum a|mu| is the value itself
-    want, _, st = wk._run(mu, None, None, None, S, P, None)
+    want, _, st = wk.rows_rays(mu, None, S, P)
     want = want[:, 0]
     K = wk.last_kf
     planar = st == 2

@@ -192,7 +192,7 @@ def test_crossing_conditioning_by_hand():
     P = S + np.array([[4.0, 0, 0]])
     wk = oracle.Walker(verts, tets)
     for cap, g_out in ((64.0, np.sqrt(3.0)), (1.0, 1.0)):
-        fwd, bwd, st = wk._run(np.array([-1.5]), np.array([2.0]), None, None, S, P, 1, cap)
+        fwd, bwd, st = wk.rows_rays(np.array([-1.5]), np.array([2.0]), S, P, threads=1, cap=cap)
         assert st[0] == 0 and abs(fwd[0, 0] - (-1.5 * 0.7)) < 1e-15
         want = 3.0 + 3.7 * g_out
         assert abs(wk.last_kf[0, 0, 0] - 1.5 * want) < 1e-13
@@ -216,7 +216,7 @@ def test_crossing_conditioning_constant_mu(meshes):
     dn = np.linalg.norm(d, axis=1)
     chord = cube_chord(S, P)
     ok = chord > 1e-3
-    _, _, st = wk._run(np.ones(w.tets.shape[0]), None, None, None, S[ok], P[ok], None, 64.0)
+    _, _, st = wk.rows_rays(np.ones(w.tets.shape[0]), None, S[ok], P[ok])
     K = wk.last_kf[:, 0, 1]
     t_in = np.full(S.shape[0], -np.inf)
     t_out = np.full(S.shape[0], np.inf)
