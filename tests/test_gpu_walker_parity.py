@@ -147,29 +147,29 @@ class Single:
         self.planar = self.status == 2
         print(f"{w.name}: walker status counts {np.bincount(self.status, minlength=3)}")
 
-    def run(self, tp, prec, options=None):
+    def run(self, tp, prec, options=None, backward=None):
         import torch
         dt = _dt(prec)
         mu = torch.tensor(np.asarray(self.w.mu), dtype=dt, device="cuda")
         self.mesh.stats_reset()
         proj = tp.forward(self.mesh, self.geo, mu, options=options)
         y = scatter_sample(self.geo.shape, self.C, self.idx, self.yv, dt)
-        back = tp.backward(self.mesh, self.geo, y, options=options)
+        back = (backward or tp.backward)(self.mesh, self.geo, y, options=options)
         torch.cuda.synchronize()
         assert self.mesh.stats()["error"] == 0
         got = proj.reshape(-1, self.C)[torch.tensor(self.idx, device="cuda")].double().cpu().numpy()
         return got, back.double().cpu().numpy()
 
-    def check(self, tp, prec, options=None):
-        got, back = self.run(tp, prec, options)
+    def check(self, tp, prec, options=None, backward=None, label=""):
+        got, back = self.run(tp, prec, options, backward)
         w = self.w
         R = float(np.abs(w.verts).max())
-        check_cond(f"{w.name} forward {prec} (10^5 rays, {int(self.planar.sum())} in-plane left out)",
+        check_cond(f"{w.name}{label} forward {prec} (10^5 rays, {int(self.planar.sum())} in-plane left out)",
                    got, self.want, self.scale, self.kf, prec, skip=self.planar)
         hit = self.cnt > 0
-        check_cond(f"{w.name} backward {prec} ({int(hit.sum())} tets crossed)", back[hit],
+        check_cond(f"{w.name}{label} backward {prec} ({int(hit.sum())} tets crossed)", back[hit],
                    self.wantb[hit], self.wantb[hit], self.kb[hit], prec)
-        check_uncrossed(f"{w.name} backward {prec}", back, self.cnt, prec, R, float(self.yv.max()))
+        check_uncrossed(f"{w.name}{label} backward {prec}", back, self.cnt, prec, R, float(self.yv.max()))
 
 
 @pytest.fixture(scope="module")
@@ -190,6 +190,32 @@ def test_config2_walker_sampled(tp, c2, prec):
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_config4_walker_sampled(tp, c4, prec):
     c4.check(tp, prec)
+
+
+@pytest.mark.parametrize("scatter", ["warp", "sort"])
+def test_config2_scatter_variants_walker_sampled(tp, c2, scatter):
+    """The two other backprojection scatters on the bench workload (FP32):
+    warp-aggregated reductions into the FP64 accumulator, and the
+    deterministic segment sort-and-reduce."""
+    sc = tp.SCATTER_WARP if scatter == "warp" else tp.SCATTER_SORT
+    c2.check(tp, "f32", tp.make_options(scatter=sc), label=f" ({scatter} scatter)")
+
+
+def test_config4_backward_noalloc_walker_sampled(tp, c4):
+    """The allocation-free backprojection (fixed device scratch) on the
+    config-4 mesh (1.57M tets: within its 32 MB accumulator at C = 1)."""
+    c4.check(tp, "f32", backward=lambda m, g, y, options=None: tp.backward_noalloc(m, g, y),
+             label=" (noalloc backprojection)")
+
+
+@pytest.mark.parametrize("k", [12, 18])
+def test_config5_single_calls_fp32_walker_sampled(tp, k):
+    """Config-5 problems through single calls (filtered FP32, 4 channels):
+    #12, the largest mesh (118^3), and #18 (~10^5 segments per tet, two-level
+    accumulation)."""
+    n, N, na = W.config5_specs()[k]
+    s = Single(tp, W.config5_problem(k, n, N, na, channels=4), 720 + k)
+    s.check(tp, "f32", tp.make_options(channels=4))
 
 
 @pytest.mark.parametrize("k", [9, 5])
@@ -321,4 +347,21 @@ def test_config3_adversarial_rays_walker_sampled(tp):
         torch.cuda.synchronize()
         check_cond(f"C3 adversarial forward {prec} ({int(planar.sum())} in-plane left out)",
                    got.double().cpu().numpy(), want, want, K, prec, skip=planar)
+    # the explicit-ray backprojection of y >= 0 on these rays (0 on in-plane ones)
+    yv = rng.uniform(0.5, 1.5, size=sel.size).astype(np.float32).astype(np.float64)
+    yv[planar] = 0.0
+    _, wantb, _ = wk.rows_rays(None, yv, S, P)
+    wantb = wantb[:, 0]
+    cnt, Kb = wk.last_count, wk.last_kb
+    hit = cnt > 0
+    for prec in ("f32", "f64"):
+        o = tp.make_options(precision=tp.FILTERED if prec == "f32" else tp.PLAIN_FP64)
+        back = tp.backward_rays(mesh, src, dst, torch.tensor(yv, dtype=_dt(prec), device="cuda"),
+                                options=o)
+        torch.cuda.synchronize()
+        back = back.double().cpu().numpy()
+        check_cond(f"C3 adversarial backward {prec} ({int(hit.sum())} tets crossed)", back[hit],
+                   wantb[hit], wantb[hit], Kb[hit], prec)
+        check_uncrossed(f"C3 adversarial backward {prec}", back, cnt, prec,
+                        float(np.abs(w.verts).max()), 1.5)
     assert mesh.stats()["error"] == 0
