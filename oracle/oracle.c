@@ -779,7 +779,13 @@ static int walk_brute(const walker *w, const double S[3], const double d[3], dou
         load_tet(w->verts, w->tets, i, v);
         if (!tet_clip(v, S, d, NULL, &lo, &hi, &planar)) continue;
         if (planar) planar_any = 1;
-        if (hi > lo && wpush(out, (int32_t)i, (hi - lo) * len, lo, hi)) return -1;
+        /* tets the ray only touches (an edge or vertex: hi within WALK_TOL of
+         * lo) are listed with a_ij = 0: they add nothing to the sums, but a
+         * computed walk may visit them with a chord of the size of its
+         * rounding, and their crossings' conditioning bounds that */
+        if (hi > lo - WALK_TOL &&
+            wpush(out, (int32_t)i, hi > lo ? (hi - lo) * len : 0.0, lo, hi > lo ? hi : lo))
+            return -1;
     }
     return planar_any ? 2 : 1;
 }
@@ -973,6 +979,8 @@ static void *walk_worker(void *arg) {
  *   y  != NULL: out_bwd[i][c] = sum_k a_ik y[k][c]          (Eq. 3 over these
  *               rays only; y is indexed by k, not by the cone ray index), and,
  *               if out_count != NULL, out_count[i] = #{k : a_ik > 0}
+ * (rows of rays not walked also list the tets the ray only touches, with
+ * a_ik = 0: they count in the conditioning sums below, not in out_count)
  * Conditioning of the crossings (for error bounds: under rounding a crossing
  * moves along the ray by ~u (its distance from the source + the mesh radius)
  * / sin of the angle between ray and face plane), with 1 / sin capped at
@@ -1035,7 +1043,8 @@ int oracle_walk(void *h, const double *mu, const double *y, int C, double dso, d
         if (!rc && out_count) {
             memset(out_count, 0, sizeof(int64_t) * (size_t)w->nt);
             for (int i = 0; i < nthreads; ++i)
-                for (int64_t q = 0; q < jobs[i].rows.n; ++q) out_count[jobs[i].rows.s[q].tet]++;
+                for (int64_t q = 0; q < jobs[i].rows.n; ++q)
+                    if (jobs[i].rows.s[q].a > 0.0) out_count[jobs[i].rows.s[q].tet]++;
         }
         if (!rc && out_kb) {
             memset(out_kb, 0, sizeof(double) * (size_t)(2 * m));
@@ -1103,8 +1112,9 @@ static void *trace_walk_worker(void *arg) {
 }
 
 /* Row j of A as the sequence of tets the ray visits (walk order; for rays not
- * walked, status 1 or 2, the brute-force row sorted by entry parameter) with
- * each a_ij, for explicit rays S, P [n][3].  out_count[k] is the full count
+ * walked, status 1 or 2, the brute-force row sorted by entry parameter, which
+ * also lists the tets the ray only touches, with a_ij = 0) with each a_ij, for
+ * explicit rays S, P [n][3].  out_count[k] is the full count
  * (visits past max_visits are dropped).  out_cond (or NULL) [n][max_visits][2]:
  * each visit's w_in / sin_in + w_out / sin_out (see oracle_walk), with 1 / sin
  * capped at 64 and uncapped.  Returns 0 or -1 (no memory). */
