@@ -419,20 +419,21 @@ class Walker:
     def rows_cone(self, mu, y, geom, ray_idx, threads=None, cap=64.0):
         """Both at once (each row walked once): (b [n, C], x [nt, C], status).
         Also sets the crossings' conditioning (``oracle_walk`` in oracle.c):
-        ``last_kf`` [n, C, 2] per ray, sum of |mu jump| w / sin over its
+        ``last_kf`` [n, C, 2] per ray, sum of |mu jump| w kappa / sin over its
         crossings, and ``last_kb`` [nt, C, 2] per tet, sum over the rays
-        crossing it of |y| (w_in / sin_in + w_out / sin_out); [..., 0] with
-        1 / sin capped at ``cap``, [..., 1] uncapped; w = distance from the
-        source + mesh radius."""
+        crossing or touching it of |y| (w kappa / sin)_in + |y| (w kappa /
+        sin)_out; [..., 0] with 1 / sin capped at ``cap``, [..., 1] uncapped;
+        w = distance from the source + mesh radius, kappa = the crossed face's
+        shape factor (sum of squared edges / (2 |n|))."""
         return self._run(mu, y, geom, ray_idx, None, None, threads, cap)
 
     def trace_rays(self, S, P, max_visits=512, threads=None):
         """Visit sequences of explicit rays: (tet [n, max_visits] int32, a_ij
         [n, max_visits], count [n], status [n]); tets in walk order (rays not
         walked: the brute-force row sorted by entry parameter).  Sets
-        ``last_cond`` [n, max_visits, 2]: each visit's (L + R) / sin summed
-        over its two crossings (1 / sin capped at 64, uncapped), the scale of
-        its chord's rounding error (see ``rows_cone``)."""
+        ``last_cond`` [n, max_visits, 2]: each visit's (L + R) kappa / sin
+        summed over its two crossings (1 / sin capped at 64, uncapped), the
+        scale of its chord's rounding error (see ``rows_cone``)."""
         s, sp = _d(S)
         p, pp = _d(P)
         n = s.shape[0]

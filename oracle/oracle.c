@@ -709,10 +709,13 @@ void *oracle_walker_create(const double *verts, int64_t nv, const int32_t *tets,
 
 /* Outward face planes of tet v along the ray (the orientation rule of
  * tet_clip_range): den[k] = n_k.d, for den[k] != 0 tf[k] = the t at which the
- * ray meets face k's plane, and sn[k] = |n_k.d| / (|n_k| |d|), the sine of
- * the angle between the ray and that plane. */
+ * ray meets face k's plane, sn[k] = |n_k.d| / (|n_k| |d|), the sine of the
+ * angle between the ray and that plane, and, if kap != NULL, kap[k] = the sum
+ * of the face's squared edge lengths over 2 |n_k| (sqrt 3 for an equilateral
+ * face, ~1 / sin of the smallest angle for a sliver: the factor by which the
+ * rounding of the cross product n_k turns its direction). */
 static void tet_face_params(const double v[4][3], const double S[3], const double d[3],
-                            double tf[4], double den[4], double sn[4]) {
+                            double tf[4], double den[4], double sn[4], double *kap) {
     for (int k = 0; k < 4; ++k) {
         const double *q0 = v[(k + 1) & 3], *q1 = v[(k + 2) & 3], *q2 = v[(k + 3) & 3];
         double e1[3], e2[3], n[3], x[3], qs[3];
@@ -725,14 +728,20 @@ static void tet_face_params(const double v[4][3], const double S[3], const doubl
         den[k] = dot3(n, d);
         tf[k] = den[k] != 0.0 ? dot3(n, qs) / den[k] : 0.0;
         sn[k] = fabs(den[k]) / (sqrt(dot3(n, n)) * sqrt(dot3(d, d)));
+        if (kap) {
+            double e3[3];
+            sub3(q2, q1, e3);
+            kap[k] = (dot3(e1, e1) + dot3(e2, e2) + dot3(e3, e3)) / (2.0 * sqrt(dot3(n, n)));
+        }
     }
 }
 
 /* One entry of a row: tet, a_ij, its clipped interval, and for the crossings
  * where the ray enters (i) and leaves (o) it: the inverse sine of the angle
- * with the face plane (g) and the distance from the source plus the mesh
- * radius (w); gi = 0 when the interval starts at the source (t = 0). */
-typedef struct { int32_t tet; double a, lo, hi, gi, go, wi, wo; } wseg;
+ * with the face plane (g), the face's shape factor (c, see tet_face_params)
+ * and the distance from the source plus the mesh radius (w); gi = 0 when the
+ * interval starts at the source (t = 0). */
+typedef struct { int32_t tet; double a, lo, hi, gi, go, ci, co, wi, wo; } wseg;
 typedef struct { wseg *s; int64_t n, cap; } wbuf;
 
 static int wgrow(wbuf *b) {
@@ -841,7 +850,7 @@ static int walk_row(const walker *w, const double S[3], const double P[3], wbuf 
         /* the entry must be through a boundary face: the face plane that sets lo */
         double v[4][3], tf[4], den[4], sn[4];
         load_tet(w->verts, w->tets, cur, v);
-        tet_face_params(v, S, d, tf, den, sn);
+        tet_face_params(v, S, d, tf, den, sn, NULL);
         int nset = 0, bnd = 0;
         for (int k = 0; k < 4; ++k)
             if (den[k] < 0.0 && fabs(tf[k] - lo) <= WALK_TOL) { ++nset; bnd = w->adj[4 * (int64_t)cur + k] < 0; }
@@ -852,7 +861,7 @@ static int walk_row(const walker *w, const double S[3], const double P[3], wbuf 
         if (wpush(out, cur, (hi - lo) * len, lo, hi)) return -1;
         double v[4][3], tf[4], den[4], sn[4];
         load_tet(w->verts, w->tets, cur, v);
-        tet_face_params(v, S, d, tf, den, sn);
+        tet_face_params(v, S, d, tf, den, sn, NULL);
         int g = -1;
         for (int k = 0; k < 4; ++k)
             if (den[k] > 0.0 && (g < 0 || tf[k] < tf[g])) g = k;
@@ -881,9 +890,9 @@ static void row_cond(const walker *w, const double S[3], const double d[3], doub
     if (!sorted) qsort(row->s, (size_t)row->n, sizeof(wseg), seg_lo_cmp);
     for (int64_t q = 0; q < row->n; ++q) {
         wseg *e = row->s + q;
-        double v[4][3], tf[4], den[4], sn[4];
+        double v[4][3], tf[4], den[4], sn[4], kap[4];
         load_tet(w->verts, w->tets, e->tet, v);
-        tet_face_params(v, S, d, tf, den, sn);
+        tet_face_params(v, S, d, tf, den, sn, kap);
         int ki = -1, ko = -1;
         for (int k = 0; k < 4; ++k) {
             if (den[k] < 0.0 && (ki < 0 || tf[k] > tf[ki])) ki = k;
@@ -891,6 +900,22 @@ static void row_cond(const walker *w, const double S[3], const double d[3], doub
         }
         e->gi = (e->lo > 0.0 && ki >= 0) ? 1.0 / fmax(sn[ki], 1e-300) : 0.0;
         e->go = ko >= 0 ? 1.0 / fmax(sn[ko], 1e-300) : 0.0;
+        e->ci = ki >= 0 ? kap[ki] : 0.0;
+        e->co = ko >= 0 ? kap[ko] : 0.0;
+        if (!(e->a > 0.0)) {
+            /* a tet the ray only touches: it may be entered and left through
+             * any of the faces through the touching point (the largest inverse
+             * sine and the largest shape factor among them) */
+            double g = 0.0, c = 0.0;
+            for (int k = 0; k < 4; ++k)
+                if (den[k] == 0.0 || fabs(tf[k] - e->lo) <= WALK_TOL) {
+                    g = fmax(g, 1.0 / fmax(sn[k], 1e-300));
+                    c = fmax(c, kap[k]);
+                }
+            e->gi = e->lo > 0.0 ? g : 0.0;
+            e->go = g;
+            e->ci = e->co = c;
+        }
         e->wi = e->lo * len + w->radius;
         e->wo = e->hi * len + w->radius;
     }
@@ -946,13 +971,21 @@ static void *walk_worker(void *arg) {
                 double s0 = 0.0, s1 = 0.0, prev = 0.0, g = 0.0, wd = 0.0;
                 for (int64_t q = 0; q <= row.n; ++q) {
                     double cur = q < row.n ? jb->mu[(int64_t)row.s[q].tet * C + c] : 0.0;
-                    if (q == 0) { g = row.n ? row.s[0].gi : 0.0; wd = row.n ? row.s[0].wi : 0.0; }
-                    else if (q == row.n) { g = row.s[q - 1].go; wd = row.s[q - 1].wo; }
-                    else {
+                    double kp;
+                    if (q == 0) {
+                        g = row.n ? row.s[0].gi : 0.0;
+                        wd = row.n ? row.s[0].wi : 0.0;
+                        kp = row.n ? row.s[0].ci : 0.0;
+                    } else if (q == row.n) {
+                        g = row.s[q - 1].go;
+                        wd = row.s[q - 1].wo;
+                        kp = row.s[q - 1].co;
+                    } else {
                         g = fmax(row.s[q - 1].go, row.s[q].gi);
                         wd = fmax(row.s[q - 1].wo, row.s[q].wi);
+                        kp = fmax(row.s[q - 1].co, row.s[q].ci);
                     }
-                    double jump = fabs(prev - cur) * wd;
+                    double jump = fabs(prev - cur) * wd * kp;
                     s0 += jump * fmin(g, jb->cap);
                     s1 += jump * g;
                     prev = cur;
@@ -982,13 +1015,14 @@ static void *walk_worker(void *arg) {
  * (rows of rays not walked also list the tets the ray only touches, with
  * a_ik = 0: they count in the conditioning sums below, not in out_count)
  * Conditioning of the crossings (for error bounds: under rounding a crossing
- * moves along the ray by ~u (its distance from the source + the mesh radius)
- * / sin of the angle between ray and face plane), with 1 / sin capped at
- * `cap` in [..][0] and uncapped in [..][1]:
+ * moves along the ray by ~u w kappa / sin, w = its distance from the source +
+ * the mesh radius, sin = of the angle between ray and face plane, kappa = the
+ * face's shape factor, see tet_face_params), with 1 / sin capped at `cap` in
+ * [..][0] and uncapped in [..][1]:
  *   out_kf [n][C][2] (with mu): sum over a ray's crossings of
- *       |mu before - mu after| w / sin, mu = 0 outside the mesh;
+ *       |mu before - mu after| w kappa / sin, mu = 0 outside the mesh;
  *   out_kb [nt][C][2] (with y): sum over the rays crossing tet i of
- *       |y[k][c]| (w_in / sin_in + w_out / sin_out).
+ *       |y[k][c]| (w_in kappa_in / sin_in + w_out kappa_out / sin_out).
  * status[k]: 0 walked, 1 brute force, 2 brute force and a face plane contains
  * the ray (closed-tet measure: the integral counts both sides).  Backward sums
  * are added in ray order after the threads finish (deterministic).
@@ -1054,8 +1088,8 @@ int oracle_walk(void *h, const double *mu, const double *y, int C, double dso, d
                 for (int64_t k = j->begin; k < j->end; ++k)
                     for (; q < j->row_end[k - j->begin]; ++q) {
                         const wseg *e = j->rows.s + q;
-                        double c0 = e->wi * fmin(e->gi, cap) + e->wo * fmin(e->go, cap);
-                        double c1 = e->wi * e->gi + e->wo * e->go;
+                        double c0 = e->wi * e->ci * fmin(e->gi, cap) + e->wo * e->co * fmin(e->go, cap);
+                        double c1 = e->wi * e->ci * e->gi + e->wo * e->co * e->go;
                         for (int c = 0; c < C; ++c) {
                             double ay = fabs(y[k * C + c]);
                             out_kb[((int64_t)e->tet * C + c) * 2] += ay * c0;
@@ -1102,8 +1136,9 @@ static void *trace_walk_worker(void *arg) {
             jb->tet[k * jb->max_visits + q] = e->tet;
             jb->len[k * jb->max_visits + q] = e->a;
             if (jb->cond) {
-                jb->cond[(k * jb->max_visits + q) * 2] = e->wi * fmin(e->gi, 64.0) + e->wo * fmin(e->go, 64.0);
-                jb->cond[(k * jb->max_visits + q) * 2 + 1] = e->wi * e->gi + e->wo * e->go;
+                jb->cond[(k * jb->max_visits + q) * 2] =
+                    e->wi * e->ci * fmin(e->gi, 64.0) + e->wo * e->co * fmin(e->go, 64.0);
+                jb->cond[(k * jb->max_visits + q) * 2 + 1] = e->wi * e->ci * e->gi + e->wo * e->co * e->go;
             }
         }
     }
@@ -1116,7 +1151,8 @@ static void *trace_walk_worker(void *arg) {
  * also lists the tets the ray only touches, with a_ij = 0) with each a_ij, for
  * explicit rays S, P [n][3].  out_count[k] is the full count
  * (visits past max_visits are dropped).  out_cond (or NULL) [n][max_visits][2]:
- * each visit's w_in / sin_in + w_out / sin_out (see oracle_walk), with 1 / sin
+ * each visit's w_in kappa_in / sin_in + w_out kappa_out / sin_out (see
+ * oracle_walk), with 1 / sin
  * capped at 64 and uncapped.  Returns 0 or -1 (no memory). */
 int oracle_walk_trace(void *h, const double *S, const double *P, int64_t n, int64_t max_visits,
                       int32_t *out_tet, double *out_len, double *out_cond, int64_t *out_count,

@@ -15,21 +15,25 @@ checks and get y = 0 in the backprojections; their references are the exact
 ones of test_gpu_parity / test_gpu_fullsize.
 
 Tolerances, from the arithmetic.  Rounding moves a crossing point along the
-ray by about u (L + R) / sin(alpha): L its distance from the source, R the
-mesh radius, alpha the angle between ray and face plane (the crossing is a
+ray by about u (L + R) kappa / sin(alpha): L its distance from the source, R
+the mesh radius, alpha the angle between ray and face plane, kappa the
+crossed face's shape factor (sum of squared edges / 2|n|: sqrt 3 for an
+equilateral face, ~1 / sin of the smallest angle for a sliver, by which the
+rounding of the face normal's cross product turns it).  The crossing is a
 ratio of two quantities each computed to a few u of magnitudes proportional
-to sin(alpha) -- in the oracle's clipper and in both GPU paths).  A ray's
+to sin(alpha) -- in the oracle's clipper and in both GPU paths.  A ray's
 integral moves by the crossing's shift times the jump of mu there; a tet's
 backprojection by the shifts of its two crossings times y.  The walker sums
-these per ray (K_j = sum |mu jump| (L + R) / sin) and per tet (K_i = sum_j
-|y_j| ((L + R) / sin_in + (L + R) / sin_out)).  Bounds:
+these per ray (K_j = sum |mu jump| (L + R) kappa / sin) and per tet
+(K_i = sum_j |y_j| ((L + R) kappa / sin)_in + ((L + R) kappa / sin)_out).
+Bounds:
   per ray  |b_gpu - b_ref| <= max(tau sum_i a_ij |mu_i|, 32 e K_j)
   per tet  |x_gpu - x_ref| <= max(tau sum_j a_ij |y_j|, 32 e K_i)
 with e = 2^-53 on the FP64 path, and on the FP32 path e K = 2^-24 K(1 / sin
 capped at 64) + 2^-53 K (crossings with sin below 1/64 are placed again in
-FP64).  32 covers both sides' errors (each ~13 u (L + R) / sin: the cross
-product, the two dot products and the division).  tau is 1e-5 (FP32) or
-1e-12 (FP64) relative.  Each check prints how many rays or tets only the
+FP64).  32 covers both sides' errors (each ~13 u (L + R) kappa / sin: the
+cross product, the two dot products and the division).  tau is 1e-5 (FP32)
+or 1e-12 (FP64) relative.  Each check prints how many rays or tets only the
 conditioning term admits.  A ray through an edge or vertex touches tets with
 a_ij = 0 that a computed walk may visit with a chord of its rounding's size:
 the walker's rows for such rays list those tets, so their conditioning is in

@@ -182,33 +182,38 @@ def test_crossing_conditioning_by_hand():
     """The conditioning sums the parity tests scale their floors by, on the
     corner tet (0,0,0), (1,0,0), (0,1,0), (0,0,1) and the ray from (-2, .1, .2)
     along +x (d = (4, 0, 0)): it enters through x = 0 at t = 1/2 (distance 2
-    from the source, sin 1) and leaves through x + y + z = 1 at x = 0.7,
-    t = 0.675 (distance 2.7, sin 1/sqrt 3); mesh radius 1.  Per ray
-    K = |mu| (2 + 1) / 1 + |mu| (2.7 + 1) sqrt 3; per tet the same with |y|;
-    with 1 / sin capped at 1 the second term loses its sqrt 3."""
+    from the source, sin 1; the face's edges 1, 1, sqrt 2 and |n| = 1 give the
+    shape factor (1 + 1 + 2) / 2 = 2) and leaves through x + y + z = 1 at
+    x = 0.7, t = 0.675 (distance 2.7, sin 1/sqrt 3; edges sqrt 2, |n| = sqrt 3:
+    factor 6 / (2 sqrt 3) = sqrt 3); mesh radius 1.  Per ray
+    K = |mu| (2 + 1) 2 / 1 + |mu| (2.7 + 1) sqrt 3 sqrt 3; per tet the same
+    with |y|; with 1 / sin capped at 1 the second term's sin factor is 1."""
     verts = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
     tets = np.array([[0, 1, 2, 3]])
     S = np.array([[-2.0, 0.1, 0.2]])
     P = S + np.array([[4.0, 0, 0]])
     wk = oracle.Walker(verts, tets)
-    for cap, g_out in ((64.0, np.sqrt(3.0)), (1.0, 1.0)):
+    r3 = np.sqrt(3.0)
+    for cap, g_out in ((64.0, r3), (1.0, 1.0)):
         fwd, bwd, st = wk.rows_rays(np.array([-1.5]), np.array([2.0]), S, P, threads=1, cap=cap)
         assert st[0] == 0 and abs(fwd[0, 0] - (-1.5 * 0.7)) < 1e-15
-        want = 3.0 + 3.7 * g_out
+        want = 6.0 + 3.7 * r3 * g_out
         assert abs(wk.last_kf[0, 0, 0] - 1.5 * want) < 1e-13
-        assert abs(wk.last_kf[0, 0, 1] - 1.5 * (3.0 + 3.7 * np.sqrt(3.0))) < 1e-13
+        assert abs(wk.last_kf[0, 0, 1] - 1.5 * (6.0 + 3.7 * 3.0)) < 1e-13
         assert abs(wk.last_kb[0, 0, 0] - 2.0 * want) < 1e-13
         assert abs(bwd[0, 0] - 2.0 * 0.7) < 1e-15
     tet, ln, cnt, st = wk.trace_rays(S, P, max_visits=4)
     assert cnt[0] == 1 and tet[0, 0] == 0 and abs(ln[0, 0] - 0.7) < 1e-15
-    assert abs(wk.last_cond[0, 0, 1] - (3.0 + 3.7 * np.sqrt(3.0))) < 1e-13
+    assert abs(wk.last_cond[0, 0, 1] - (6.0 + 3.7 * 3.0)) < 1e-13
 
 
 def test_crossing_conditioning_constant_mu(meshes):
     """mu = 1 on a jittered mesh: mu jumps only where the ray enters and leaves
-    the cube, so K = (L_in + R) / sin_in + (L_out + R) / sin_out with the
-    cube's axis faces (sin = |d_k| / |d| for the face normal to axis k),
-    L the distance from the source, R = 1."""
+    the cube, so K = 2 (L_in + R) / sin_in + 2 (L_out + R) / sin_out with the
+    cube's axis faces (sin = |d_k| / |d| for the face normal to axis k; the
+    boundary faces are unjittered right isosceles triangles: shape factor
+    (h^2 + h^2 + 2 h^2) / (2 h^2) = 2), L the distance from the source,
+    R = 1."""
     w = meshes["jittered"]
     wk = oracle.Walker(w.verts, w.tets)
     S, P = W.random_rays_through_box(2000, np.random.default_rng(12))
@@ -232,8 +237,8 @@ def test_crossing_conditioning_constant_mu(meshes):
         ax_out = np.where(hi < t_out, k, ax_out)
         t_out = np.minimum(t_out, hi)
     r = np.arange(S.shape[0])
-    want = ((t_in * dn + 1.0) * dn / np.abs(d[r, ax_in]) +
-            (t_out * dn + 1.0) * dn / np.abs(d[r, ax_out]))[ok]
+    want = 2.0 * ((t_in * dn + 1.0) * dn / np.abs(d[r, ax_in]) +
+                  (t_out * dn + 1.0) * dn / np.abs(d[r, ax_out]))[ok]
     keep = st == 0
     assert keep.mean() > 0.95
     assert np.all(np.abs(K[keep] - want[keep]) <= 1e-9 * want[keep])
