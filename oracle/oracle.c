@@ -893,29 +893,22 @@ static void row_cond(const walker *w, const double S[3], const double d[3], doub
         double v[4][3], tf[4], den[4], sn[4], kap[4];
         load_tet(w->verts, w->tets, e->tet, v);
         tet_face_params(v, S, d, tf, den, sn, kap);
-        int ki = -1, ko = -1;
+        /* the faces whose planes pass through the entry and the exit point:
+         * one each for a crossing through a face's interior; two or three
+         * when the ray crosses an edge or a vertex (a tet it only touches has
+         * entry = exit), where a computed walk may cross any of them -- take
+         * the largest inverse sine and the largest shape factor among them */
+        double gi = 0.0, go = 0.0, ci = 0.0, co = 0.0;
         for (int k = 0; k < 4; ++k) {
-            if (den[k] < 0.0 && (ki < 0 || tf[k] > tf[ki])) ki = k;
-            if (den[k] > 0.0 && (ko < 0 || tf[k] < tf[ko])) ko = k;
+            const double g = 1.0 / fmax(sn[k], 1e-300);
+            if (den[k] == 0.0) continue;  /* parallel to the ray: not crossed */
+            if (fabs(tf[k] - e->lo) <= WALK_TOL) { gi = fmax(gi, g); ci = fmax(ci, kap[k]); }
+            if (fabs(tf[k] - e->hi) <= WALK_TOL) { go = fmax(go, g); co = fmax(co, kap[k]); }
         }
-        e->gi = (e->lo > 0.0 && ki >= 0) ? 1.0 / fmax(sn[ki], 1e-300) : 0.0;
-        e->go = ko >= 0 ? 1.0 / fmax(sn[ko], 1e-300) : 0.0;
-        e->ci = ki >= 0 ? kap[ki] : 0.0;
-        e->co = ko >= 0 ? kap[ko] : 0.0;
-        if (!(e->a > 0.0)) {
-            /* a tet the ray only touches: it may be entered and left through
-             * any of the faces through the touching point (the largest inverse
-             * sine and the largest shape factor among them) */
-            double g = 0.0, c = 0.0;
-            for (int k = 0; k < 4; ++k)
-                if (den[k] == 0.0 || fabs(tf[k] - e->lo) <= WALK_TOL) {
-                    g = fmax(g, 1.0 / fmax(sn[k], 1e-300));
-                    c = fmax(c, kap[k]);
-                }
-            e->gi = e->lo > 0.0 ? g : 0.0;
-            e->go = g;
-            e->ci = e->co = c;
-        }
+        e->gi = e->lo > 0.0 ? gi : 0.0;  /* no entry crossing when the interval starts at the source */
+        e->ci = e->lo > 0.0 ? ci : 0.0;
+        e->go = go;
+        e->co = co;
         e->wi = e->lo * len + w->radius;
         e->wo = e->hi * len + w->radius;
     }
