@@ -263,3 +263,25 @@ def test_trace_equals_brute_force_trace(meshes, name):
         n = cnt[k]
         assert np.array_equal(tet[k, :n], bt[k, :n]), k
         assert np.array_equal(ln[k, :n], (bhi[k, :n] - blo[k, :n]) * dl[k])
+
+
+def test_crossing_conditioning_at_an_edge():
+    """A ray entering the corner tet exactly through its edge (0,0,0)-(0,0,1),
+    at (0, 0, 1/2), along d = (2, 4, 0) from S = (-1, -2, 1/2): two face planes
+    pass through the entry point, x = 0 (sin = 2/|d| = 1/sqrt 5) and y = 0
+    (sin 2/sqrt 5), both with shape factor 2; the bound takes the worse,
+    1/sin = sqrt 5.  Entry at t = 1/2 (distance sqrt 5), exit through
+    x + y + z = 1 at t = 7/12 (distance 7 sqrt 5 / 6, sin 3/sqrt 15, shape
+    factor sqrt 3); chord sqrt 5 / 6; mesh radius 1."""
+    verts = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    tets = np.array([[0, 1, 2, 3]])
+    S = np.array([[-1.0, -2.0, 0.5]])
+    P = np.array([[1.0, 2.0, 0.5]])
+    wk = oracle.Walker(verts, tets)
+    fwd, bwd, st = wk.rows_rays(np.array([1.0]), np.array([1.0]), S, P)
+    r5 = np.sqrt(5.0)
+    assert st[0] == 1  # the entry is a tie: the row comes from the clipper
+    assert abs(fwd[0, 0] - r5 / 6) < 1e-15
+    want = (r5 + 1.0) * 2.0 * r5 + (7 * r5 / 6 + 1.0) * np.sqrt(3.0) * np.sqrt(15.0) / 3.0
+    assert abs(wk.last_kf[0, 0, 1] - want) < 1e-12 * want
+    assert abs(wk.last_kb[0, 0, 1] - want) < 1e-12 * want
