@@ -53,3 +53,17 @@ def test_single_process_paths():
     import bench
     assert bench.max_over_ranks(42.0, None) == 42.0
     assert bench.job_throughput(1, 500, 250.0) == pytest.approx(2000.0)
+
+
+def test_cpu_baseline_both_oracles():
+    """The CPU baseline leg (and the reference arm) times the oracle walker by
+    default and the brute-force clipper on request; both run on a small case."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    w = W.config1(n_cells=4, det=16, pitch=0.3, nangles=4)
+    for kind in ("walker", "clipper"):
+        rate, threads, dt, n = bench.cpu_baseline(w, 64, kind=kind)
+        assert n == 64 and rate > 0 and dt > 0 and threads >= 1
+        assert "oracle walker" in bench.cpu_sample_text("walker", 64, w.geom.nrays)
