@@ -285,3 +285,81 @@ def test_crossing_conditioning_at_an_edge():
     want = (r5 + 1.0) * 2.0 * r5 + (7 * r5 / 6 + 1.0) * np.sqrt(3.0) * np.sqrt(15.0) / 3.0
     assert abs(wk.last_kf[0, 0, 1] - want) < 1e-12 * want
     assert abs(wk.last_kb[0, 0, 1] - want) < 1e-12 * want
+
+
+# Plausible mistakes planted in a copy of oracle.c: each must fail one of the
+# pins above (values equal to the brute-force clipper's, most rays walked).
+PLANTED = [
+    ("exit through the farthest face plane",
+     "if (den[k] > 0.0 && (g < 0 || tf[k] < tf[g])) g = k;",
+     "if (den[k] > 0.0 && (g < 0 || tf[k] > tf[g])) g = k;"),
+    ("neighbour's tet index off by one",
+     "w->adj[f[x].code] = f[x + 1].code >> 2;",
+     "w->adj[f[x].code] = (f[x + 1].code >> 2) ^ 1;"),
+    ("entry through the last boundary tet instead of the first",
+     "if (l < lo) { second = lo; lo = l; hi = h; cur = w->btet[q]; }",
+     "if (lo == INFINITY || l > lo) { second = INFINITY; lo = l; hi = h; cur = w->btet[q]; }"),
+    ("chord measured from the source instead of the entry",
+     "if (wpush(out, cur, (hi - lo) * len, lo, hi)) return -1;",
+     "if (wpush(out, cur, hi * len, lo, hi)) return -1;"),
+]
+
+
+def _walk_copy(tmp_path, w, src):
+    """Compile `src` (a copy of oracle.c) and walk every 5th cone ray of `w`
+    with it: (values equal the clipper's, more than 90% of rays walked)."""
+    import ctypes
+    import subprocess
+    (tmp_path / "oracle.c").write_text(src)
+    lib = str(tmp_path / "libcopy.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+                    "-o", lib, str(tmp_path / "oracle.c"), "-lm"], check=True)
+    L = ctypes.CDLL(lib)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_walker_create.restype = ctypes.c_void_p
+    L.oracle_walker_create.argtypes = [dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    L.oracle_walk.restype = ctypes.c_int
+    L.oracle_walk.argtypes = ([ctypes.c_void_p, dp, dp, ctypes.c_int] + [ctypes.c_double] * 2 +
+                              [ctypes.c_int64] * 2 + [ctypes.c_double] * 2 +
+                              [dp, ctypes.c_int64, ctypes.c_void_p, dp, dp, ctypes.c_int64, dp, dp,
+                               ctypes.c_void_p, ctypes.c_double, dp, dp,
+                               ctypes.POINTER(ctypes.c_int8), ctypes.c_int])
+    L.oracle_walker_destroy.argtypes = [ctypes.c_void_p]
+    v = np.ascontiguousarray(w.verts, dtype=np.float64)
+    t = np.ascontiguousarray(w.tets, dtype=np.int32)
+    st = ctypes.c_int(0)
+    h = L.oracle_walker_create(v.ctypes.data_as(dp), v.shape[0],
+                               t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), t.shape[0],
+                               ctypes.byref(st))
+    assert h
+    S, P = oracle.cone_rays(w.geom, np.arange(0, w.geom.nrays, 5))
+    S, P = np.ascontiguousarray(S), np.ascontiguousarray(P)
+    n = S.shape[0]
+    mu = np.ascontiguousarray(w.mu, dtype=np.float64)
+    out = np.zeros(n)
+    status = np.zeros(n, dtype=np.int8)
+    rc = L.oracle_walk(h, mu.ctypes.data_as(dp), None, 1, 0.0, 0.0, 0, 0, 0.0, 0.0, None, 0, None,
+                       S.ctypes.data_as(dp), P.ctypes.data_as(dp), n, out.ctypes.data_as(dp), None,
+                       None, 64.0, None, None, status.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), 4)
+    L.oracle_walker_destroy(h)
+    want = oracle.forward_rays(w.verts, w.tets, mu, S, P)
+    values_ok = rc == 0 and bool(np.all(np.abs(out - want) <= 1e-14 * np.abs(want) + 1e-300))
+    return values_ok, bool((status == 0).mean() > 0.9)
+
+
+def _oracle_source():
+    import os
+    return open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+
+
+def test_copy_harness_passes_unchanged_source(tmp_path, meshes):
+    assert _walk_copy(tmp_path, meshes["jittered"], _oracle_source()) == (True, True)
+
+
+@pytest.mark.parametrize("what,old,new", PLANTED, ids=[p[0] for p in PLANTED])
+def test_pins_catch_planted_mistakes(tmp_path, meshes, what, old, new):
+    src = _oracle_source()
+    assert src.count(old) == 1
+    values_ok, walked_ok = _walk_copy(tmp_path, meshes["jittered"], src.replace(old, new))
+    assert not (values_ok and walked_ok), what
