@@ -209,3 +209,85 @@ def test_miss_is_zero(oracle_lib):
     P = np.array([[-4.0, 0, 2.5], [0, 3.0, 5.0]])
     b = oracle_lib.forward_rays(verts, tets, np.ones(tets.shape[0]), S, P)
     assert np.all(b == 0.0)
+
+
+# Plausible mistakes planted in a compiled copy of oracle.c's clipper: each must
+# fail the golden chords or the closed-form cube chord above.
+PLANTED = [
+    ("exit parameter keeps the largest face crossing", "            if (t < h) h = t;",
+     "            if (t > h || h == INFINITY) h = t;"),
+    ("face normals oriented inwards",
+     "if (side > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }",
+     "if (side < 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }"),
+    ("the whole line instead of the half-line t >= 0", "    double l = t0, h = t1;",
+     "    double l = -INFINITY, h = t1;"),
+    ("chord in units of t instead of length",
+     "    return hi > lo ? (hi - lo) * sqrt(dot3(d, d)) : 0.0;",
+     "    return hi > lo ? (hi - lo) : 0.0;"),
+]
+
+
+def _golden_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "single_tet_chords.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append([float(x) for x in line.split()])
+    return rows
+
+
+def _clipper_copy_ok(tmp_path, src):
+    """Compile `src` (a copy of oracle.c); True if its chords match the golden
+    file and its mu = 1 sums on a jittered 4^3 mesh the cube chord."""
+    import ctypes
+    import subprocess
+    (tmp_path / "oracle.c").write_text(src)
+    lib = str(tmp_path / "libclip.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+                    "-o", lib, str(tmp_path / "oracle.c"), "-lm"], check=True)
+    L = ctypes.CDLL(lib)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_tet_chord.restype = ctypes.c_double
+    L.oracle_tet_chord.argtypes = [dp, dp, dp, dp, dp]
+    L.oracle_forward_rays.restype = ctypes.c_int
+    L.oracle_forward_rays.argtypes = [dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.c_int64, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int64,
+                                      dp, ctypes.c_int]
+    V = np.ascontiguousarray([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    for r in _golden_rows():
+        S = np.ascontiguousarray(r[0:3], dtype=np.float64)
+        P = np.ascontiguousarray(r[3:6], dtype=np.float64)
+        a = L.oracle_tet_chord(V.ctypes.data_as(dp), S.ctypes.data_as(dp), P.ctypes.data_as(dp),
+                               ctypes.byref(lo), ctypes.byref(hi))
+        if not abs(a - r[6]) <= 1e-15 * max(1.0, r[6]):
+            return False
+    verts, tets = W.kuhn_cube(4)
+    verts = np.ascontiguousarray(W.jitter_interior(verts, tets, 4, W.rng_for(9, 2)))
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    S, P = W.random_rays_through_box(300, np.random.default_rng(13))
+    S, P = np.ascontiguousarray(S), np.ascontiguousarray(P)
+    ones = np.ones(tets.shape[0])
+    out = np.zeros(S.shape[0])
+    rc = L.oracle_forward_rays(verts.ctypes.data_as(dp), verts.shape[0],
+                               tets.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), tets.shape[0],
+                               ones.ctypes.data_as(dp), 1, S.ctypes.data_as(dp),
+                               P.ctypes.data_as(dp), None, S.shape[0], out.ctypes.data_as(dp), 4)
+    want = np.array([_cube_chord(S[k], P[k]) for k in range(S.shape[0])])
+    return rc == 0 and bool(np.all(np.abs(out - want) <= 1e-12 * np.maximum(want, 1.0)))
+
+
+def _oracle_source():
+    return open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "oracle", "oracle.c")).read()
+
+
+def test_clipper_copy_harness_passes_unchanged_source(tmp_path):
+    assert _clipper_copy_ok(tmp_path, _oracle_source())
+
+
+@pytest.mark.parametrize("what,old,new", PLANTED, ids=[p[0] for p in PLANTED])
+def test_pins_catch_planted_clipper_mistakes(tmp_path, what, old, new):
+    src = _oracle_source()
+    assert src.count(old) == 1
+    assert not _clipper_copy_ok(tmp_path, src.replace(old, new)), what
