@@ -92,7 +92,8 @@ struct tetproj_mesh {
 // of them when a call has several chunks); on the 94M-ray jittered 96^3 step
 // 1% faster than 2^23 (272.7 vs 275.5 ms), 2^22 was 2% slower.  A batch holds
 // one queue pair for all its problems and runs rounds of 2^25 rays (2.5 GB
-// each): on 24 config-5 problems 2,606 ms per step against 2,722 at 2^23.
+// each): on 24 jittered Kuhn meshes of 16^3-118^3 cells (1.6G rays, C = 4)
+// 2,606 ms per forward + backprojection against 2,722 at 2^23.
 static const int64_t kQueueMax = int64_t(1) << 24;
 static const int64_t kBatchQueueMax = int64_t(1) << 25;
 

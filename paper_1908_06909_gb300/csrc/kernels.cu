@@ -1392,8 +1392,8 @@ static cudaError_t launch_entry_map(KParams &p, int64_t b0, int64_t nb, cudaStre
 #define TP_BATCH_RING 4
 
 // 7 resident CTAs per SM: at most 72 registers, no spills (8 CTAs cap it at 64 with
-// spills in the backprojection; batch of 24 config-5 problems, C = 4: 2,746
-// vs 2,835 ms per forward + backprojection)
+// spills in the backprojection; 24 jittered Kuhn meshes of 16^3-118^3 cells,
+// 1.6G rays, C = 4: 2,746 vs 2,835 ms per forward + backprojection)
 #ifndef TP_BATCH_MIN_BLOCKS
 #define TP_BATCH_MIN_BLOCKS 7
 #endif
