@@ -207,6 +207,13 @@ def test_config4_walker_sampled(tp, c4, prec):
     c4.check(tp, prec)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_config3_detector_rays_walker_sampled(tp, prec):
+    """Config 3's detector rays (cubic-mapped Kuhn 64^3, spacing ratio ~3e3:
+    sliver tets near the centre), 10^5 of them, both precisions."""
+    Single(tp, W.config3(n_adversarial=0), 63).check(tp, prec)
+
+
 @pytest.mark.parametrize("scatter", ["warp", "sort"])
 def test_config2_scatter_variants_walker_sampled(tp, c2, scatter):
     """The two other backprojection scatters on the bench workload (FP32):
