@@ -67,3 +67,25 @@ def test_cpu_baseline_both_oracles():
         rate, threads, dt, n = bench.cpu_baseline(w, 64, kind=kind)
         assert n == 64 and rate > 0 and dt > 0 and threads >= 1
         assert "oracle walker" in bench.cpu_sample_text("walker", 64, w.geom.nrays)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` prints one JSON line with the contract's keys
+    (run on a small workload, as on the host of a GPU machine)."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "kuhn24", "--steps", "1", "--warmup", "1",
+                        "--cpu-sample", "256"], capture_output=True, text=True, cwd=ROOT,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
